@@ -1,0 +1,290 @@
+#!/usr/bin/env python
+"""REXI steps/s at T341, K=256 poles on one GB300 (or N replicas).
+
+Workload: one T-REXI step (Algorithm 1) of the linear SWE for a batch of 16
+seeded states (complex-normal n^-3 spectra, h' std 50 m, u,v std 5 m/s),
+truncation T341 on a 1024 x 512 Gaussian grid, M = 256 Gaussian basis functions
+per side (P = 535 poles), h = 0.2, tau = 1200 s, grid layout in and out (h', u, v
+float64).  A step = longitude FFTs, Legendre analysis, the 535 x 342 x 2 banded
+solves with the beta-weighted pole sum, Legendre synthesis, inverse FFTs.
+Inputs (201 MB) and factors (4.5 GB) are larger than L2, so no flush is done.
+
+`python bench.py [--gpus N --steps K --warmup W] [--impl reference]` prints
+one JSON line.  For N > 1 (torchrun) every rank runs an independent replica
+(the path has no exchange step) and value is the sum over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORK = dict(N=341, nlat=512, nlon=1024, M=256, h=0.2, tau=1200.0, batch=16, seed=1005)
+METRIC = "REXI steps/s at T341, K=256 poles: chosen vs plain FP64 form at stated error"
+FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve
+
+
+def rows_of(N):
+    return (N + 1) * (N + 2) // 2 - 1  # every (m, n) except (0, 0)
+
+
+def fp64_peak_tflops(sm_mhz):
+    # GB300: 152 SMs x 2 FP64 FMA/clk/SM (nominal 1.25 TFLOP/s at 2070 MHz)
+    return 152 * 4 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def cpu_baseline(sample_ms=None):
+    """The CPU oracle as it stands on a bounded sample of the workload, extrapolated to one step."""
+    import threadpoolctl  # noqa: F401  (thread count report only)
+    from oracle import rexi_coeffs
+    from oracle import step as ostep
+    from paper_1812_03431_gb300 import inputs
+    N, B = WORK["N"], WORK["batch"]
+    al, be, _ = rexi_coeffs.rexi_coefficients(WORK["M"], WORK["h"])
+    S = inputs.random_spectral(N, 1, WORK["seed"])
+    ms = sample_ms if sample_ms is not None else list(range(0, N + 1, 57))
+    t0 = time.perf_counter()
+    ostep.rexi_step_spectral(S, N, al, be, WORK["tau"], ms=ms)
+    t_solve = time.perf_counter() - t0
+    rows_sample = sum(N - m + 1 for m in ms)
+    rows_all = rows_of(N) + 1
+    gs = ostep.GridStep(N, WORK["nlat"], WORK["nlon"], al[:1], be[:1], WORK["tau"])
+    t0 = time.perf_counter()
+    x = gs.synthesise(S)
+    gs.analyse(x)
+    t_tr = time.perf_counter() - t0
+    t_step = B * (t_solve * rows_all / rows_sample + t_tr)
+    cores = 1
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([1] + [i.get("num_threads", 1) for i in threadpool_info()])
+    except Exception:
+        pass
+    sample = ("1 of %d states; banded solves for m in %s (%d of %d coefficient rows, all %d poles) plus one "
+              "analysis+synthesis, extrapolated linearly to the full step" % (B, ms, rows_sample, rows_all, len(al)))
+    return {"value": 1.0 / t_step, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample,
+            "sample_seconds": t_solve + t_tr}
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    per = []
+    for i in range(args.warmup + args.steps):
+        m0 = (37 * i) % (WORK["N"] + 1)
+        r = cpu_baseline(sample_ms=[m0, (m0 + 171) % (WORK["N"] + 1)])
+        if i >= args.warmup:
+            per.append(1.0 / r["value"])
+    ms_step = 1e3 * statistics.mean(per)
+    v = 1e3 / ms_step
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(), "cpu_baseline": {**r, "value": v},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config():
+    return {"workload": "T-REXI step, linear SWE on the sphere: T341, 1024x512 Gaussian grid, K=M=256 "
+                        "(P=535 poles), h=0.2, tau=1200 s, 16 seeded n^-3 states, grid layout",
+            "global_batch": WORK["batch"], "truncation": WORK["N"], "grid": [WORK["nlat"], WORK["nlon"]],
+            "poles": 2 * (WORK["M"] + 11) + 1, "parallelism": "replicas",
+            "l2": "inputs (201 MB) and factors (4.5 GB) larger than L2, no flush"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1812_03431_gb300 import inputs, rexi
+
+    W = WORK
+    B = W["batch"]
+    precisions = ["fp64"]
+    if args.precision in ("auto", "mixed"):
+        try:
+            rexi.Plan(15, 16, 48, M=4, precision="mixed").close()
+            precisions = ["mixed", "fp64"] if args.precision == "auto" else ["mixed"]
+        except rexi.RexiError:
+            if args.precision == "mixed":
+                raise
+    S = torch.from_numpy(inputs.random_spectral(W["N"], B, W["seed"])).cuda()
+    results = {}
+    stream = torch.cuda.current_stream()
+    for prec in precisions:
+        plan = rexi.Plan(W["N"], W["nlat"], W["nlon"], M=W["M"], h=W["h"], tau=W["tau"], max_batch=B,
+                         precision=prec)
+        x = plan.synthesize(S)
+        y = torch.empty_like(x)
+        for _ in range(args.warmup):
+            plan.step(x, out=y)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        plan.profile_enable(args.steps)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.step(x, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms = e0.elapsed_time(e1) / args.steps
+        stages, ncalls = plan.profile_read()
+        plan.profile_enable(0)
+        ck = clocks.stop()
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        # e2e through the public API with pinned host buffers, copies inside the timed region
+        xh = x.cpu().pin_memory()
+        yh = torch.empty(y.shape, dtype=y.dtype).pin_memory()
+        xd = torch.empty_like(x)
+        for _ in range(2):
+            xd.copy_(xh, non_blocking=True)
+            plan.step(xd, out=y)
+            yh.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            xd.copy_(xh, non_blocking=True)
+            plan.step(xd, out=y)
+            yh.copy_(y, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = f0.elapsed_time(f1) / args.steps
+        if dist:
+            t = torch.tensor([ms_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        results[prec] = dict(ms=ms, ms_e2e=ms_e2e, stages={k: v / max(ncalls, 1) for k, v in stages.items()},
+                             clocks=ck, y=y, bytes=x.numel() * 8, info=plan.info())
+        plan.close()
+
+    chosen = precisions[0]
+    r = results[chosen]
+    P = 2 * (W["M"] + 11) + 1
+    solve_ms = r["stages"]["solve"]
+    flops = FLOPS_PER_ROW * B * P * rows_of(W["N"])
+    sm_mhz = (r["clocks"] or {}).get("sm_max_mhz") or 2070.0
+    peak = fp64_peak_tflops(sm_mhz)
+    achieved = flops / (solve_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": world * 1e3 / r["ms"], "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if chosen == "fp64" else "f64 solves + 3xtf32 legendre",
+        "data": "synthetic", "config": {**workload_config(), "form": chosen},
+        "roofline": {"bound": "alu", "kernel": "solve_kernel (FP64 banded solves + pole sum)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz",
+                     "flops_per_launch": flops, "launch_ms": solve_ms},
+        "stage_ms": r["stages"],
+        "e2e": {"value": world * 1e3 / r["ms_e2e"], "unit": "steps/s", "h2d_bytes_per_step": r["bytes"],
+                "d2h_bytes_per_step": r["bytes"]},
+        "gpu_launches": 6 * args.steps,
+        "clocks": r["clocks"],
+    }
+    if "fp64" in results and chosen != "fp64":
+        f = results["fp64"]
+        d = (results[chosen]["y"] - f["y"]).norm() / f["y"].norm()
+        line["fp64_form"] = {"value": world * 1e3 / f["ms"], "ms_per_step": f["ms"], "stage_ms": f["stages"]}
+        line["error_vs_fp64_form"] = float(d)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * rexi.h -- C-ABI of librexi: one T-REXI time step of the linearised
+ * shallow-water equations (SWE) on the rotating sphere, on one GB300 GPU.
+ *
+ * Method (Schreiber & Loft, "A parallel time-integrator for solving the
+ * linearized shallow water equations on the rotating sphere", Sec. 4-5,
+ * Algorithm 1):
+ *
+ *     U(t + tau)  ~  Re  sum_{k=1}^{P}  beta_k (alpha_k + tau L)^{-1} U(t)
+ *
+ * with L the linear SWE operator of Eq. (1) in vorticity-divergence form and
+ * (alpha_k, beta_k) the T-REXI poles of Sec. 4.1.  This is the paper's form
+ * (alpha + L); the equivalent form sum beta'(alpha' - tau L)^{-1} has
+ * alpha' = -alpha, beta' = -beta.  L is block-diagonal in the zonal
+ * wavenumber m, so every (pole, m) pair is an independent banded solve in the
+ * spherical-harmonic degree n (Sec. 5).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Spectral state: complex128 (interleaved re, im doubles), layout
+ *   [batch][3][nspec], fields (Phi, zeta, delta) = (geopotential perturbation
+ *   g h' in m^2/s^2, relative vorticity in 1/s, divergence in 1/s); within a
+ *   field the coefficients xi_n^m, 0 <= m <= n <= N, are m-major:
+ *   idx(m, n) = m (2N + 3 - m) / 2 + (n - m),  nspec = (N + 1)(N + 2) / 2.
+ *   Orthonormal associated Legendre functions, int_{-1}^{1} Pbar^2 dmu = 1,
+ *   no Condon-Shortley phase; a real field is sum over m = -N..N with
+ *   xi^{-m} = conj(xi^m).  zeta_0^0 and delta_0^0 are not state variables:
+ *   ignored on input, zero on output.  m = 0 outputs are real.
+ * Grid state: float64, layout [batch][3][nlat][nlon], fields (h', u, v) in
+ *   (m, m/s, m/s) on the Gaussian grid: latitude j = 0..nlat-1 from north to
+ *   south (mu_j = sin(lat_j) are the Gauss-Legendre nodes, descending),
+ *   longitude lambda_i = 2 pi i / nlon.  Robert's cos(lat) scaling (Sec. 3) is
+ *   applied inside.
+ * Device pointers: every in/out pointer below named *_dev is a device pointer
+ *   to caller-owned, contiguous, 16-byte aligned memory; in and out must not
+ *   overlap (REXI_EINVAL).  The plan owns every other allocation.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *   enqueue work and return without synchronising the host; no device memory
+ *   is allocated inside rexi_step / rexi_step_adjoint once a batch size has
+ *   been seen by the plan (its work list is cached), so those calls can be
+ *   captured in a CUDA graph after a first eager call with the same batch.
+ * Errors: negative rexi_status; rexi_last_error() gives a thread-local
+ *   message.  A CUDA launch error is reported by the call that launched.
+ */
+#ifndef REXI_H
+#define REXI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  REXI_OK = 0,
+  REXI_EINVAL = -1,   /* bad argument, size or alignment */
+  REXI_ENOMEM = -2,   /* device or host allocation failed */
+  REXI_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+  REXI_ERANGE = -4,   /* tau * max|omega| outside the poles' valid range (strict plans only) */
+  REXI_ETIMEOUT = -5  /* a bounded device-side wait expired */
+} rexi_status;
+
+enum { REXI_FP64 = 0,      /* every stage in FP64 */
+       REXI_MIXED = 1 };   /* Legendre contractions as 3xTF32 tensor-core products with FP32
+                              accumulation and FP32 longitude FFTs; banded solves and the
+                              beta-weighted pole sum stay FP64 */
+enum { REXI_GRID = 0,      /* rexi_step in/out are grid states */
+       REXI_SPECTRAL = 1 }; /* rexi_step in/out are spectral states */
+
+typedef struct rexi_plan rexi_plan;
+
+/* Plan parameters.  Defaults (rexi_params_default): earth constants of
+ * Sec. 6 (a = 6.37122e6 m, Omega = 7.292e-5 1/s, g = 9.80616 m/s^2,
+ * Hbar = 1e4 m), h = 0.2, normalize = 1, FP64, grid layout, max_batch = 1. */
+typedef struct {
+  int32_t ntrunc;       /* N: triangular truncation, 1 <= N */
+  int32_t nlat, nlon;   /* Gaussian grid; nlat even, nlat >= N + 1, nlon >= 2N + 1,
+                           nlon = 2^a 3^b 5^c; used by the grid layout only */
+  int32_t M;            /* Gaussian basis functions per side (Sec. 4.1); P = 2 (M + 11) + 1 */
+  double h;             /* width parameter of the Gaussian basis (Sec. 4.1) */
+  double tau;           /* time-step size (s) */
+  double radius, omega, gravity, mean_depth; /* a, Omega, g, Hbar */
+  int32_t normalize;    /* 1: beta <- beta / sum(beta/alpha) (Sec. 6.1) */
+  int32_t precision;    /* REXI_FP64 | REXI_MIXED */
+  int32_t layout;       /* REXI_GRID | REXI_SPECTRAL */
+  int32_t max_batch;    /* largest batch passed to rexi_step (sizes workspaces) */
+  int32_t strict_range; /* 1: plan creation fails with REXI_ERANGE when tau * max|omega|
+                           exceeds h (M - 10), the range where Re of the REXI symbol
+                           matches cos to the fit level */
+  int32_t pole_slots;   /* 0: autotuned; else number of pole groups summed separately in
+                           the solve kernel (a deterministic tuning knob, any >= 1) */
+  const double *alpha;  /* optional: P complex poles (re, im interleaved); NULL -> computed */
+  const double *beta;   /* optional: P complex weights, used as given (no renormalisation) */
+  int32_t npoles;       /* P when alpha/beta are given */
+} rexi_params;
+
+/* Fill *p with the defaults above (ntrunc = 63, nlat = 96, nlon = 192, M = 128,
+ * tau = 3600).  Host only. */
+void rexi_params_default(rexi_params *p);
+
+/* T-REXI coefficients on the host, no GPU needed (Sec. 4.1; Sec. 6.1 for the
+ * renormalisation).  alpha_n = h (mu + i n), n = -(M+11)..(M+11) ascending,
+ * beta_n = h sum_{l+m=n} Re(b_m) a_l with the refitted Gaussian rational
+ * approximation (mu, a_l) and b_m = e^{h^2} e^{-i m h}.  alpha and beta must
+ * hold 2P doubles each (P = 2(M+11)+1, re/im interleaved); *P receives P and
+ * *eps the x = 0 residual 1 - sum beta/alpha before renormalisation (may be
+ * NULL).  Returns REXI_EINVAL for M < 1 or h <= 0. */
+rexi_status rexi_coefficients(int32_t M, double h, int32_t normalize,
+                              double *alpha, double *beta, int32_t *P, double *eps);
+
+/* Create a plan on the current CUDA device: Gaussian grid, Legendre tables,
+ * REXI poles, the per-(pole, m, n) factors of the banded solves for the step
+ * and its adjoint, and workspaces for max_batch states.  Allocates device
+ * memory; synchronises the device once.  *out is NULL on failure. */
+rexi_status rexi_plan_create(const rexi_params *params, rexi_plan **out);
+
+/* One T-REXI step (Algorithm 1): out = Re sum_k beta_k (alpha_k + tau L)^{-1} in,
+ * with the spherical-harmonic transforms of Sec. 3 around it in the grid layout.
+ * in_dev/out_dev: [batch][3][nspec] complex128 (REXI_SPECTRAL) or
+ * [batch][3][nlat][nlon] float64 (REXI_GRID).  1 <= batch <= max_batch. */
+rexi_status rexi_step(rexi_plan *plan, const void *in_dev, void *out_dev,
+                      int32_t batch, void *stream);
+
+/* Transpose of rexi_step for the Euclidean inner products (sum x y on the grid,
+ * Re sum conj(x) y on coefficients): sum_k conj(beta_k) (conj(alpha_k) + tau L^H)^{-1}
+ * framed by the transposed transforms.  Gives dJ/dU0 from dJ/dU1 (no paper
+ * counterpart; the adjoint of the paper's operator).  Same layouts as rexi_step. */
+rexi_status rexi_step_adjoint(rexi_plan *plan, const void *gout_dev, void *gin_dev,
+                              int32_t batch, void *stream);
+
+/* Spectral <-> grid transforms of the plan's grid (Sec. 3): analysis maps
+ * grid (h', u, v) to spectral (Phi, zeta, delta); synthesis the reverse. */
+rexi_status rexi_analyze(rexi_plan *plan, const void *grid_dev, void *spec_dev,
+                         int32_t batch, void *stream);
+rexi_status rexi_synthesize(rexi_plan *plan, const void *spec_dev, void *grid_dev,
+                            int32_t batch, void *stream);
+
+/* One shifted system (alpha_k + tau L) X = U for pole index k (0 <= k < P, the
+ * ascending order of rexi_get_coefficients), spectral layout, no beta weight.
+ * For tests of a single (pole, m) family of banded solves (Sec. 5). */
+rexi_status rexi_solve_pole(rexi_plan *plan, int32_t k, const void *in_dev, void *out_dev,
+                            int32_t batch, void *stream);
+
+/* Copy the plan's poles to host arrays of 2P doubles each; *P receives P. */
+rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *beta, int32_t *P);
+
+/* Host-side description of a plan: writes up to 8 int64 values
+ * {N, nspec, P, nlat, nlon, max_batch, pole_slots, device bytes held}. */
+rexi_status rexi_plan_info(const rexi_plan *plan, int64_t *info, int32_t n);
+
+/* Optional per-stage timing: with max_calls > 0 the next max_calls calls of
+ * rexi_step / rexi_step_adjoint record CUDA events on their stream around each
+ * stage (0 FFT forward, 1 Legendre analysis, 2 banded solve + pole sum,
+ * 3 slot reduction, 4 Legendre synthesis, 5 FFT inverse, 6/7 layout
+ * transposes).  max_calls = 0 turns it off.  rexi_profile_read waits for the
+ * recorded events, writes the summed milliseconds per stage to stage_ms[0..n)
+ * and the number of timed calls to *calls, and restarts the count. */
+rexi_status rexi_profile_enable(rexi_plan *plan, int32_t max_calls);
+rexi_status rexi_profile_read(rexi_plan *plan, double *stage_ms, int32_t n, int32_t *calls);
+
+/* Free everything the plan holds; NULL-safe.  The caller synchronises streams
+ * that still use the plan first. */
+void rexi_destroy(rexi_plan *plan);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *rexi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REXI_H */

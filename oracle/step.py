@@ -67,12 +67,14 @@ def _check_band(A):
     return n
 
 
-def rexi_step_spectral(U, N, alpha, beta, tau, c=Consts(), adjoint=False, ms=None):
+def rexi_step_spectral(U, N, alpha, beta, tau, c=Consts(), adjoint=False, ms=None, real_m0=True):
     """Apply sum_n beta_n (alpha_n + tau L)^{-1} to spectral states.
 
     U: [..., 3, nspec] complex (Phi, zeta, delta).  With ``adjoint`` the
     transposed map sum_n conj(beta_n) (conj(alpha_n) + tau L^H)^{-1} is applied.
     ``ms`` restricts the work to a subset of zonal orders (other m left zero).
+    ``real_m0=False`` keeps the m = 0 result complex (a single pole is not a
+    conjugate-symmetric set, so its m = 0 response is complex).
     """
     U = np.asarray(U, dtype=np.complex128)
     out = np.zeros_like(U)
@@ -94,7 +96,7 @@ def rexi_step_spectral(U, N, alpha, beta, tau, c=Consts(), adjoint=False, ms=Non
             ab[_BW, :] += a_n
             acc += b_n * solve_banded((_BW, _BW), ab, rhs)
         res = (acc * mask[:, None]).T.reshape(lead + (-1,))
-        if m == 0:
+        if m == 0 and real_m0:
             res = res.real.astype(np.complex128)
         deinterleave(res, out, m, N)
     return out

@@ -1,0 +1,244 @@
+// Longitude transforms (paper Sec. 3): for every latitude row of every field,
+//   forward  F_m = s_m sum_i x_i e^{-i m lambda_i},   m = 0..N,
+//   inverse  x_i = sum_{m=-N}^{N} X_m e^{i m lambda_i},  X_{-m} = conj(X_m),  X_m = s_m F_m,
+// with per-(field, latitude) input/output scales that carry Robert's cos(lat)
+// factor, g, the Gaussian weights and the transposes' scalings.
+//
+// Two real rows are packed as one complex sequence z = x1 + i x2 and
+// transformed by a mixed-radix (2, 3, 4, 5) Stockham autosort FFT in shared
+// memory; X1 and X2 are separated from Z_m and conj(Z_{n-m}).  The inverse is
+// conj(FFT(conj(Z))) on the Hermitian-extended spectrum.
+//
+// Layouts: grid [B][3][nlat][nlon] float64; Fourier [nlat][N+1][3B] complex,
+// column c = 3 b + field, so that for each latitude the Legendre kernels read
+// contiguous columns.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "rexi_internal.h"
+
+namespace rexi {
+
+namespace {
+
+struct FftArgs {
+  const double2 *tw;  // n twiddles e^{-2 pi i k / n}
+  int n, nstages, N, nlat, ncol, np;  // np: complex rows (column pairs) per CTA
+  int radix[24];
+  double c3, s3, c5a, s5a, c5b, s5b;  // cos/sin of 2pi/3, 2pi/5, 4pi/5
+};
+
+__device__ __forceinline__ double2 cmulz(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 addz(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 subz(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// -i * a
+__device__ __forceinline__ double2 mulmi(double2 a) { return make_double2(a.y, -a.x); }
+
+__device__ __forceinline__ void dft_small(double2 *v, int R, const FftArgs &a) {
+  if (R == 2) {
+    double2 t = v[0];
+    v[0] = addz(t, v[1]);
+    v[1] = subz(t, v[1]);
+  } else if (R == 4) {
+    double2 t0 = addz(v[0], v[2]), t1 = subz(v[0], v[2]);
+    double2 t2 = addz(v[1], v[3]), t3 = mulmi(subz(v[1], v[3]));
+    v[0] = addz(t0, t2);
+    v[2] = subz(t0, t2);
+    v[1] = addz(t1, t3);
+    v[3] = subz(t1, t3);
+  } else if (R == 3) {
+    double2 s = addz(v[1], v[2]);
+    double2 d = subz(v[1], v[2]);
+    double2 y0 = addz(v[0], s);
+    double2 t = make_double2(v[0].x + a.c3 * s.x, v[0].y + a.c3 * s.y);
+    double2 u = mulmi(make_double2(a.s3 * d.x, a.s3 * d.y));
+    v[0] = y0;
+    v[1] = addz(t, u);
+    v[2] = subz(t, u);
+  } else {  // R == 5
+    double2 b1 = addz(v[1], v[4]), b2 = addz(v[2], v[3]);
+    double2 d1 = subz(v[1], v[4]), d2 = subz(v[2], v[3]);
+    double2 y0 = addz(v[0], addz(b1, b2));
+    double2 t1 = make_double2(v[0].x + a.c5a * b1.x + a.c5b * b2.x, v[0].y + a.c5a * b1.y + a.c5b * b2.y);
+    double2 t2 = make_double2(v[0].x + a.c5b * b1.x + a.c5a * b2.x, v[0].y + a.c5b * b1.y + a.c5a * b2.y);
+    double2 u1 = mulmi(make_double2(a.s5a * d1.x + a.s5b * d2.x, a.s5a * d1.y + a.s5b * d2.y));
+    double2 u2 = mulmi(make_double2(a.s5b * d1.x - a.s5a * d2.x, a.s5b * d1.y - a.s5a * d2.y));
+    v[0] = y0;
+    v[1] = addz(t1, u1);
+    v[4] = subz(t1, u1);
+    v[2] = addz(t2, u2);
+    v[3] = subz(t2, u2);
+  }
+}
+
+// In-shared-memory forward FFT of np rows of length n; returns the buffer
+// holding the result (buf0 or buf1).
+__device__ double2 *fft_smem(double2 *buf0, double2 *buf1, const FftArgs &a) {
+  const int n = a.n;
+  double2 *src = buf0, *dst = buf1;
+  int Ns = 1;
+  for (int s = 0; s < a.nstages; ++s) {
+    const int R = a.radix[s];
+    const int nb = n / R;
+    const int stride = n / (Ns * R);
+    for (int t = threadIdx.x; t < a.np * nb; t += blockDim.x) {
+      const int q = t / nb, jb = t - q * nb;
+      const double2 *in = src + q * n;
+      double2 *out = dst + q * n;
+      double2 v[5];
+      const int jm = jb % Ns;
+      for (int r = 0; r < R; ++r) {
+        double2 x = in[jb + r * nb];
+        if (r > 0 && jm > 0) x = cmulz(x, __ldg(a.tw + r * jm * stride));
+        v[r] = x;
+      }
+      dft_small(v, R, a);
+      const int od = (jb / Ns) * Ns * R + jm;
+      for (int r = 0; r < R; ++r) out[od + r * Ns] = v[r];
+    }
+    __syncthreads();
+    double2 *tmp = src;
+    src = dst;
+    dst = tmp;
+    Ns *= R;
+  }
+  return src;
+}
+
+__global__ void fft_fwd_kernel(FftArgs a, const double *grid, double2 *four, const double *in_scale,
+                               const double *m_scale) {
+  extern __shared__ double2 sm[];
+  const int n = a.n;
+  double2 *buf0 = sm, *buf1 = sm + a.np * n;
+  const int j = blockIdx.y;
+  const int pair0 = blockIdx.x * a.np;
+  for (int t = threadIdx.x; t < a.np * n; t += blockDim.x) {
+    const int q = t / n, i = t - q * n;
+    const int c1 = 2 * (pair0 + q), c2 = c1 + 1;
+    double x1 = 0.0, x2 = 0.0;
+    if (c1 < a.ncol) x1 = grid[((int64_t)c1 * a.nlat + j) * n + i] * in_scale[(c1 % 3) * a.nlat + j];
+    if (c2 < a.ncol) x2 = grid[((int64_t)c2 * a.nlat + j) * n + i] * in_scale[(c2 % 3) * a.nlat + j];
+    buf0[t] = make_double2(x1, x2);
+  }
+  __syncthreads();
+  const double2 *Z = fft_smem(buf0, buf1, a);
+  const int M1 = a.N + 1;
+  for (int t = threadIdx.x; t < a.np * M1; t += blockDim.x) {
+    const int m = t / a.np, q = t - m * a.np;
+    const int c1 = 2 * (pair0 + q), c2 = c1 + 1;
+    const double2 zm = Z[q * n + m];
+    const double2 zn = Z[q * n + (m == 0 ? 0 : n - m)];
+    const double s = m_scale[m];
+    // X1 = (Z_m + conj Z_{n-m}) / 2,  X2 = (Z_m - conj Z_{n-m}) / (2 i)
+    const double2 x1 = make_double2(0.5 * s * (zm.x + zn.x), 0.5 * s * (zm.y - zn.y));
+    const double2 x2 = make_double2(0.5 * s * (zm.y + zn.y), -0.5 * s * (zm.x - zn.x));
+    double2 *o = four + ((int64_t)j * M1 + m) * a.ncol;
+    if (c1 < a.ncol) o[c1] = x1;
+    if (c2 < a.ncol) o[c2] = x2;
+  }
+}
+
+__global__ void fft_inv_kernel(FftArgs a, const double2 *four, double *grid, const double *m_scale,
+                               const double *out_scale) {
+  extern __shared__ double2 sm[];
+  const int n = a.n;
+  double2 *buf0 = sm, *buf1 = sm + a.np * n;
+  const int j = blockIdx.y;
+  const int pair0 = blockIdx.x * a.np;
+  const int M1 = a.N + 1;
+  for (int t = threadIdx.x; t < a.np * n; t += blockDim.x) buf0[t] = make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int t = threadIdx.x; t < a.np * M1; t += blockDim.x) {
+    const int m = t / a.np, q = t - m * a.np;
+    const int c1 = 2 * (pair0 + q), c2 = c1 + 1;
+    const double2 *in = four + ((int64_t)j * M1 + m) * a.ncol;
+    const double s = m_scale[m];
+    double2 x1 = c1 < a.ncol ? in[c1] : make_double2(0, 0);
+    double2 x2 = c2 < a.ncol ? in[c2] : make_double2(0, 0);
+    x1 = make_double2(s * x1.x, s * x1.y);
+    x2 = make_double2(s * x2.x, s * x2.y);
+    if (m == 0) {
+      x1.y = 0.0;
+      x2.y = 0.0;
+    }
+    // Z_m = X1 + i X2 and Z_{n-m} = conj(X1) + i conj(X2); store conj(Z) for the inverse
+    buf0[q * n + m] = make_double2(x1.x - x2.y, -(x1.y + x2.x));
+    if (m > 0) buf0[q * n + n - m] = make_double2(x1.x + x2.y, -(x2.x - x1.y));
+  }
+  __syncthreads();
+  const double2 *z = fft_smem(buf0, buf1, a);
+  for (int t = threadIdx.x; t < a.np * n; t += blockDim.x) {
+    const int q = t / n, i = t - q * n;
+    const int c1 = 2 * (pair0 + q), c2 = c1 + 1;
+    const double2 r = z[t];  // conj of the inverse transform: x1 = r.x, x2 = -r.y
+    if (c1 < a.ncol) grid[((int64_t)c1 * a.nlat + j) * n + i] = r.x * out_scale[(c1 % 3) * a.nlat + j];
+    if (c2 < a.ncol) grid[((int64_t)c2 * a.nlat + j) * n + i] = -r.y * out_scale[(c2 % 3) * a.nlat + j];
+  }
+}
+
+FftArgs make_args(const Plan &pl, int B) {
+  FftArgs a;
+  a.tw = static_cast<const double2 *>(pl.fft.tw_dev);
+  a.n = pl.fft.n;
+  a.nstages = pl.fft.nstages;
+  for (int s = 0; s < 24; ++s) a.radix[s] = pl.fft.radix[s];
+  a.N = pl.N;
+  a.nlat = pl.nlat;
+  a.ncol = 3 * B;
+  a.np = pl.fft.nsplit;
+  a.c3 = std::cos(2.0 * M_PI / 3.0);
+  a.s3 = std::sin(2.0 * M_PI / 3.0);
+  a.c5a = std::cos(2.0 * M_PI / 5.0);
+  a.s5a = std::sin(2.0 * M_PI / 5.0);
+  a.c5b = std::cos(4.0 * M_PI / 5.0);
+  a.s5b = std::sin(4.0 * M_PI / 5.0);
+  return a;
+}
+
+}  // namespace
+
+// Factor n into radices 4, 2, 3, 5 (4s first); false if another prime divides n.
+bool fft_factor(int n, int *radix, int *nstages) {
+  int k = 0, m = n;
+  while (m % 4 == 0) { radix[k++] = 4; m /= 4; }
+  while (m % 2 == 0) { radix[k++] = 2; m /= 2; }
+  while (m % 3 == 0) { radix[k++] = 3; m /= 3; }
+  while (m % 5 == 0) { radix[k++] = 5; m /= 5; }
+  *nstages = k;
+  return m == 1 && k < 24;
+}
+
+size_t fft_smem_bytes(const Plan &pl) { return (size_t)2 * pl.fft.nsplit * pl.fft.n * sizeof(double2); }
+
+cudaError_t launch_fft_fwd(Plan &pl, const double *grid, double2 *four, int B, const double *in_scale,
+                           const double *m_scale, cudaStream_t st) {
+  FftArgs a = make_args(pl, B);
+  const int npairs = (a.ncol + 1) / 2;
+  dim3 g((unsigned)((npairs + a.np - 1) / a.np), (unsigned)pl.nlat);
+  size_t sm = fft_smem_bytes(pl);
+  fft_fwd_kernel<<<g, 256, sm, st>>>(a, grid, four, in_scale, m_scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_inv(Plan &pl, const double2 *four, double *grid, int B, const double *m_scale,
+                           const double *out_scale, cudaStream_t st) {
+  FftArgs a = make_args(pl, B);
+  const int npairs = (a.ncol + 1) / 2;
+  dim3 g((unsigned)((npairs + a.np - 1) / a.np), (unsigned)pl.nlat);
+  size_t sm = fft_smem_bytes(pl);
+  fft_inv_kernel<<<g, 256, sm, st>>>(a, four, grid, m_scale, out_scale);
+  return cudaGetLastError();
+}
+
+cudaError_t fft_configure(Plan &pl) {
+  cudaError_t e = cudaFuncSetAttribute(fft_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fft_smem_bytes(pl));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fft_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fft_smem_bytes(pl));
+}
+
+}  // namespace rexi

@@ -1,0 +1,350 @@
+// Plan creation for librexi: Gaussian grid and Legendre tables (Sec. 3), REXI
+// poles (Sec. 4.1), the per-(pole, m, n) factors of the banded solves (Sec. 5)
+// for the step and its adjoint, solve work lists and workspaces.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "rexi_internal.h"
+
+namespace rexi {
+
+bool fft_factor(int n, int *radix, int *nstages);
+cudaError_t fft_configure(Plan &pl);
+cudaError_t legendre_configure();
+
+namespace {
+
+template <typename T>
+cudaError_t upload(T **dev, const std::vector<T> &host, size_t *bytes) {
+  cudaError_t e = cudaMalloc(dev, std::max<size_t>(1, host.size()) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  *bytes += host.size() * sizeof(T);
+  if (host.empty()) return cudaSuccess;
+  return cudaMemcpy(*dev, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+cudaError_t dalloc(T **dev, size_t count, size_t *bytes) {
+  cudaError_t e = cudaMalloc(dev, std::max<size_t>(1, count) * sizeof(T));
+  if (e == cudaSuccess) *bytes += count * sizeof(T);
+  return e;
+}
+
+double eps_nm(int n, int m) {
+  if (n <= m) return 0.0;
+  return std::sqrt(((double)n * n - (double)m * m) / (4.0 * n * n - 1.0));
+}
+
+// Orthonormal Pbar_n^m and H_n^m = (1-mu^2) dPbar/dmu for n = m..N at one mu,
+// by the standard m-diagonal seed and the three-term recurrence in n.
+void alp_column(int m, int N, double mu, double *P, double *H) {
+  const double s = std::sqrt(1.0 - mu * mu);
+  double pmm = 1.0 / std::sqrt(2.0);
+  for (int k = 1; k <= m; ++k) pmm *= std::sqrt((2.0 * k + 1.0) / (2.0 * k)) * s;
+  const int K = N - m + 2;  // one extra degree for H_N
+  std::vector<double> p(K);
+  p[0] = pmm;
+  if (K > 1) p[1] = std::sqrt(2.0 * m + 3.0) * mu * pmm;
+  for (int i = 2; i < K; ++i) {
+    const int n = m + i;
+    p[i] = (mu * p[i - 1] - eps_nm(n - 1, m) * p[i - 2]) / eps_nm(n, m);
+  }
+  for (int i = 0; i <= N - m; ++i) {
+    const int n = m + i;
+    P[i] = p[i];
+    double h = -n * eps_nm(n + 1, m) * p[i + 1];
+    if (i > 0) h += (n + 1) * eps_nm(n, m) * p[i - 1];
+    H[i] = h;
+  }
+}
+
+}  // namespace
+
+void free_plan(Plan *pl);
+
+rexi_status build_plan(const rexi_params &prm, Plan *pl) {
+  pl->prm = prm;
+  const int N = prm.ntrunc;
+  pl->N = N;
+  pl->nlat = prm.nlat;
+  pl->nlon = prm.nlon;
+  pl->J = prm.nlat / 2;
+  pl->nspec = nspec_of(N);
+  size_t &bytes = pl->bytes;
+  cudaError_t e;
+  auto fail = [&](const char *what, cudaError_t err) {
+    set_error(std::string("plan: ") + what + ": " + cudaGetErrorString(err));
+    return err == cudaErrorMemoryAllocation ? REXI_ENOMEM : REXI_ECUDA;
+  };
+  cudaGetDevice(&pl->device);
+  cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
+
+  // ---- poles
+  if (prm.alpha && prm.beta) {
+    pl->P = prm.npoles;
+    pl->alpha.resize(pl->P);
+    pl->beta.resize(pl->P);
+    for (int k = 0; k < pl->P; ++k) {
+      pl->alpha[k] = cplx(prm.alpha[2 * k], prm.alpha[2 * k + 1]);
+      pl->beta[k] = cplx(prm.beta[2 * k], prm.beta[2 * k + 1]);
+    }
+  } else {
+    rexi_coeffs_host(prm.M, prm.h, prm.normalize != 0, pl->alpha, pl->beta, &pl->eps0);
+    pl->P = (int)pl->alpha.size();
+  }
+  const int P = pl->P;
+  const double tau = prm.tau, a = prm.radius, om = prm.omega;
+  const double phibar = prm.gravity * prm.mean_depth;
+  if (prm.strict_range) {
+    const double wmax = std::sqrt(4.0 * om * om + phibar * N * (N + 1.0) / (a * a));
+    if (tau * wmax > prm.h * (prm.M - 10)) {
+      set_error("plan: tau * max|omega| exceeds h (M - 10)");
+      return REXI_ERANGE;
+    }
+  }
+  std::vector<double2> al(P), be(P);
+  for (int k = 0; k < P; ++k) {
+    al[k] = make_double2(pl->alpha[k].real(), pl->alpha[k].imag());
+    be[k] = make_double2(pl->beta[k].real(), pl->beta[k].imag());
+  }
+  if ((e = upload(&pl->alpha_dev, al, &bytes))) return fail("alpha", e);
+  if ((e = upload(&pl->beta_dev, be, &bytes))) return fail("beta", e);
+
+  // ---- systems (m, parity) and rows
+  pl->sys.resize(2 * (N + 1));
+  int64_t row = 0;
+  int lmax = 0;
+  for (int m = 0; m <= N; ++m)
+    for (int p = 0; p < 2; ++p) {
+      const int nmin = std::max(m, 1);
+      int n0 = m + p;
+      while (n0 < nmin) n0 += 2;
+      const int len = n0 <= N ? (N - n0) / 2 + 1 : 0;
+      pl->sys[2 * m + p] = SysInfo{m, p, n0, len, row};
+      row += len;
+      lmax = std::max(lmax, len);
+    }
+  pl->nrows = row;
+  pl->lmax = std::max(lmax, 1);
+  std::vector<int4> sysv;
+  for (const SysInfo &s : pl->sys) sysv.push_back(make_int4(s.m, s.n0, s.len, (int)s.row0));
+  if ((e = upload(&pl->sys_dev, sysv, &bytes))) return fail("systems", e);
+
+  // ---- per-coefficient data: sigma, ct, dt, G; zonal order; reduce flags; zeta weights
+  const int64_t NS = pl->nspec;
+  std::vector<double> coef(4 * NS, 0.0);
+  std::vector<int32_t> m_of(NS);
+  std::vector<uint8_t> rflags(3 * NS, 0);
+  std::vector<double2> wf(NS, make_double2(0, 0)), wa(NS, make_double2(0, 0));
+  std::vector<double> zd_syn(NS), zd_ana_adj(NS), zd_one(NS, 1.0), zd_mone(NS, -1.0);
+  for (int m = 0; m <= N; ++m) {
+    const int nmin = std::max(m, 1);
+    for (int n = m; n <= N; ++n) {
+      const int64_t ix = spec_idx(N, m, n);
+      m_of[ix] = m;
+      double sig = 0, ct = 0, dt = 0;
+      if (n > 0) {
+        sig = 2.0 * om * m / (n * (n + 1.0));
+        if (n - 1 >= nmin) ct = eps_nm(n, m) * (n + 1.0) / n;
+        if (n + 1 <= N) dt = eps_nm(n + 1, m) * n / (n + 1.0);
+      }
+      coef[4 * ix + 0] = sig;
+      coef[4 * ix + 1] = ct;
+      coef[4 * ix + 2] = dt;
+      coef[4 * ix + 3] = n * (n + 1.0) / (a * a);
+      zd_syn[ix] = n > 0 ? -a / (n * (n + 1.0)) : 0.0;
+      zd_ana_adj[ix] = n > 0 ? a / (n * (n + 1.0)) : 0.0;
+      // reduce flags: Phi/delta rows have partials iff n >= nmin; zeta rows iff a
+      // delta row of the other parity sits at n - 1 or n + 1
+      const bool staterow = n >= nmin;
+      rflags[0 * NS + ix] = staterow ? 1 : 0;
+      rflags[2 * NS + ix] = staterow ? 1 : 2;
+      bool zp = staterow && ((n - 1 >= nmin) || (n + 1 <= N));
+      rflags[1 * NS + ix] = staterow ? (zp ? 1 : 0) : 2;
+      if (staterow) {
+        cplx sf(0, 0), sa(0, 0);
+        for (int k = 0; k < P; ++k) {
+          sf += pl->beta[k] / (pl->alpha[k] + cplx(0, tau * sig));
+          sa += std::conj(pl->beta[k]) / (std::conj(pl->alpha[k]) - cplx(0, tau * sig));
+        }
+        wf[ix] = make_double2(sf.real(), sf.imag());
+        wa[ix] = make_double2(sa.real(), sa.imag());
+      }
+    }
+  }
+  cplx sphf(0, 0), spha(0, 0);
+  for (int k = 0; k < P; ++k) {
+    sphf += pl->beta[k] / pl->alpha[k];
+    spha += std::conj(pl->beta[k]) / std::conj(pl->alpha[k]);
+  }
+  pl->sphi_fwd = make_double2(sphf.real(), sphf.imag());
+  pl->sphi_adj = make_double2(spha.real(), spha.imag());
+  if ((e = upload(&pl->coef_dev, coef, &bytes))) return fail("coef", e);
+  if ((e = upload(&pl->m_of_dev, m_of, &bytes))) return fail("m_of", e);
+  if ((e = upload(&pl->rflags_dev, rflags, &bytes))) return fail("rflags", e);
+  if ((e = upload(&pl->w_fwd, wf, &bytes))) return fail("w", e);
+  if ((e = upload(&pl->w_adj, wa, &bytes))) return fail("w", e);
+  if ((e = upload(&pl->zd_syn, zd_syn, &bytes))) return fail("zd", e);
+  if ((e = upload(&pl->zd_ana_adj, zd_ana_adj, &bytes))) return fail("zd", e);
+  if ((e = upload(&pl->zd_one, zd_one, &bytes))) return fail("zd", e);
+  if ((e = upload(&pl->zd_mone, zd_mone, &bytes))) return fail("zd", e);
+
+  // ---- solve factors (forward now; adjoint on first use)
+  const size_t nfac = (size_t)F_NCOMP * pl->nrows * P;
+  if ((e = dalloc(&pl->fac_fwd, nfac, &bytes))) return fail("factors", e);
+  if ((e = launch_factor_setup(*pl, false, 0))) return fail("factor setup", e);
+
+  // ---- grid, Legendre tables, FFT
+  {  // tables serve the grid layout and rexi_analyze / rexi_synthesize
+    std::vector<double> mu, w;
+    gauss_legendre_host(pl->nlat, mu, w);
+    if ((e = upload(&pl->mu_dev, mu, &bytes))) return fail("mu", e);
+    const int J = pl->J, nlat = pl->nlat;
+    std::vector<double> tP((size_t)NS * J), tH((size_t)NS * J);
+    std::vector<double> colP(N + 1), colH(N + 1);
+    for (int m = 0; m <= N; ++m)
+      for (int j = 0; j < J; ++j) {
+        alp_column(m, N, mu[j], colP.data(), colH.data());
+        for (int n = m; n <= N; ++n) {
+          tP[(size_t)spec_idx(N, m, n) * J + j] = colP[n - m];
+          tH[(size_t)spec_idx(N, m, n) * J + j] = colH[n - m];
+        }
+      }
+    if ((e = upload(&pl->tabP, tP, &bytes))) return fail("tables", e);
+    if ((e = upload(&pl->tabH, tH, &bytes))) return fail("tables", e);
+    std::vector<double> sin_(3 * nlat), sout(3 * nlat);
+    for (int j = 0; j < nlat; ++j) {
+      const double cl = std::sqrt(1.0 - mu[j] * mu[j]);
+      sin_[0 * nlat + j] = prm.gravity * w[j];
+      sin_[1 * nlat + j] = cl * w[j] / (a * (1.0 - mu[j] * mu[j]));
+      sin_[2 * nlat + j] = sin_[1 * nlat + j];
+      sout[0 * nlat + j] = 1.0 / prm.gravity;
+      sout[1 * nlat + j] = 1.0 / cl;
+      sout[2 * nlat + j] = 1.0 / cl;
+    }
+    if ((e = upload(&pl->scale_ana_in, sin_, &bytes))) return fail("scales", e);
+    if ((e = upload(&pl->scale_syn_out, sout, &bytes))) return fail("scales", e);
+    std::vector<double> mf(N + 1), mc(N + 1), ma(N + 1), m1(N + 1, 1.0);
+    for (int m = 0; m <= N; ++m) {
+      mf[m] = 1.0 / pl->nlon;
+      mc[m] = m == 0 ? 1.0 : 2.0;
+      ma[m] = m == 0 ? 1.0 / pl->nlon : 0.5 / pl->nlon;
+    }
+    if ((e = upload(&pl->mscale_fwd, mf, &bytes))) return fail("mscale", e);
+    if ((e = upload(&pl->mscale_c, mc, &bytes))) return fail("mscale", e);
+    if ((e = upload(&pl->mscale_adj, ma, &bytes))) return fail("mscale", e);
+    if ((e = upload(&pl->mscale_one, m1, &bytes))) return fail("mscale", e);
+    FftPlan &f = pl->fft;
+    f.n = pl->nlon;
+    fft_factor(f.n, f.radix, &f.nstages);
+    f.nsplit = std::max(1, 2048 / f.n);
+    std::vector<double2> tw(f.n);
+    for (int k = 0; k < f.n; ++k) {
+      const double th = 2.0 * M_PI * k / f.n;
+      tw[k] = make_double2(std::cos(th), -std::sin(th));
+    }
+    double2 *twd = nullptr;
+    if ((e = upload(&twd, tw, &bytes))) return fail("twiddles", e);
+    f.tw_dev = twd;
+    if ((e = fft_configure(*pl))) return fail("fft configure", e);
+    if ((e = legendre_configure())) return fail("legendre configure", e);
+  }
+
+  // ---- workspaces
+  const int B = prm.max_batch;
+  if ((e = dalloc(&pl->four, (size_t)pl->nlat * (N + 1) * 3 * B, &bytes))) return fail("fourier", e);
+  if ((e = dalloc(&pl->s_in, (size_t)3 * NS * B, &bytes))) return fail("spectral", e);
+  if ((e = dalloc(&pl->s_out, (size_t)3 * NS * B, &bytes))) return fail("spectral", e);
+  // partial sums: at most 64 slots and ~2 GiB
+  size_t per_slot = (size_t)3 * NS * B * sizeof(double2);
+  int cap = (int)std::min<size_t>(64, std::max<size_t>(1, (size_t)(2ull << 30) / per_slot));
+  cap = std::min(cap, P);
+  pl->partial_cap = (size_t)cap;
+  if ((e = dalloc(&pl->partial, (size_t)cap * 3 * NS * B, &bytes))) return fail("partials", e);
+  pl->resident_warps = pl->num_sms * 16;
+  if ((e = dalloc(&pl->yscratch, (size_t)pl->resident_warps * pl->lmax * 32, &bytes))) return fail("scratch", e);
+  if ((e = dalloc(&pl->counter, 1, &bytes))) return fail("counter", e);
+  pl->slots_override = prm.pole_slots;
+  if ((e = cudaDeviceSynchronize())) return fail("setup", e);
+  return REXI_OK;
+}
+
+// Work list for batch B: items (m, slot group, first state), longest first.
+rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out) {
+  const int key = single ? -B : B;
+  auto it = pl.layouts.find(key);
+  if (it != pl.layouts.end()) {
+    *out = &it->second;
+    return REXI_OK;
+  }
+  SolveLayout L;
+  L.batch = B;
+  int bw = 1;
+  while (bw < B && bw < 16) bw *= 2;
+  L.bw = bw;
+  int slots_cap = (int)pl.partial_cap;
+  // lanes kk >= L.kk stay idle, so slots = groups * kk never exceeds the partial buffer
+  L.kk = single ? 1 : std::min(32 / (2 * bw), slots_cap);
+  if (single) {
+    L.groups = 1;
+  } else if (pl.slots_override > 0) {
+    L.groups = std::max(1, std::min(pl.slots_override, slots_cap) / L.kk);
+  } else {
+    // enough items that the longest fits ~1/2 of a warp's fair share of the work
+    const int nb = (B + bw - 1) / bw;
+    double total = 0;
+    int lmax = 0;
+    for (int m = 0; m <= pl.N; ++m) {
+      int l = std::max(pl.sys[2 * m].len, pl.sys[2 * m + 1].len);
+      total += (double)l * pl.P * nb;
+      lmax = std::max(lmax, l);
+    }
+    total /= L.kk;  // work per warp-lane set
+    double share = total / (2.0 * pl.resident_warps);
+    int g = 1;
+    while (g * L.kk < slots_cap && (double)lmax * pl.P / (g * L.kk) > share) g *= 2;
+    L.groups = std::max(1, std::min(g, slots_cap / L.kk));
+  }
+  L.slots = L.groups * L.kk;
+  std::vector<WorkItem> items;
+  const int nb = (B + bw - 1) / bw;
+  for (int m = 0; m <= pl.N; ++m) {
+    const int l = std::max(pl.sys[2 * m].len, pl.sys[2 * m + 1].len);
+    if (l == 0) continue;
+    for (int g = 0; g < L.groups; ++g)
+      for (int bb = 0; bb < nb; ++bb) items.push_back(WorkItem{m, g, bb * bw, l});
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const WorkItem &x, const WorkItem &y) { return x.len > y.len; });
+  L.nitems = (int)items.size();
+  cudaError_t e = cudaMalloc(&L.items_dev, std::max<size_t>(1, items.size()) * sizeof(WorkItem));
+  if (e != cudaSuccess) {
+    set_error(std::string("work list: ") + cudaGetErrorString(e));
+    return REXI_ENOMEM;
+  }
+  cudaMemcpy(L.items_dev, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+  auto res = pl.layouts.emplace(key, L);
+  *out = &res.first->second;
+  return REXI_OK;
+}
+
+void free_plan(Plan *pl) {
+  if (!pl) return;
+  void *ptrs[] = {pl->coef_dev, pl->sys_dev, pl->m_of_dev, pl->fac_fwd, pl->fac_adj, pl->alpha_dev,
+                  pl->beta_dev, pl->w_fwd, pl->w_adj, pl->rflags_dev, pl->mu_dev, pl->tabP, pl->tabH,
+                  pl->tabP_hi, pl->tabP_lo, pl->tabH_hi, pl->tabH_lo, pl->scale_ana_in,
+                  pl->scale_syn_out, pl->mscale_fwd, pl->mscale_c, pl->mscale_adj, pl->mscale_one,
+                  pl->zd_syn, pl->zd_ana_adj, pl->zd_one, pl->zd_mone, pl->fft.tw_dev, pl->four,
+                  pl->s_in, pl->s_out, pl->partial, pl->yscratch, pl->counter};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (auto &kv : pl->layouts)
+    if (kv.second.items_dev) cudaFree(kv.second.items_dev);
+  delete pl;
+}
+
+}  // namespace rexi

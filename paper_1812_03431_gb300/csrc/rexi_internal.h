@@ -1,0 +1,157 @@
+// Internal declarations of librexi (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/rexi.h"
+
+namespace rexi {
+
+using cplx = std::complex<double>;
+
+constexpr int kGaussTerms = 11;  // K of the Gaussian rational approximation (Sec. 4.1)
+
+// ---- host math (coeffs.cpp) -------------------------------------------------
+// Refitted Gaussian rational approximation psi(y) ~ Re sum_l a_l/(i y + mu + i l).
+struct GaussFit {
+  double mu;
+  cplx a[2 * kGaussTerms + 1];  // l = -K..K
+  double sup_err;
+};
+const GaussFit &gauss_fit();
+void rexi_coeffs_host(int M, double h, bool normalize, std::vector<cplx> &alpha,
+                      std::vector<cplx> &beta, double *eps);
+void gauss_legendre_host(int nlat, std::vector<double> &mu, std::vector<double> &w);
+
+// ---- spectral indexing ---------------------------------------------------------
+inline int64_t spec_idx(int N, int m, int n) { return (int64_t)m * (2 * N + 3 - m) / 2 + (n - m); }
+inline int64_t nspec_of(int N) { return (int64_t)(N + 1) * (N + 2) / 2; }
+
+// One row of a banded system: zonal order m, parity p (of n - m), position i.
+// Rows of a (m, p) system are n = n0(m, p) + 2 i, i = 0..len-1; zeta_0^0 and
+// delta_0^0 are excluded (so m = 0 starts at n = 2 / n = 1).
+struct SysInfo {
+  int m, p, n0, len;
+  int64_t row0;  // first global row id
+};
+
+// Solve-kernel work item: (m, pole-slot group, first state) for one warp.
+struct WorkItem {
+  int32_t m, g, b0, len;
+};
+
+// Lane layout of the solve kernel for a given batch: lane = (b_local, p, kk)
+// with bw * 2 * kk_per_warp = 32.
+struct SolveLayout {
+  int batch, bw, kk, groups, slots;  // slots = groups * kk
+  int nitems;
+  WorkItem *items_dev = nullptr;
+};
+
+struct FftPlan {
+  int n;
+  int nstages;
+  int radix[24];
+  int nsplit;     // rows per CTA (pairs of real rows packed as one complex row)
+  void *tw_dev;   // n twiddles e^{-2 pi i k/n} in the plan's precision
+};
+
+enum FacComp { F_L = 0, F_G, F_E, F_F, F_C, F_BD, F_BAD, F_ZP, F_ZM, F_NCOMP };
+
+struct Plan {
+  rexi_params prm{};
+  int N = 0, nlat = 0, nlon = 0, J = 0, P = 0;
+  int64_t nspec = 0, nrows = 0;
+  std::vector<cplx> alpha, beta;
+  double eps0 = 0;
+  int device = 0, num_sms = 0;
+  size_t bytes = 0;
+
+  // systems and rows
+  std::vector<SysInfo> sys;  // index 2 m + p
+  // per-coefficient coupling data on the device: {sigma, ct, dt, G} per idx(m, n)
+  double *coef_dev = nullptr;
+  // per system (index 2 m + p): {m, n0, len, row0}; per idx: zonal order m
+  int4 *sys_dev = nullptr;
+  int32_t *m_of_dev = nullptr;
+
+  // solve factors (forward and adjoint): [F_NCOMP][nrows][P] double2
+  double2 *fac_fwd = nullptr, *fac_adj = nullptr;
+  double2 *alpha_dev = nullptr, *beta_dev = nullptr;
+  // pole-independent parts: W[idx] = sum_k beta_k/s_{k,n} (zeta), scalar S_Phi
+  double2 *w_fwd = nullptr, *w_adj = nullptr;
+  double2 sphi_fwd{}, sphi_adj{};
+  // reduce flags per (field, idx): bit0 has partials, bit1 forced zero
+  uint8_t *rflags_dev = nullptr;
+
+  // grid / Legendre
+  double *mu_dev = nullptr;
+  double *tabP = nullptr, *tabH = nullptr;       // [nspec][J] FP64
+  float *tabP_hi = nullptr, *tabP_lo = nullptr;  // mixed: TF32 hi/lo splits
+  float *tabH_hi = nullptr, *tabH_lo = nullptr;
+  double *scale_ana_in = nullptr;   // [3][nlat]: analysis pre-scale (g w, cos w/(a(1-mu^2)))
+  double *scale_syn_out = nullptr;  // [3][nlat]: synthesis post-scale (1/g, 1/cos)
+  double *mscale_fwd = nullptr;     // [N+1]: 1/nlon
+  double *mscale_c = nullptr;       // [N+1]: c_m = 1, 2, 2, ...
+  double *mscale_adj = nullptr;     // [N+1]: 1/nlon, 1/(2 nlon), ...
+  double *mscale_one = nullptr;     // [N+1]: 1
+  double *zd_syn = nullptr;         // [nspec]: -a/(n(n+1)) (0 at n = 0)
+  double *zd_ana_adj = nullptr;     // [nspec]: +a/(n(n+1))
+  double *zd_one = nullptr;         // [nspec]: 1
+  double *zd_mone = nullptr;        // [nspec]: -1
+  FftPlan fft{};
+
+  // workspaces (max_batch)
+  double2 *four = nullptr;     // [nlat][N+1][3 B] complex (FP64 or FP32 pairs in mixed mode)
+  double2 *s_in = nullptr;     // [3][nspec][B]
+  double2 *s_out = nullptr;    // [3][nspec][B]
+  double2 *partial = nullptr;  // [3][nspec][slots][B]
+  double2 *yscratch = nullptr; // [resident warps][Lmax][32]
+  int resident_warps = 0, lmax = 0;
+  unsigned *counter = nullptr;
+  size_t partial_cap = 0;
+
+  std::map<int, SolveLayout> layouts;  // per batch size
+  int slots_override = 0;
+
+  // optional per-stage timing with CUDA events on the launching stream
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;  // [calls][kStages + 1]
+  int prof_calls = 0, prof_cap = 0;
+};
+
+enum Stage { ST_FFT_FWD = 0, ST_LEG_ANA, ST_SOLVE, ST_REDUCE, ST_LEG_SYN, ST_FFT_INV, ST_TRANS_IN,
+             ST_TRANS_OUT, kStages };
+
+// ---- kernels (launchers) ------------------------------------------------------------
+cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st);
+cudaError_t launch_solve(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin,
+                         int B, int pole_begin, int pole_end, bool use_beta, cudaStream_t st);
+cudaError_t launch_reduce(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin,
+                          double2 *sout, int B, bool single_pole, int pole, cudaStream_t st);
+cudaError_t launch_transpose_in(const double2 *user, double2 *sint, int64_t nspec, int B,
+                                cudaStream_t st);
+cudaError_t launch_transpose_out(const double2 *sint, double2 *user, int64_t nspec, int B, int N,
+                                 cudaStream_t st);
+cudaError_t launch_fft_fwd(Plan &pl, const double *grid, double2 *four, int B,
+                           const double *in_scale, const double *m_scale, cudaStream_t st);
+cudaError_t launch_fft_inv(Plan &pl, const double2 *four, double *grid, int B,
+                           const double *m_scale, const double *out_scale, cudaStream_t st);
+cudaError_t launch_leg_ana(Plan &pl, const double2 *four, double2 *sint, int B,
+                           const double *zdscale, cudaStream_t st);
+cudaError_t launch_leg_syn(Plan &pl, const double2 *sint, double2 *four, int B,
+                           const double *zdscale, cudaStream_t st);
+cudaError_t launch_leg_ana_tc(Plan &pl, const double2 *four, double2 *sint, int B,
+                              const double *zdscale, cudaStream_t st);
+cudaError_t launch_leg_syn_tc(Plan &pl, const double2 *sint, double2 *four, int B,
+                              const double *zdscale, cudaStream_t st);
+
+void set_error(const std::string &msg);
+
+}  // namespace rexi

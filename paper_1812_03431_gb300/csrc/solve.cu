@@ -1,0 +1,446 @@
+// Banded shifted solves and the beta-weighted pole sum (paper Sec. 4.2, Sec. 5,
+// Algorithm 1), FP64.
+//
+// Per zonal order m, (alpha + tau L_m) X = U couples (Phi_n, zeta_n, delta_n)
+// with L_m of Eq. (1) in spectral form:
+//   (L Phi)_n = -Phibar delta_n
+//   (L zeta)_n = i sigma_n zeta_n - 2 Omega [c_n delta_{n-1} + d_n delta_{n+1}]
+//   (L delta)_n = i sigma_n delta_n + 2 Omega [c_n zeta_{n-1} + d_n zeta_{n+1}] + G_n Phi_n
+// Eliminating Phi_n (Phi row) and zeta_{n+-1} (zeta rows) leaves, for each
+// parity of n - m, a complex tridiagonal system in delta over n, n +- 2.  This
+// is the paper's banded matrix B of Sec. 5 reached by a different elimination
+// (the paper multiplies by alpha^2 + f^2 and keeps Phi, bandwidth 5); the
+// shifted operator and its solution are the same.
+//
+// Everything that depends only on (pole k, m, n) -- the LU factors of the
+// tridiagonal systems, the right-hand-side couplings and the beta-weighted
+// recovery weights of Phi and zeta -- is computed once per plan
+// (factor_setup_kernel).  The per-step kernel then does, per (state, m,
+// parity, pole) and per row, a forward sweep
+//   y_i = delta0_n - g Phi0_n - e zeta0_{n-1} - f zeta0_{n+1} - l y_{i-1}
+// and a backward sweep  w_i = y_i - Chat w_{i+1}  (delta_n = w_i / d'_i, folded
+// into the weights) accumulating beta-weighted sums of delta, Phi and zeta in
+// FP64.  The poles are split into `slots` groups summed separately (each in
+// ascending k) and reduced in slot order, so results are bit-reproducible.
+#include <cuda_runtime.h>
+
+#include "rexi_internal.h"
+
+namespace rexi {
+
+namespace {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+// acc - a * b  (4 FP64 FMA)
+__device__ __forceinline__ double2 cfms(double2 acc, double2 a, double2 b) {
+  double re = fma(-a.x, b.x, acc.x);
+  re = fma(a.y, b.y, re);
+  double im = fma(-a.x, b.y, acc.y);
+  im = fma(-a.y, b.x, im);
+  return make_double2(re, im);
+}
+// acc + a * b  (4 FP64 FMA)
+__device__ __forceinline__ double2 cfma(double2 acc, double2 a, double2 b) {
+  double re = fma(a.x, b.x, acc.x);
+  re = fma(-a.y, b.y, re);
+  double im = fma(a.x, b.y, acc.y);
+  im = fma(a.y, b.x, im);
+  return make_double2(re, im);
+}
+
+struct SetupArgs {
+  const double *coef;   // [nspec][4] = sigma, ct, dt, G
+  const double2 *alpha, *beta;
+  double2 *fac;         // [F_NCOMP][nrows][P]
+  const int4 *sys;      // per system (m, p): {m, n0, len, row0}
+  int nsys, P, N;
+  int64_t nrows;
+  double tau, phibar, q;  // q = 2 Omega tau
+  int adjoint;
+};
+
+__device__ __forceinline__ int64_t sidx(int N, int m, int n) { return (int64_t)m * (2 * N + 3 - m) / 2 + (n - m); }
+
+// One thread per (pole, system): builds the tridiagonal rows, factorises them
+// (Thomas, no pivoting) and writes every per-row factor.
+__global__ void factor_setup_kernel(SetupArgs a) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)a.P * a.nsys) return;
+  const int k = (int)(t % a.P);
+  const int4 sy = a.sys[t / a.P];
+  const int m = sy.x, n0 = sy.y, len = sy.z;
+  const int64_t row0 = sy.w;
+  if (len <= 0) return;
+  const int N = a.N, nmin = m > 1 ? m : 1;
+  double2 al = a.alpha[k], be = a.beta[k];
+  if (a.adjoint) { al = cconj(al); be = cconj(be); }
+  const double tau = a.tau, q = a.q, pb = a.phibar;
+  auto C4 = [&](int n, int c) -> double {
+    if (n < nmin || n > N) return 0.0;
+    return a.coef[4 * sidx(N, m, n) + c];
+  };
+  auto ct = [&](int n) { return C4(n, 1); };
+  auto dt = [&](int n) { return C4(n, 2); };
+  auto s_of = [&](int n) -> double2 {  // alpha + i tau sigma_n (forward) / conj(alpha) - i tau sigma_n
+    double sg = C4(n, 0);
+    return a.adjoint ? make_double2(al.x, al.y - tau * sg) : make_double2(al.x, al.y + tau * sg);
+  };
+  const int64_t NR = a.nrows, P = a.P;
+  double2 *F = a.fac;
+  auto put = [&](int comp, int64_t row, double2 v) { F[((int64_t)comp * NR + row) * P + k] = v; };
+  const double2 one = make_double2(1.0, 0.0);
+
+  // first pass: d' and l, store d' temporarily in the F_C slot
+  double2 dprev = make_double2(1.0, 0.0), Cprev = make_double2(0.0, 0.0);
+  for (int i = 0; i < len; ++i) {
+    const int n = n0 + 2 * i;
+    const double G = C4(n, 3);
+    const double2 sn = s_of(n);
+    double2 D = cadd(sn, cscale(cdiv(one, al), tau * tau * pb * G));
+    double2 A = make_double2(0, 0), C = make_double2(0, 0);
+    double2 g, e = make_double2(0, 0), f = make_double2(0, 0);
+    if (!a.adjoint) {
+      if (ct(n) != 0.0) {
+        double2 inv = cdiv(one, s_of(n - 1));
+        D = cadd(D, cscale(inv, q * q * ct(n) * dt(n - 1)));
+        A = cscale(inv, q * q * ct(n) * ct(n - 1));
+        e = cscale(inv, q * ct(n));
+      }
+      if (dt(n) != 0.0) {
+        double2 inv = cdiv(one, s_of(n + 1));
+        D = cadd(D, cscale(inv, q * q * dt(n) * ct(n + 1)));
+        C = cscale(inv, q * q * dt(n) * dt(n + 1));
+        f = cscale(inv, q * dt(n));
+      }
+      g = cscale(cdiv(one, al), tau * G);
+    } else {
+      if (dt(n - 1) != 0.0) {
+        double2 inv = cdiv(one, s_of(n - 1));
+        D = cadd(D, cscale(inv, q * q * dt(n - 1) * ct(n)));
+        A = cscale(inv, q * q * dt(n - 1) * dt(n - 2));
+        e = cscale(inv, -q * dt(n - 1));
+      }
+      if (ct(n + 1) != 0.0) {
+        double2 inv = cdiv(one, s_of(n + 1));
+        D = cadd(D, cscale(inv, q * q * ct(n + 1) * dt(n)));
+        C = cscale(inv, q * q * ct(n + 1) * ct(n + 2));
+        f = cscale(inv, -q * ct(n + 1));
+      }
+      g = cscale(cdiv(one, al), -tau * pb);
+    }
+    double2 l = make_double2(0, 0), dp = D;
+    if (i > 0) {
+      l = cdiv(A, dprev);
+      dp = csub(D, cmul(l, Cprev));
+    }
+    const int64_t row = row0 + i;
+    put(F_L, row, l);
+    put(F_G, row, g);
+    put(F_E, row, e);
+    put(F_F, row, f);
+    put(F_C, row, C);   // raw upper coefficient, rescaled below
+    put(F_BD, row, dp); // d' (replaced below)
+    dprev = dp;
+    Cprev = C;
+  }
+  // second pass: Chat_i = C_i / d'_{i+1} and the beta-weighted recovery weights
+  double2 dnext = make_double2(1.0, 0.0);
+  for (int i = len - 1; i >= 0; --i) {
+    const int n = n0 + 2 * i;
+    const int64_t row = row0 + i;
+    const double2 C = F[((int64_t)F_C * NR + row) * P + k];
+    const double2 dp = F[((int64_t)F_BD * NR + row) * P + k];
+    put(F_C, row, i == len - 1 ? make_double2(0, 0) : cdiv(C, dnext));
+    const double2 bd = cdiv(be, dp);  // beta / d'
+    const double G = C4(n, 3);
+    double2 bad, zp = make_double2(0, 0), zm = make_double2(0, 0);
+    if (!a.adjoint) {
+      bad = cscale(cdiv(bd, al), tau * pb);
+      if (ct(n + 1) != 0.0) zp = cscale(cdiv(bd, s_of(n + 1)), q * ct(n + 1));
+      if (dt(n - 1) != 0.0) zm = cscale(cdiv(bd, s_of(n - 1)), q * dt(n - 1));
+    } else {
+      bad = cscale(cdiv(bd, al), -tau * G);
+      if (dt(n) != 0.0) zp = cscale(cdiv(bd, s_of(n + 1)), -q * dt(n));
+      if (ct(n) != 0.0) zm = cscale(cdiv(bd, s_of(n - 1)), -q * ct(n));
+    }
+    put(F_BD, row, bd);
+    put(F_BAD, row, bad);
+    put(F_ZP, row, zp);
+    put(F_ZM, row, zm);
+    dnext = dp;
+  }
+}
+
+struct SolveArgs {
+  const double2 *fac;   // [F_NCOMP][nrows][P]
+  const double2 *sin;   // [3][nspec][B]
+  double2 *part;        // [3][nspec][slots][B]
+  double2 *ybuf;        // [resident warps][lmax][32]
+  const WorkItem *items;
+  const int4 *sys;      // per (m, p): {m, n0, len, row0}
+  unsigned *counter;
+  int nitems, B, bw, kk, slots, P, N, lmax, pole_begin, pole_end;
+  int64_t nspec, nrows;
+};
+
+__device__ __forceinline__ double2 ld(const double2 *p) { return __ldg(p); }
+
+// Persistent kernel: each warp takes (m, pole group, first state) items from an
+// atomic counter (items are sorted longest first) and runs one tridiagonal
+// forward/backward sweep per (lane, pole).  Lane = (state b, parity p, slot kk).
+__global__ void __launch_bounds__(128) solve_kernel(SolveArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int wslot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  double2 *ybuf = a.ybuf + (int64_t)wslot * a.lmax * 32 + lane;
+  const int bl = lane % a.bw;
+  const int p = (lane / a.bw) & 1;
+  const int kk = lane / (2 * a.bw);
+  const int64_t NR = a.nrows, P = a.P, NS = a.nspec;
+  const int N = a.N, B = a.B, S = a.slots;
+  for (;;) {
+    unsigned it = 0;
+    if (lane == 0) it = atomicAdd(a.counter, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= (unsigned)a.nitems) break;
+    const WorkItem w = a.items[it];
+    const int b = w.b0 + bl;
+    const int4 sy = a.sys[2 * w.m + p];
+    const int m = sy.x, n0 = sy.y, len = sy.z;
+    const int64_t row0 = sy.w;
+    const int slot = w.g * a.kk + kk;
+    if (kk >= a.kk || b >= B || len <= 0 || slot >= S) continue;
+    const int nmin = m > 1 ? m : 1;
+    const int64_t base_idx = (int64_t)m * (2 * N + 3 - m) / 2 - m;  // idx(m, n) = base_idx + n
+    const double2 *sPhi = a.sin + b;
+    const double2 *sZeta = a.sin + NS * B + b;
+    const double2 *sDel = a.sin + 2 * NS * B + b;
+    double2 *pPhi = a.part + (int64_t)slot * B + b;
+    double2 *pZeta = pPhi + NS * S * B;
+    double2 *pDel = pPhi + 2 * NS * S * B;
+    const int64_t rstride = (int64_t)S * B;  // partial stride per idx
+    bool first = true;
+    for (int k = a.pole_begin + slot; k < a.pole_end; k += S) {
+      // ---- forward sweep
+      const double2 *fL = a.fac + ((int64_t)F_L * NR + row0) * P + k;
+      const double2 *fG = a.fac + ((int64_t)F_G * NR + row0) * P + k;
+      const double2 *fE = a.fac + ((int64_t)F_E * NR + row0) * P + k;
+      const double2 *fF = a.fac + ((int64_t)F_F * NR + row0) * P + k;
+      double2 yprev = make_double2(0, 0);
+      double2 zprev = (n0 - 1 >= nmin) ? ld(sZeta + (base_idx + n0 - 1) * B) : make_double2(0, 0);
+      for (int i = 0; i < len; ++i) {
+        const int n = n0 + 2 * i;
+        const int64_t ix = base_idx + n;
+        const double2 zn = (n + 1 <= N) ? ld(sZeta + (ix + 1) * B) : make_double2(0, 0);
+        double2 y = ld(sDel + ix * B);
+        y = cfms(y, ld(fG + (int64_t)i * P), ld(sPhi + ix * B));
+        y = cfms(y, ld(fE + (int64_t)i * P), zprev);
+        y = cfms(y, ld(fF + (int64_t)i * P), zn);
+        y = cfms(y, ld(fL + (int64_t)i * P), yprev);
+        ybuf[(int64_t)i * 32] = y;
+        yprev = y;
+        zprev = zn;
+      }
+      // ---- backward sweep with the beta-weighted accumulation
+      const double2 *fC = a.fac + ((int64_t)F_C * NR + row0) * P + k;
+      const double2 *fBD = a.fac + ((int64_t)F_BD * NR + row0) * P + k;
+      const double2 *fBAD = a.fac + ((int64_t)F_BAD * NR + row0) * P + k;
+      const double2 *fZP = a.fac + ((int64_t)F_ZP * NR + row0) * P + k;
+      const double2 *fZM = a.fac + ((int64_t)F_ZM * NR + row0) * P + k;
+      double2 wnext = make_double2(0, 0), carry = make_double2(0, 0);
+      for (int i = len - 1; i >= 0; --i) {
+        const int n = n0 + 2 * i;
+        const int64_t ix = base_idx + n;
+        const double2 y = ybuf[(int64_t)i * 32];
+        const double2 wv = cfms(y, ld(fC + (int64_t)i * P), wnext);
+        double2 accD = first ? make_double2(0, 0) : pDel[ix * rstride];
+        double2 accP = first ? make_double2(0, 0) : pPhi[ix * rstride];
+        pDel[ix * rstride] = cfma(accD, ld(fBD + (int64_t)i * P), wv);
+        pPhi[ix * rstride] = cfma(accP, ld(fBAD + (int64_t)i * P), wv);
+        if (n + 1 <= N) {
+          double2 accZ = first ? carry : cadd(pZeta[(ix + 1) * rstride], carry);
+          pZeta[(ix + 1) * rstride] = cfma(accZ, ld(fZP + (int64_t)i * P), wv);
+        }
+        carry = cmul(ld(fZM + (int64_t)i * P), wv);
+        wnext = wv;
+      }
+      if (n0 - 1 >= nmin) {
+        const int64_t ix = base_idx + n0 - 1;
+        pZeta[ix * rstride] = first ? carry : cadd(pZeta[ix * rstride], carry);
+      }
+      first = false;
+    }
+  }
+}
+
+struct ReduceArgs {
+  const double2 *part, *sin;
+  double2 *sout;
+  const uint8_t *rflags;   // [3][nspec]
+  const double2 *w;        // [nspec] zeta weights sum beta/s
+  const double *coef;      // [nspec][4] (for single-pole s_n)
+  const int32_t *m_of;     // [nspec] zonal order of idx
+  double2 sphi;
+  int slots, B, N;
+  int64_t nspec;
+  int single, realm0, adjoint;
+  double2 alpha_k, beta_k;
+  double tau;
+};
+
+// out[f][idx][b] = sum over slots (in order) + the pole-independent terms.
+__global__ void reduce_kernel(ReduceArgs a) {
+  const int64_t total = 3 * a.nspec * a.B;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t % a.B);
+    const int64_t fi = t / a.B;  // f * nspec + idx
+    const int f = (int)(fi / a.nspec);
+    const int64_t ix = fi - (int64_t)f * a.nspec;
+    const uint8_t fl = a.rflags[fi];
+    double2 acc = make_double2(0, 0);
+    if (!(fl & 2)) {
+      if (fl & 1) {
+        const double2 *p = a.part + fi * a.slots * a.B + b;
+        for (int s = 0; s < a.slots; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
+      }
+      const double2 x0 = a.sin[t];
+      if (!a.single) {
+        if (f == 0) acc = cfma(acc, a.sphi, x0);
+        else if (f == 1) acc = cfma(acc, a.w[ix], x0);
+      } else {
+        // single pole: partials carry beta_k X_k; divide beta_k out and add Phi0/alpha, zeta0/s
+        acc = cdiv(acc, a.beta_k);
+        if (f == 0) acc = cadd(acc, cdiv(x0, a.alpha_k));
+        else if (f == 1) {
+          double sg = a.coef[4 * ix + 0];
+          double2 s = a.adjoint ? make_double2(a.alpha_k.x, -a.alpha_k.y - a.tau * sg)
+                                : make_double2(a.alpha_k.x, a.alpha_k.y + a.tau * sg);
+          acc = cadd(acc, cdiv(x0, s));
+        }
+      }
+      if (a.realm0 && a.m_of[ix] == 0) acc.y = 0.0;
+    }
+    a.sout[t] = acc;
+  }
+}
+
+// [rows][cols] -> [cols][rows] of double2 via 32x32 shared tiles.
+__global__ void transpose_kernel(const double2 *in, double2 *out, int64_t rows, int64_t cols) {
+  __shared__ double2 tile[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    int64_t r = r0 + j, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[j][threadIdx.x] = in[r * cols + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    int64_t c = c0 + j, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[c * rows + r] = tile[threadIdx.x][j];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st) {
+  SetupArgs a;
+  a.coef = pl.coef_dev;
+  a.alpha = pl.alpha_dev;
+  a.beta = pl.beta_dev;
+  a.fac = adjoint ? pl.fac_adj : pl.fac_fwd;
+  a.sys = pl.sys_dev;
+  a.nsys = (int)pl.sys.size();
+  a.P = pl.P;
+  a.N = pl.N;
+  a.nrows = pl.nrows;
+  a.tau = pl.prm.tau;
+  a.phibar = pl.prm.gravity * pl.prm.mean_depth;
+  a.q = 2.0 * pl.prm.omega * pl.prm.tau;
+  a.adjoint = adjoint ? 1 : 0;
+  int64_t total = (int64_t)a.P * a.nsys;
+  factor_setup_kernel<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, int B,
+                         int pole_begin, int pole_end, bool, cudaStream_t st) {
+  SolveArgs a;
+  a.fac = adjoint ? pl.fac_adj : pl.fac_fwd;
+  a.sin = sin;
+  a.part = pl.partial;
+  a.ybuf = pl.yscratch;
+  a.items = lay.items_dev;
+  a.sys = pl.sys_dev;
+  a.counter = pl.counter;
+  a.nitems = lay.nitems;
+  a.B = B;
+  a.bw = lay.bw;
+  a.kk = lay.kk;
+  a.slots = lay.slots;
+  a.P = pl.P;
+  a.N = pl.N;
+  a.lmax = pl.lmax;
+  a.pole_begin = pole_begin;
+  a.pole_end = pole_end;
+  a.nspec = pl.nspec;
+  a.nrows = pl.nrows;
+  cudaError_t e = cudaMemsetAsync(pl.counter, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  solve_kernel<<<pl.resident_warps / 4, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin,
+                          double2 *sout, int B, bool single_pole, int pole, cudaStream_t st) {
+  ReduceArgs a;
+  a.part = pl.partial;
+  a.sin = sin;
+  a.sout = sout;
+  a.rflags = pl.rflags_dev;
+  a.w = adjoint ? pl.w_adj : pl.w_fwd;
+  a.coef = pl.coef_dev;
+  a.m_of = pl.m_of_dev;
+  a.sphi = adjoint ? pl.sphi_adj : pl.sphi_fwd;
+  a.slots = single_pole ? 1 : lay.slots;
+  a.B = B;
+  a.N = pl.N;
+  a.nspec = pl.nspec;
+  a.single = single_pole ? 1 : 0;
+  a.realm0 = single_pole ? 0 : 1;
+  a.adjoint = adjoint ? 1 : 0;
+  a.tau = pl.prm.tau;
+  a.alpha_k = single_pole ? make_double2(pl.alpha[pole].real(), pl.alpha[pole].imag()) : make_double2(0, 0);
+  a.beta_k = single_pole ? make_double2(pl.beta[pole].real(), pl.beta[pole].imag()) : make_double2(1, 0);
+  int64_t total = 3 * pl.nspec * B;
+  int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)pl.num_sms * 8);
+  reduce_kernel<<<blocks, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_in(const double2 *user, double2 *sint, int64_t nspec, int B,
+                                cudaStream_t st) {
+  // user [B][3 nspec] -> sint [3 nspec][B]
+  int64_t rows = B, cols = 3 * nspec;
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(user, sint, rows, cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_out(const double2 *sint, double2 *user, int64_t nspec, int B, int,
+                                 cudaStream_t st) {
+  int64_t rows = 3 * nspec, cols = B;
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(sint, user, rows, cols);
+  return cudaGetLastError();
+}
+
+}  // namespace rexi
