@@ -96,7 +96,6 @@ class ClockSampler:
 
 def cpu_baseline(sample_ms=None):
     """The CPU oracle as it stands on a bounded sample of the workload, extrapolated to one step."""
-    import threadpoolctl  # noqa: F401  (thread count report only)
     from oracle import rexi_coeffs
     from oracle import step as ostep
     from paper_1812_03431_gb300 import inputs

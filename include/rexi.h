@@ -74,8 +74,8 @@ typedef struct rexi_plan rexi_plan;
  * Hbar = 1e4 m), h = 0.2, normalize = 1, FP64, grid layout, max_batch = 1. */
 typedef struct {
   int32_t ntrunc;       /* N: triangular truncation, 1 <= N */
-  int32_t nlat, nlon;   /* Gaussian grid; nlat even, nlat >= N + 1, nlon >= 2N + 1,
-                           nlon = 2^a 3^b 5^c; used by the grid layout only */
+  int32_t nlat, nlon;   /* Gaussian grid; nlat even, nlat >= N + 1, nlon even, nlon >= 2N + 2,
+                           nlon = 2^a 3^b 5^c (the Legendre tables are built for every layout) */
   int32_t M;            /* Gaussian basis functions per side (Sec. 4.1); P = 2 (M + 11) + 1 */
   double h;             /* width parameter of the Gaussian basis (Sec. 4.1) */
   double tau;           /* time-step size (s) */

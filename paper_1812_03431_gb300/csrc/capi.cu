@@ -28,22 +28,36 @@ rexi_status cuda_fail(const char *what, cudaError_t e) {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Event marks: call k records event (k, stage) at the start of each stage and
-// (k, kStages) at the end; stages that do not run get start == next start.
+// Event marks: a timed call records one event at the start of each stage it
+// runs and one at its end; each interval is attributed to the stage that
+// opened it.
 struct Marks {
   Plan &pl;
   cudaStream_t st;
   int call = -1;
   Marks(Plan &p, cudaStream_t s) : pl(p), st(s) {
-    if (pl.prof && pl.prof_calls < pl.prof_cap) call = pl.prof_calls++;
+    if (pl.prof && pl.prof_calls < pl.prof_cap) {
+      call = pl.prof_calls++;
+      pl.prof_n[call] = 0;
+    }
   }
   void mark(int stage) {
     if (call < 0) return;
-    for (int s2 = stage; s2 <= kStages; ++s2) cudaEventRecord(pl.prof_ev[(size_t)call * (kStages + 1) + s2], st);
+    int &k = pl.prof_n[call];
+    if (k > kStages) return;
+    const size_t at = (size_t)call * (kStages + 1) + k;
+    cudaEventRecord(pl.prof_ev[at], st);
+    pl.prof_sid[at] = stage;
+    ++k;
   }
 };
 
+rexi_status check_io2(const Plan &pl, const void *in, const void *out, int B, bool grid_in, bool grid_out);
 rexi_status check_io(const Plan &pl, const void *in, const void *out, int B, bool grid) {
+  return check_io2(pl, in, out, B, grid, grid);
+}
+
+rexi_status check_io2(const Plan &pl, const void *in, const void *out, int B, bool grid_in, bool grid_out) {
   if (!in || !out) {
     set_error("null device pointer");
     return REXI_EINVAL;
@@ -56,10 +70,11 @@ rexi_status check_io(const Plan &pl, const void *in, const void *out, int B, boo
     set_error("device pointers must be 16-byte aligned");
     return REXI_EINVAL;
   }
-  const size_t bytes = grid ? (size_t)B * 3 * pl.nlat * pl.nlon * sizeof(double)
-                            : (size_t)B * 3 * pl.nspec * 2 * sizeof(double);
+  const size_t gbytes = (size_t)B * 3 * pl.nlat * pl.nlon * sizeof(double);
+  const size_t sbytes = (size_t)B * 3 * pl.nspec * 2 * sizeof(double);
+  const size_t ibytes = grid_in ? gbytes : sbytes, obytes = grid_out ? gbytes : sbytes;
   const char *a = static_cast<const char *>(in), *b = static_cast<const char *>(out);
-  if (a < b + bytes && b < a + bytes) {
+  if (a < b + obytes && b < a + ibytes) {
     set_error("in and out overlap");
     return REXI_EINVAL;
   }
@@ -222,8 +237,8 @@ rexi_status rexi_plan_create(const rexi_params *prm, rexi_plan **out) {
     set_error("rexi_plan_create: give both alpha and beta with npoles >= 1, or M >= 1 and h > 0");
     return REXI_EINVAL;
   }
-  if (p.nlat % 2 != 0 || p.nlat < p.ntrunc + 1 || p.nlon < 2 * p.ntrunc + 1) {
-    set_error("rexi_plan_create: need even nlat >= N + 1 and nlon >= 2N + 1");
+  if (p.nlat % 2 != 0 || p.nlon % 2 != 0 || p.nlat < p.ntrunc + 1 || p.nlon < 2 * p.ntrunc + 2) {
+    set_error("rexi_plan_create: need even nlat >= N + 1 and even nlon >= 2N + 2");
     return REXI_EINVAL;
   }
   {
@@ -265,7 +280,7 @@ rexi_status rexi_step_adjoint(rexi_plan *plan, const void *gout_dev, void *gin_d
 rexi_status rexi_analyze(rexi_plan *plan, const void *grid_dev, void *spec_dev, int32_t B, void *stream) {
   if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
   Plan &pl = *plan->pl;
-  rexi_status r = check_io(pl, grid_dev, spec_dev, B, true);
+  rexi_status r = check_io2(pl, grid_dev, spec_dev, B, true, false);
   if (r != REXI_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Marks mk(pl, st);
@@ -278,7 +293,7 @@ rexi_status rexi_analyze(rexi_plan *plan, const void *grid_dev, void *spec_dev, 
 rexi_status rexi_synthesize(rexi_plan *plan, const void *spec_dev, void *grid_dev, int32_t B, void *stream) {
   if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
   Plan &pl = *plan->pl;
-  rexi_status r = check_io(pl, spec_dev, grid_dev, B, true);
+  rexi_status r = check_io2(pl, spec_dev, grid_dev, B, false, true);
   if (r != REXI_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = launch_transpose_in(static_cast<const double2 *>(spec_dev), pl.s_out, pl.nspec, B, st);
@@ -344,6 +359,8 @@ rexi_status rexi_profile_enable(rexi_plan *plan, int32_t max_calls) {
   pl.prof_cap = max_calls;
   pl.prof = max_calls > 0;
   pl.prof_ev.resize((size_t)max_calls * (kStages + 1));
+  pl.prof_sid.assign((size_t)max_calls * (kStages + 1), kStages);
+  pl.prof_n.assign((size_t)max_calls, 0);
   for (auto &ev : pl.prof_ev) {
     cudaError_t e = cudaEventCreate(&ev);
     if (e != cudaSuccess) return cuda_fail("event create", e);
@@ -356,14 +373,17 @@ rexi_status rexi_profile_read(rexi_plan *plan, double *stage_ms, int32_t n, int3
   Plan &pl = *plan->pl;
   std::vector<double> acc(kStages, 0.0);
   for (int c = 0; c < pl.prof_calls; ++c) {
-    cudaEvent_t *ev = &pl.prof_ev[(size_t)c * (kStages + 1)];
-    cudaError_t e = cudaEventSynchronize(ev[kStages]);
+    const size_t base = (size_t)c * (kStages + 1);
+    const int k = pl.prof_n[c];
+    if (k < 2) continue;
+    cudaError_t e = cudaEventSynchronize(pl.prof_ev[base + k - 1]);
     if (e != cudaSuccess) return cuda_fail("event sync", e);
-    for (int s = 0; s < kStages; ++s) {
+    for (int i = 0; i + 1 < k; ++i) {
       float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
+      e = cudaEventElapsedTime(&ms, pl.prof_ev[base + i], pl.prof_ev[base + i + 1]);
       if (e != cudaSuccess) return cuda_fail("event time", e);
-      acc[s] += ms;
+      const int sid = pl.prof_sid[base + i];
+      if (sid >= 0 && sid < kStages) acc[sid] += ms;
     }
   }
   for (int s = 0; s < n && s < kStages; ++s) stage_ms[s] = acc[s];

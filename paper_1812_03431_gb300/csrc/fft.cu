@@ -4,10 +4,14 @@
 // with per-(field, latitude) input/output scales that carry Robert's cos(lat)
 // factor, g, the Gaussian weights and the transposes' scalings.
 //
-// Two real rows are packed as one complex sequence z = x1 + i x2 and
+// Each real row of even length n is transformed on its own: its even and odd
+// samples form one complex sequence z_k = x_{2k} + i x_{2k+1} of length n/2,
 // transformed by a mixed-radix (2, 3, 4, 5) Stockham autosort FFT in shared
-// memory; X1 and X2 are separated from Z_m and conj(Z_{n-m}).  The inverse is
-// conj(FFT(conj(Z))) on the Hermitian-extended spectrum.
+// memory; X_m = E_m + e^{-2 pi i m/n} O_m with E_m = (Z_m + conj Z_{n/2-m})/2,
+// O_m = (Z_m - conj Z_{n/2-m})/(2i).  (Packing two different rows instead would
+// let the rounding of a large row leak into a small one.)  The inverse builds
+// Z'_m = E'_m + i O'_m from the Hermitian spectrum and evaluates
+// conj(FFT(conj Z')).
 //
 // Layouts: grid [B][3][nlat][nlon] float64; Fourier [nlat][N+1][3B] complex,
 // column c = 3 b + field, so that for each latitude the Legendre kernels read
@@ -23,8 +27,8 @@ namespace rexi {
 namespace {
 
 struct FftArgs {
-  const double2 *tw;  // n twiddles e^{-2 pi i k / n}
-  int n, nstages, N, nlat, ncol, np;  // np: complex rows (column pairs) per CTA
+  const double2 *tw;  // n twiddles e^{-2 pi i k / n} (n = nlon)
+  int n, h, nstages, N, nlat, ncol, np;  // h = n / 2 complex points per row; np rows per CTA
   int radix[24];
   double c3, s3, c5a, s5a, c5b, s5b;  // cos/sin of 2pi/3, 2pi/5, 4pi/5
 };
@@ -77,7 +81,7 @@ __device__ __forceinline__ void dft_small(double2 *v, int R, const FftArgs &a) {
 // In-shared-memory forward FFT of np rows of length n; returns the buffer
 // holding the result (buf0 or buf1).
 __device__ double2 *fft_smem(double2 *buf0, double2 *buf1, const FftArgs &a) {
-  const int n = a.n;
+  const int n = a.h;
   double2 *src = buf0, *dst = buf1;
   int Ns = 1;
   for (int s = 0; s < a.nstages; ++s) {
@@ -92,7 +96,7 @@ __device__ double2 *fft_smem(double2 *buf0, double2 *buf1, const FftArgs &a) {
       const int jm = jb % Ns;
       for (int r = 0; r < R; ++r) {
         double2 x = in[jb + r * nb];
-        if (r > 0 && jm > 0) x = cmulz(x, __ldg(a.tw + r * jm * stride));
+        if (r > 0 && jm > 0) x = cmulz(x, __ldg(a.tw + 2 * r * jm * stride));
         v[r] = x;
       }
       dft_small(v, R, a);
@@ -111,71 +115,83 @@ __device__ double2 *fft_smem(double2 *buf0, double2 *buf1, const FftArgs &a) {
 __global__ void fft_fwd_kernel(FftArgs a, const double *grid, double2 *four, const double *in_scale,
                                const double *m_scale) {
   extern __shared__ double2 sm[];
-  const int n = a.n;
-  double2 *buf0 = sm, *buf1 = sm + a.np * n;
+  const int h = a.h;
+  double2 *buf0 = sm, *buf1 = sm + a.np * h;
   const int j = blockIdx.y;
-  const int pair0 = blockIdx.x * a.np;
-  for (int t = threadIdx.x; t < a.np * n; t += blockDim.x) {
-    const int q = t / n, i = t - q * n;
-    const int c1 = 2 * (pair0 + q), c2 = c1 + 1;
-    double x1 = 0.0, x2 = 0.0;
-    if (c1 < a.ncol) x1 = grid[((int64_t)c1 * a.nlat + j) * n + i] * in_scale[(c1 % 3) * a.nlat + j];
-    if (c2 < a.ncol) x2 = grid[((int64_t)c2 * a.nlat + j) * n + i] * in_scale[(c2 % 3) * a.nlat + j];
-    buf0[t] = make_double2(x1, x2);
+  const int c0 = blockIdx.x * a.np;
+  const double2 *g2 = reinterpret_cast<const double2 *>(grid);
+  for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
+    const int q = t / h, k = t - q * h;
+    const int c = c0 + q;
+    double2 v = make_double2(0.0, 0.0);
+    if (c < a.ncol) {
+      const double s = in_scale[(c % 3) * a.nlat + j];
+      v = g2[((int64_t)c * a.nlat + j) * h + k];
+      v = make_double2(s * v.x, s * v.y);
+    }
+    buf0[t] = v;
   }
   __syncthreads();
   const double2 *Z = fft_smem(buf0, buf1, a);
   const int M1 = a.N + 1;
   for (int t = threadIdx.x; t < a.np * M1; t += blockDim.x) {
     const int m = t / a.np, q = t - m * a.np;
-    const int c1 = 2 * (pair0 + q), c2 = c1 + 1;
-    const double2 zm = Z[q * n + m];
-    const double2 zn = Z[q * n + (m == 0 ? 0 : n - m)];
+    const int c = c0 + q;
+    if (c >= a.ncol) continue;
+    const double2 zm = Z[q * h + m];
+    const double2 zr = Z[q * h + (m == 0 ? 0 : h - m)];
+    // E = (Z_m + conj Z_{h-m}) / 2,  O = (Z_m - conj Z_{h-m}) / (2 i)
+    const double2 E = make_double2(0.5 * (zm.x + zr.x), 0.5 * (zm.y - zr.y));
+    const double2 O = make_double2(0.5 * (zm.y + zr.y), -0.5 * (zm.x - zr.x));
+    const double2 w = __ldg(a.tw + m);
+    const double2 X = addz(E, cmulz(w, O));
     const double s = m_scale[m];
-    // X1 = (Z_m + conj Z_{n-m}) / 2,  X2 = (Z_m - conj Z_{n-m}) / (2 i)
-    const double2 x1 = make_double2(0.5 * s * (zm.x + zn.x), 0.5 * s * (zm.y - zn.y));
-    const double2 x2 = make_double2(0.5 * s * (zm.y + zn.y), -0.5 * s * (zm.x - zn.x));
-    double2 *o = four + ((int64_t)j * M1 + m) * a.ncol;
-    if (c1 < a.ncol) o[c1] = x1;
-    if (c2 < a.ncol) o[c2] = x2;
+    four[((int64_t)j * M1 + m) * a.ncol + c] = make_double2(s * X.x, s * X.y);
   }
 }
 
 __global__ void fft_inv_kernel(FftArgs a, const double2 *four, double *grid, const double *m_scale,
                                const double *out_scale) {
   extern __shared__ double2 sm[];
-  const int n = a.n;
-  double2 *buf0 = sm, *buf1 = sm + a.np * n;
+  const int h = a.h;
+  double2 *buf0 = sm, *buf1 = sm + a.np * h;
   const int j = blockIdx.y;
-  const int pair0 = blockIdx.x * a.np;
-  const int M1 = a.N + 1;
-  for (int t = threadIdx.x; t < a.np * n; t += blockDim.x) buf0[t] = make_double2(0.0, 0.0);
-  __syncthreads();
-  for (int t = threadIdx.x; t < a.np * M1; t += blockDim.x) {
-    const int m = t / a.np, q = t - m * a.np;
-    const int c1 = 2 * (pair0 + q), c2 = c1 + 1;
-    const double2 *in = four + ((int64_t)j * M1 + m) * a.ncol;
-    const double s = m_scale[m];
-    double2 x1 = c1 < a.ncol ? in[c1] : make_double2(0, 0);
-    double2 x2 = c2 < a.ncol ? in[c2] : make_double2(0, 0);
-    x1 = make_double2(s * x1.x, s * x1.y);
-    x2 = make_double2(s * x2.x, s * x2.y);
-    if (m == 0) {
-      x1.y = 0.0;
-      x2.y = 0.0;
+  const int c0 = blockIdx.x * a.np;
+  const int N = a.N, M1 = N + 1;
+  for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
+    const int q = t / h, m = t - q * h;
+    const int c = c0 + q;
+    double2 A = make_double2(0, 0), Bc = make_double2(0, 0);
+    if (c < a.ncol) {
+      if (m <= N) {
+        const double s = m_scale[m];
+        const double2 v = four[((int64_t)j * M1 + m) * a.ncol + c];
+        A = make_double2(s * v.x, m == 0 ? 0.0 : s * v.y);
+      }
+      const int mr = h - m;  // partner X_{h-m}, present when h - m <= N
+      if (m > 0 && mr <= N) {
+        const double s = m_scale[mr];
+        const double2 v = four[((int64_t)j * M1 + mr) * a.ncol + c];
+        Bc = make_double2(s * v.x, mr == 0 ? 0.0 : -s * v.y);  // conj(X_{h-m})
+      }
     }
-    // Z_m = X1 + i X2 and Z_{n-m} = conj(X1) + i conj(X2); store conj(Z) for the inverse
-    buf0[q * n + m] = make_double2(x1.x - x2.y, -(x1.y + x2.x));
-    if (m > 0) buf0[q * n + n - m] = make_double2(x1.x + x2.y, -(x2.x - x1.y));
+    // E' = X_m + conj X_{h-m},  O' = (X_m - conj X_{h-m}) e^{+2 pi i m / n},  Z' = E' + i O'
+    const double2 E = addz(A, Bc);
+    const double2 w = __ldg(a.tw + m);
+    const double2 O = cmulz(subz(A, Bc), make_double2(w.x, -w.y));
+    const double2 Zp = make_double2(E.x - O.y, E.y + O.x);
+    buf0[t] = make_double2(Zp.x, -Zp.y);  // conj(Z') for the inverse by a forward FFT
   }
   __syncthreads();
-  const double2 *z = fft_smem(buf0, buf1, a);
-  for (int t = threadIdx.x; t < a.np * n; t += blockDim.x) {
-    const int q = t / n, i = t - q * n;
-    const int c1 = 2 * (pair0 + q), c2 = c1 + 1;
-    const double2 r = z[t];  // conj of the inverse transform: x1 = r.x, x2 = -r.y
-    if (c1 < a.ncol) grid[((int64_t)c1 * a.nlat + j) * n + i] = r.x * out_scale[(c1 % 3) * a.nlat + j];
-    if (c2 < a.ncol) grid[((int64_t)c2 * a.nlat + j) * n + i] = -r.y * out_scale[(c2 % 3) * a.nlat + j];
+  const double2 *r = fft_smem(buf0, buf1, a);
+  double2 *g2 = reinterpret_cast<double2 *>(grid);
+  for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
+    const int q = t / h, k = t - q * h;
+    const int c = c0 + q;
+    if (c >= a.ncol) continue;
+    const double s = out_scale[(c % 3) * a.nlat + j];
+    const double2 v = r[t];  // conj of z_k = x_{2k} + i x_{2k+1}
+    g2[((int64_t)c * a.nlat + j) * h + k] = make_double2(s * v.x, -s * v.y);
   }
 }
 
@@ -183,6 +199,7 @@ FftArgs make_args(const Plan &pl, int B) {
   FftArgs a;
   a.tw = static_cast<const double2 *>(pl.fft.tw_dev);
   a.n = pl.fft.n;
+  a.h = pl.fft.n / 2;
   a.nstages = pl.fft.nstages;
   for (int s = 0; s < 24; ++s) a.radix[s] = pl.fft.radix[s];
   a.N = pl.N;
@@ -211,13 +228,12 @@ bool fft_factor(int n, int *radix, int *nstages) {
   return m == 1 && k < 24;
 }
 
-size_t fft_smem_bytes(const Plan &pl) { return (size_t)2 * pl.fft.nsplit * pl.fft.n * sizeof(double2); }
+size_t fft_smem_bytes(const Plan &pl) { return (size_t)pl.fft.nsplit * pl.fft.n * sizeof(double2); }
 
 cudaError_t launch_fft_fwd(Plan &pl, const double *grid, double2 *four, int B, const double *in_scale,
                            const double *m_scale, cudaStream_t st) {
   FftArgs a = make_args(pl, B);
-  const int npairs = (a.ncol + 1) / 2;
-  dim3 g((unsigned)((npairs + a.np - 1) / a.np), (unsigned)pl.nlat);
+  dim3 g((unsigned)((a.ncol + a.np - 1) / a.np), (unsigned)pl.nlat);
   size_t sm = fft_smem_bytes(pl);
   fft_fwd_kernel<<<g, 256, sm, st>>>(a, grid, four, in_scale, m_scale);
   return cudaGetLastError();
@@ -226,8 +242,7 @@ cudaError_t launch_fft_fwd(Plan &pl, const double *grid, double2 *four, int B, c
 cudaError_t launch_fft_inv(Plan &pl, const double2 *four, double *grid, int B, const double *m_scale,
                            const double *out_scale, cudaStream_t st) {
   FftArgs a = make_args(pl, B);
-  const int npairs = (a.ncol + 1) / 2;
-  dim3 g((unsigned)((npairs + a.np - 1) / a.np), (unsigned)pl.nlat);
+  dim3 g((unsigned)((a.ncol + a.np - 1) / a.np), (unsigned)pl.nlat);
   size_t sm = fft_smem_bytes(pl);
   fft_inv_kernel<<<g, 256, sm, st>>>(a, four, grid, m_scale, out_scale);
   return cudaGetLastError();

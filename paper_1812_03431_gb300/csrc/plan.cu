@@ -240,8 +240,8 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
     if ((e = upload(&pl->mscale_one, m1, &bytes))) return fail("mscale", e);
     FftPlan &f = pl->fft;
     f.n = pl->nlon;
-    fft_factor(f.n, f.radix, &f.nstages);
-    f.nsplit = std::max(1, 2048 / f.n);
+    fft_factor(f.n / 2, f.radix, &f.nstages);  // half-length complex FFT per real row
+    f.nsplit = std::max(1, 4096 / f.n);
     std::vector<double2> tw(f.n);
     for (int k = 0; k < f.n; ++k) {
       const double th = 2.0 * M_PI * k / f.n;

@@ -122,7 +122,9 @@ struct Plan {
 
   // optional per-stage timing with CUDA events on the launching stream
   bool prof = false;
-  std::vector<cudaEvent_t> prof_ev;  // [calls][kStages + 1]
+  std::vector<cudaEvent_t> prof_ev;  // [calls][kStages + 1], in recording order
+  std::vector<int> prof_sid;         // stage id of each recorded mark (kStages = end)
+  std::vector<int> prof_n;           // marks recorded per call
   int prof_calls = 0, prof_cap = 0;
 };
 
