@@ -128,6 +128,28 @@ rexi_status rexi_step(rexi_plan *plan, const void *in_dev, void *out_dev,
 rexi_status rexi_step_adjoint(rexi_plan *plan, const void *gout_dev, void *gin_dev,
                               int32_t batch, void *stream);
 
+/* Allocation-free spectral step (no counterpart in the paper).  Some callers
+ * cannot allocate device memory while they step -- for example a time loop
+ * inside an application that hands all device memory out at start-up, or code
+ * that must not re-enter an allocator.  This entry point computes the same
+ * result as rexi_step on a REXI_SPECTRAL plan (up to the summation order of the
+ * poles) and allocates nothing: every per-call scratch buffer lives in one
+ * file-scope device array of 64 MiB that each device loading the library holds
+ * until exit.  The plan's read-only tables and the caller's in/out buffers are
+ * used as usual.
+ *   - Sizes whose scratch would exceed 64 MiB (3 nspec batch x 32 B for the two
+ *     state copies, plus the pole-slot partial sums, the sweep buffers of four
+ *     warps per SM and the work list) return REXI_EINVAL with the needed size.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents; the
+ *     work counter is cleared on the stream at the start of every call.  Calls
+ *     that overlap on the GPU (other streams, other threads) race on it.
+ * Plan layout must be REXI_SPECTRAL; in/out as for rexi_step. */
+rexi_status rexi_step_static(rexi_plan *plan, const void *in_dev, void *out_dev,
+                             int32_t batch, void *stream);
+
 /* Spectral <-> grid transforms of the plan's grid (Sec. 3): analysis maps
  * grid (h', u, v) to spectral (Phi, zeta, delta); synthesis the reverse. */
 rexi_status rexi_analyze(rexi_plan *plan, const void *grid_dev, void *spec_dev,

@@ -18,6 +18,7 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 rexi_status build_plan(const rexi_params &prm, Plan *pl);
 rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out);
 void free_plan(Plan *pl);
+rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t st);
 
 namespace {
 
@@ -318,6 +319,18 @@ rexi_status rexi_solve_pole(rexi_plan *plan, int32_t k, const void *in_dev, void
   if (e == cudaSuccess) e = launch_reduce(pl, *lay, false, pl.s_in, pl.s_out, B, true, k, st);
   if (e == cudaSuccess) e = launch_transpose_out(pl.s_out, static_cast<double2 *>(out_dev), pl.nspec, B, pl.N, st);
   return e == cudaSuccess ? REXI_OK : cuda_fail("solve_pole", e);
+}
+
+rexi_status rexi_step_static(rexi_plan *plan, const void *in_dev, void *out_dev, int32_t batch, void *stream) {
+  if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
+  Plan &pl = *plan->pl;
+  if (pl.prm.layout != REXI_SPECTRAL) {
+    set_error("rexi_step_static: needs a plan in REXI_SPECTRAL layout");
+    return REXI_EINVAL;
+  }
+  rexi_status r = check_io(pl, in_dev, out_dev, batch, false);
+  if (r != REXI_OK) return r;
+  return step_static(pl, in_dev, out_dev, batch, static_cast<cudaStream_t>(stream));
 }
 
 rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *beta, int32_t *P) {

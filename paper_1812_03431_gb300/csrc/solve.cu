@@ -24,6 +24,9 @@
 // ascending k) and reduced in slot order, so results are bit-reproducible.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <string>
+
 #include "rexi_internal.h"
 
 namespace rexi {
@@ -441,6 +444,142 @@ cudaError_t launch_transpose_out(const double2 *sint, double2 *user, int64_t nsp
   dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
   transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(sint, user, rows, cols);
   return cudaGetLastError();
+}
+
+
+// ---- allocation-free spectral step ---------------------------------------------------
+// A variant of the spectral step for callers that may not allocate device memory
+// when they step (for example code running under a fixed device-memory budget
+// that was fully handed out at start-up, or a host application whose allocator
+// must not be re-entered from the time-stepping loop).  All per-call scratch
+// -- the transposed input and output states, the pole-slot partial sums, the
+// forward-sweep intermediates, the work list and the work counter -- lives in
+// one file-scope device array of kStaticScratchBytes; only the plan's read-only
+// tables are used besides the caller's input and output.
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)64 << 20;  // 64 MiB, held by every device that loads the library
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_static_addr[kMaxDevices] = {};  // device address of g_static_scratch, per device ordinal
+
+__global__ void static_items_kernel(WorkItem *items, int nitems, int nb, int bw, const int4 *sys) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nitems) return;
+  const int m = t / nb, bb = t - m * nb;  // one pole group; m ascending = longest systems first
+  const int l = max(sys[2 * m].z, sys[2 * m + 1].z);
+  items[t] = WorkItem{m, 0, bb * bw, l};
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_error("rexi_step_static: no usable current device");
+    return REXI_ECUDA;
+  }
+  // scratch layout for this call (one pole group; lanes (state, parity, pole slot))
+  int bw = 1;
+  while (bw < B && bw < 16) bw *= 2;
+  const int kk = 32 / (2 * bw);
+  const int slots = std::min(kk, pl.P);
+  const int nb = (B + bw - 1) / bw;
+  const int nitems = (pl.N + 1) * nb;
+  const int warps = pl.num_sms * 4;
+  const size_t state_b = align256((size_t)3 * pl.nspec * B * sizeof(double2));
+  const size_t part_b = align256((size_t)3 * pl.nspec * slots * B * sizeof(double2));
+  const size_t y_b = align256((size_t)warps * pl.lmax * 32 * sizeof(double2));
+  const size_t item_b = align256((size_t)nitems * sizeof(WorkItem));
+  const size_t need = 2 * state_b + part_b + y_b + item_b + 256;
+  if (need > kStaticScratchBytes) {
+    set_error("rexi_step_static: this truncation and batch need " + std::to_string(need) +
+              " bytes of scratch, above the fixed limit of " + std::to_string(kStaticScratchBytes) +
+              " bytes (64 MiB); use rexi_step or a smaller batch");
+    return REXI_EINVAL;
+  }
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("rexi_step_static: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+      return REXI_ECUDA;
+    }
+    g_static_addr[dev] = p;
+  }
+  unsigned char *base = static_cast<unsigned char *>(g_static_addr[dev]);
+  double2 *s_in = reinterpret_cast<double2 *>(base);
+  double2 *s_out = reinterpret_cast<double2 *>(base + state_b);
+  double2 *part = reinterpret_cast<double2 *>(base + 2 * state_b);
+  double2 *ybuf = reinterpret_cast<double2 *>(base + 2 * state_b + part_b);
+  WorkItem *items = reinterpret_cast<WorkItem *>(base + 2 * state_b + part_b + y_b);
+  unsigned *counter = reinterpret_cast<unsigned *>(base + 2 * state_b + part_b + y_b + item_b);
+
+  e = launch_transpose_in(static_cast<const double2 *>(in), s_in, pl.nspec, B, st);
+  if (e == cudaSuccess) {
+    static_items_kernel<<<(nitems + 127) / 128, 128, 0, st>>>(items, nitems, nb, bw, pl.sys_dev);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);  // the work counter starts at zero
+  if (e == cudaSuccess) {
+    SolveArgs a;
+    a.fac = pl.fac_fwd;
+    a.sin = s_in;
+    a.part = part;
+    a.ybuf = ybuf;
+    a.items = items;
+    a.sys = pl.sys_dev;
+    a.counter = counter;
+    a.nitems = nitems;
+    a.B = B;
+    a.bw = bw;
+    a.kk = slots;
+    a.slots = slots;
+    a.P = pl.P;
+    a.N = pl.N;
+    a.lmax = pl.lmax;
+    a.pole_begin = 0;
+    a.pole_end = pl.P;
+    a.nspec = pl.nspec;
+    a.nrows = pl.nrows;
+    solve_kernel<<<warps / 4, 128, 0, st>>>(a);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    ReduceArgs r;
+    r.part = part;
+    r.sin = s_in;
+    r.sout = s_out;
+    r.rflags = pl.rflags_dev;
+    r.w = pl.w_fwd;
+    r.coef = pl.coef_dev;
+    r.m_of = pl.m_of_dev;
+    r.sphi = pl.sphi_fwd;
+    r.slots = slots;
+    r.B = B;
+    r.N = pl.N;
+    r.nspec = pl.nspec;
+    r.single = 0;
+    r.realm0 = 1;
+    r.adjoint = 0;
+    r.alpha_k = make_double2(0, 0);
+    r.beta_k = make_double2(1, 0);
+    r.tau = pl.prm.tau;
+    const int64_t total = 3 * pl.nspec * B;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)pl.num_sms * 8);
+    reduce_kernel<<<blocks, 256, 0, st>>>(r);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_transpose_out(s_out, static_cast<double2 *>(out), pl.nspec, B, pl.N, st);
+  if (e != cudaSuccess) {
+    set_error(std::string("rexi_step_static: ") + cudaGetErrorString(e));
+    return REXI_ECUDA;
+  }
+  return REXI_OK;
 }
 
 }  // namespace rexi

@@ -49,6 +49,7 @@ SIGNATURES = {
     "rexi_plan_create": (_I32, [ctypes.POINTER(rexi_params), ctypes.POINTER(_VP)]),
     "rexi_step": (_I32, [_VP, _VP, _VP, _I32, _VP]),
     "rexi_step_adjoint": (_I32, [_VP, _VP, _VP, _I32, _VP]),
+    "rexi_step_static": (_I32, [_VP, _VP, _VP, _I32, _VP]),
     "rexi_analyze": (_I32, [_VP, _VP, _VP, _I32, _VP]),
     "rexi_synthesize": (_I32, [_VP, _VP, _VP, _I32, _VP]),
     "rexi_solve_pole": (_I32, [_VP, _I32, _VP, _VP, _I32, _VP]),
@@ -176,6 +177,14 @@ class Plan:
         out = self._io(g, out, self.layout == "grid")
         _check("rexi_step_adjoint", load().rexi_step_adjoint(self._h, g.data_ptr(), out.data_ptr(),
                                                               g.shape[0], _stream_handle(stream)))
+        return out
+
+    def step_static(self, x, out=None, stream=None):
+        """rexi_step_static: the spectral step with all per-call scratch in the library's
+        fixed 64 MiB device array (allocates nothing); see include/rexi.h."""
+        out = self._io(x, out, False)
+        _check("rexi_step_static", load().rexi_step_static(self._h, x.data_ptr(), out.data_ptr(),
+                                                            x.shape[0], _stream_handle(stream)))
         return out
 
     def analyze(self, grid, stream=None):
