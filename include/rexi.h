@@ -180,6 +180,12 @@ rexi_status rexi_plan_info(const rexi_plan *plan, int64_t *info, int32_t n);
 rexi_status rexi_profile_enable(rexi_plan *plan, int32_t max_calls);
 rexi_status rexi_profile_read(rexi_plan *plan, double *stage_ms, int32_t n, int32_t *calls);
 
+/* Synchronise the device and report whether any kernel of this plan gave up a
+ * bounded device-side wait (tensor-core completion barriers) since the last
+ * check: REXI_ETIMEOUT (and the flag is cleared) or REXI_OK.  Kernels that give
+ * up skip their outputs, free their tensor memory and return. */
+rexi_status rexi_check_device(rexi_plan *plan);
+
 /* Free everything the plan holds; NULL-safe.  The caller synchronises streams
  * that still use the plan first. */
 void rexi_destroy(rexi_plan *plan);

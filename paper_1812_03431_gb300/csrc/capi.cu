@@ -251,10 +251,6 @@ rexi_status rexi_plan_create(const rexi_params *prm, rexi_plan **out) {
       return REXI_EINVAL;
     }
   }
-  if (p.precision == REXI_MIXED) {
-    set_error("rexi_plan_create: REXI_MIXED is not available in this build");
-    return REXI_EINVAL;
-  }
   if (p.precision == REXI_MIXED && p.layout != REXI_GRID) {
     set_error("rexi_plan_create: REXI_MIXED applies to the grid layout (the spectral step is all FP64)");
     return REXI_EINVAL;
@@ -402,6 +398,22 @@ rexi_status rexi_profile_read(rexi_plan *plan, double *stage_ms, int32_t n, int3
   for (int s = 0; s < n && s < kStages; ++s) stage_ms[s] = acc[s];
   if (calls) *calls = pl.prof_calls;
   pl.prof_calls = 0;
+  return REXI_OK;
+}
+
+rexi_status rexi_check_device(rexi_plan *plan) {
+  if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
+  Plan &pl = *plan->pl;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail("rexi_check_device", e);
+  int flag = 0;
+  e = cudaMemcpy(&flag, pl.dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail("rexi_check_device", e);
+  if (flag) {
+    cudaMemset(pl.dev_err, 0, sizeof(int));
+    set_error("a bounded device-side wait expired; the affected outputs were not written");
+    return REXI_ETIMEOUT;
+  }
   return REXI_OK;
 }
 

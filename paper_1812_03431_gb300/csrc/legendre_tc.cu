@@ -1,17 +1,572 @@
-// Mixed-precision Legendre transforms on the tcgen05 tensor cores (3xTF32 split
-// products, FP32 accumulation).  Until these kernels are built, plans with
-// REXI_MIXED are rejected at creation.
+// Legendre transforms per zonal order m (paper Sec. 3) on the 5th-generation
+// tensor cores: tcgen05.mma kind::tf32 with 3xTF32 split products
+// (a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi) accumulated in FP32 in tensor memory.
+//
+// Analysis, per (m, parity p of n - m, tile of 128 degrees, group of G states):
+//   D1[n][8b + 2f + c] = sum_j Pbar_n(mu_j) X^{p}_f(j)      f in (Phi, U, V), c = re/im
+//   D2[n][4b + 2f + c] = sum_j H_n(mu_j)    X^{1-p}_f(j)    f in (U, V)
+//   with X^0 = F(mu_j) + F(-mu_j), X^1 = F(mu_j) - F(-mu_j) over the J northern
+//   latitudes (the FFT has already applied g w_j and cos w_j / (a (1 - mu^2))), and
+//   Phi = D1[Phi], zeta = i m D1[V] + D2[U], delta = i m D1[U] - D2[V].
+// Synthesis, per (m, tile of 128 northern latitudes, group of G states), for both
+// symmetry classes s:
+//   D1_s[j][8b + ...] = sum_{n: (n-m)%2 = s}   Pbar_n(mu_j) (Phi, psi', chi')_n
+//   D2_s[j][4b + ...] = sum_{n: (n-m)%2 = 1-s} H_n(mu_j)    (psi', chi')_n
+//   F_s(Phi) = D1_s[Phi], F_s(U) = -D2_s[psi'] + i m D1_s[chi'],
+//   F_s(V) = i m D1_s[psi'] + D2_s[chi'];  F(mu) = F_0 + F_1, F(-mu) = F_0 - F_1.
+//
+// Operands are staged in shared memory in the no-swizzle K-major canonical layout:
+// core matrices of 8 rows x 16 bytes (4 tf32), adjacent along K at LBO bytes and
+// along M/N at SBO = 128 bytes.  The tables come pre-split into TF32 hi/lo and
+// pre-packed in exactly that layout (plan time); the data are folded, split and
+// packed while staging.  One thread issues the MMAs; completion is tracked with an
+// mbarrier whose waits are bounded (on expiry the kernel records an error word,
+// skips its output and still frees its tensor memory).
 #include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
 
 #include "rexi_internal.h"
 
 namespace rexi {
 
-cudaError_t launch_leg_ana_tc(Plan &, const double2 *, double2 *, int, const double *, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+constexpr int TM = 128;              // rows (analysis: degrees; synthesis: latitudes) per tile
+constexpr int KB = 32;               // K per staged block (latitudes or degrees)
+constexpr int SUB = TM * KB * 4;     // bytes of one packed 128 x 32 tf32 sub-tile (16 KiB)
+constexpr unsigned kSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-cudaError_t launch_leg_syn_tc(Plan &, const double2 *, double2 *, int, const double *, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+// tcgen05 shared-memory matrix descriptor, SWIZZLE_NONE, K-major canonical layout.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of sm_100-family tensor cores
+  return d;                // base offset 0, absolute LBO mode 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor of kind::tf32: D F32, A and B TF32, both K-major, M x N.
+__device__ __forceinline__ uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_u32(mbar)));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+}
+
+// Bounded wait for the mbarrier phase with parity `par`; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t par) {
+  const uint32_t a = smem_u32(mbar);
+  for (unsigned it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(par));
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+// 4 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *v) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+  v[2] = __uint_as_float(r2);
+  v[3] = __uint_as_float(r3);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// x ~ hi + lo with hi, lo TF32
+__device__ __forceinline__ void split_tf32(double x, uint32_t &hi, uint32_t &lo) {
+  hi = to_tf32((float)x);
+  lo = to_tf32((float)(x - (double)__uint_as_float(hi)));
+}
+
+// byte offset of element (row r, k) in a packed K-major tile with `groups` 8-row groups
+__device__ __forceinline__ uint32_t core_off(int r, int k, int groups) {
+  return (uint32_t)(((k >> 2) * groups + (r >> 3)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+// Packs FP64 tables into TF32 hi/lo core-matrix sub-tiles.
+//   analysis:  for each (m, p, tile, kb): [P_hi, P_lo, H_hi, H_lo], rows = degrees
+//              n = m + p + 2 (tile*128 + r), K = latitudes j = kb*32 + k
+//   synthesis: for each (m, jt, kb): [P0_hi, P0_lo, P1_hi, P1_lo, H0_hi, H0_lo, H1_hi, H1_lo],
+//              rows = latitudes j = jt*128 + r, K = degree index i of parity q:
+//              n = m + q + 2 (kb*32 + k)
+struct PackArgs {
+  const double *tabP, *tabH;
+  uint32_t *dst;
+  const int64_t *blk_off;  // per (m, p or jt, tile) first block (in sub-tile-set units), analysis
+  int N, J, synth;
+  int64_t nblocks;         // total (m, ., tile, kb) blocks
+  const int4 *blk;         // per block: {m, p or jt, tile (ana) / 0, kb}
+};
+
+__global__ void pack_tables_kernel(PackArgs a) {
+  const int64_t b = blockIdx.x;
+  if (b >= a.nblocks) return;
+  const int4 info = a.blk[b];
+  const int m = info.x, pq = info.y, tile = info.z, kb = info.w;
+  const int N = a.N, J = a.J;
+  const int64_t idx0 = (int64_t)m * (2 * N + 3 - m) / 2;
+  const int nsub = a.synth ? 8 : 4;
+  uint32_t *out = a.dst + b * (int64_t)nsub * (SUB / 4);
+  for (int t = threadIdx.x; t < TM * KB; t += blockDim.x) {
+    const int r = t / KB, k = t - r * KB;
+    const uint32_t off = core_off(r, k, TM / 8) / 4;
+    if (!a.synth) {
+      const int n = m + pq + 2 * (tile * TM + r);
+      const int j = kb * KB + k;
+      double p = 0.0, h = 0.0;
+      if (n <= N && j < J) {
+        p = a.tabP[(idx0 + n - m) * J + j];
+        h = a.tabH[(idx0 + n - m) * J + j];
+      }
+      uint32_t hi, lo;
+      split_tf32(p, hi, lo);
+      out[0 * (SUB / 4) + off] = hi;
+      out[1 * (SUB / 4) + off] = lo;
+      split_tf32(h, hi, lo);
+      out[2 * (SUB / 4) + off] = hi;
+      out[3 * (SUB / 4) + off] = lo;
+    } else {
+      const int j = pq * TM + r;
+      for (int q = 0; q < 2; ++q) {
+        const int n = m + q + 2 * (kb * KB + k);
+        double p = 0.0, h = 0.0;
+        if (n <= N && j < J) {
+          p = a.tabP[(idx0 + n - m) * J + j];
+          h = a.tabH[(idx0 + n - m) * J + j];
+        }
+        uint32_t hi, lo;
+        split_tf32(p, hi, lo);
+        out[(2 * q + 0) * (SUB / 4) + off] = hi;
+        out[(2 * q + 1) * (SUB / 4) + off] = lo;
+        split_tf32(h, hi, lo);
+        out[(4 + 2 * q + 0) * (SUB / 4) + off] = hi;
+        out[(4 + 2 * q + 1) * (SUB / 4) + off] = lo;
+      }
+    }
+  }
+}
+
+struct TcArgs {
+  const uint32_t *tab;   // packed tables
+  const int4 *work;      // per CTA: {m, p (analysis) or jt (synthesis), tile, first packed block}
+  double2 *four;         // [nlat][N+1][3B]
+  double2 *sint;         // [3][nspec][B]
+  const double *zd;      // [nspec]
+  int *err;              // device error word
+  int N, nlat, J, B, G, nkb_fixed;
+  int64_t nspec;
+};
+
+// ---- analysis -------------------------------------------------------------------------
+// dynamic smem: [A: 4 x 16 KiB][B1 hi, B1 lo: 8G x 32 tf32 each][B2 hi, B2 lo: 4G x 32 each]
+__global__ void __launch_bounds__(128) leg_ana_tc_kernel(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int4 w = a.work[blockIdx.x];
+  const int m = w.x, p = w.y, tile = w.z;
+  const int64_t blk0 = w.w;
+  const int b0 = blockIdx.y * a.G;
+  const int G = a.G, N1 = 8 * G, N2 = 4 * G;
+  const int nkb = (a.J + KB - 1) / KB;
+  unsigned char *sA = sm;
+  unsigned char *sB1 = sm + 4 * SUB;
+  unsigned char *sB2 = sB1 + 2 * N1 * KB * 4;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(N1 + N2)) ncols <<= 1;
+  if (warp == 0) tmem_alloc(&tmem_base, ncols);
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  const int M1 = a.N + 1, ncol = 3 * a.B;
+  bool ok = true;
+  for (int kb = 0; kb < nkb; ++kb) {
+    // tables: a straight copy of the packed 64 KiB block
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.tab + (blk0 + kb) * (int64_t)(4 * SUB / 4));
+    uint4 *dstA = reinterpret_cast<uint4 *>(sA);
+    for (int t = tid; t < 4 * SUB / 16; t += blockDim.x) dstA[t] = src[t];
+    // data: fold, split, pack
+    for (int t = tid; t < KB * G * 3; t += blockDim.x) {
+      const int k = t / (G * 3), rem = t - k * (G * 3);
+      const int bl = rem / 3, f = rem - bl * 3;
+      const int j = kb * KB + k, b = b0 + bl;
+      double2 e = make_double2(0, 0), o = e;
+      if (j < a.J && b < a.B) {
+        const double2 x1 = a.four[((int64_t)j * M1 + m) * ncol + 3 * b + f];
+        const double2 x2 = a.four[((int64_t)(a.nlat - 1 - j) * M1 + m) * ncol + 3 * b + f];
+        e = make_double2(x1.x + x2.x, x1.y + x2.y);
+        o = make_double2(x1.x - x2.x, x1.y - x2.y);
+      }
+      const double2 vp = p ? o : e;  // class of Pbar_n
+      const double2 vh = p ? e : o;  // class of H_n
+      uint32_t hi, lo;
+      for (int c = 0; c < 2; ++c) {
+        const int col = 8 * bl + 2 * f + c;
+        const uint32_t off = core_off(col, k, N1 / 8);
+        split_tf32(c ? vp.y : vp.x, hi, lo);
+        *reinterpret_cast<uint32_t *>(sB1 + off) = hi;
+        *reinterpret_cast<uint32_t *>(sB1 + N1 * KB * 4 + off) = lo;
+      }
+      if (f > 0) {
+        for (int c = 0; c < 2; ++c) {
+          const int col = 4 * bl + 2 * (f - 1) + c;
+          const uint32_t off = core_off(col, k, N2 / 8);
+          split_tf32(c ? vh.y : vh.x, hi, lo);
+          *reinterpret_cast<uint32_t *>(sB2 + off) = hi;
+          *reinterpret_cast<uint32_t *>(sB2 + N2 * KB * 4 + off) = lo;
+        }
+      } else {
+        // zero padding columns 8 bl + 6, 8 bl + 7 of B1
+        for (int c = 6; c < 8; ++c) {
+          const uint32_t off = core_off(8 * bl + c, k, N1 / 8);
+          *reinterpret_cast<uint32_t *>(sB1 + off) = 0u;
+          *reinterpret_cast<uint32_t *>(sB1 + N1 * KB * 4 + off) = 0u;
+        }
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t idesc1 = make_idesc(TM, N1), idesc2 = make_idesc(TM, N2);
+      const uint32_t aP = smem_u32(sA), aPl = aP + SUB, aH = aP + 2 * SUB, aHl = aP + 3 * SUB;
+      const uint32_t b1 = smem_u32(sB1), b1l = b1 + N1 * KB * 4;
+      const uint32_t b2 = smem_u32(sB2), b2l = b2 + N2 * KB * 4;
+      const uint32_t lboA = (TM / 8) * 128, lbo1 = (N1 / 8) * 128, lbo2 = (N2 / 8) * 128;
+      for (int s = 0; s < KB / 8; ++s) {
+        const uint32_t oA = 2 * s * lboA, o1 = 2 * s * lbo1, o2 = 2 * s * lbo2;
+        const uint32_t first = (kb == 0 && s == 0) ? 0u : 1u;
+        // small products first, then hi * hi
+        mma_tf32(tbase, make_desc(aPl + oA, lboA, 128), make_desc(b1 + o1, lbo1, 128), idesc1, first);
+        mma_tf32(tbase, make_desc(aP + oA, lboA, 128), make_desc(b1l + o1, lbo1, 128), idesc1, 1u);
+        mma_tf32(tbase, make_desc(aP + oA, lboA, 128), make_desc(b1 + o1, lbo1, 128), idesc1, 1u);
+        mma_tf32(tbase + N1, make_desc(aHl + oA, lboA, 128), make_desc(b2 + o2, lbo2, 128), idesc2, first);
+        mma_tf32(tbase + N1, make_desc(aH + oA, lboA, 128), make_desc(b2l + o2, lbo2, 128), idesc2, 1u);
+        mma_tf32(tbase + N1, make_desc(aH + oA, lboA, 128), make_desc(b2 + o2, lbo2, 128), idesc2, 1u);
+      }
+      mma_commit(&mbar);
+    }
+    if (!mbar_wait(&mbar, (uint32_t)(kb & 1))) ok = false;
+    tc_fence_after();
+    ok = __syncthreads_and(ok) != 0;  // block-uniform, so every thread leaves the loop together
+    if (!ok) break;
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(a.err, 1);
+  } else {
+    // epilogue: TMEM lane = row of the tile (warp w owns lanes 32w .. 32w + 31)
+    const int r = tile * TM + warp * 32 + (tid & 31);
+    const int n = m + p + 2 * r;
+    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+    for (int bl = 0; bl < G; ++bl) {
+      float d1[8], d2[4];
+      tmem_ld4(lane_addr + 8 * bl, d1);
+      tmem_ld4(lane_addr + 8 * bl + 4, d1 + 4);
+      tmem_ld4(lane_addr + N1 + 4 * bl, d2);
+      const int b = b0 + bl;
+      if (n <= a.N && b < a.B) {
+        const int64_t ix = (int64_t)m * (2 * a.N + 3 - m) / 2 + (n - m);
+        const double s = a.zd[ix], fm = (double)m;
+        const double2 phi = make_double2(d1[0], d1[1]);
+        const double2 pu = make_double2(d1[2], d1[3]), pv = make_double2(d1[4], d1[5]);
+        const double2 hu = make_double2(d2[0], d2[1]), hv = make_double2(d2[2], d2[3]);
+        a.sint[ix * a.B + b] = phi;
+        a.sint[(a.nspec + ix) * a.B + b] = make_double2(s * (-fm * pv.y + hu.x), s * (fm * pv.x + hu.y));
+        a.sint[(2 * a.nspec + ix) * a.B + b] = make_double2(s * (-fm * pu.y - hv.x), s * (fm * pu.x - hv.y));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, ncols);
+}
+
+// ---- synthesis ------------------------------------------------------------------------
+// dynamic smem: [A: 8 x 16 KiB][B1_0, B1_1: (hi, lo) 8G x 32][B2_0, B2_1: (hi, lo) 4G x 32]
+__global__ void __launch_bounds__(128) leg_syn_tc_kernel(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int4 w = a.work[blockIdx.x];
+  const int m = w.x, jt = w.y;
+  const int64_t blk0 = w.w;
+  const int b0 = blockIdx.y * a.G;
+  const int G = a.G, N1 = 8 * G, N2 = 4 * G;
+  const int L0 = (a.N - m) / 2 + 1;                    // degrees with n - m even
+  const int L1 = (a.N - m - 1) >= 0 ? (a.N - m - 1) / 2 + 1 : 0;
+  const int nkb = (max(L0, L1) + KB - 1) / KB;
+  unsigned char *sA = sm;
+  unsigned char *sB1 = sm + 8 * SUB;                   // class s at sB1 + s * 2 * N1 * KB * 4
+  unsigned char *sB2 = sB1 + 2 * (2 * N1 * KB * 4);    // class s at sB2 + s * 2 * N2 * KB * 4
+  const int tid = threadIdx.x, warp = tid >> 5;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(2 * (N1 + N2))) ncols <<= 1;
+  if (warp == 0) tmem_alloc(&tmem_base, ncols);
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  const int64_t idx0 = (int64_t)m * (2 * a.N + 3 - m) / 2;
+  bool ok = true;
+  for (int kb = 0; kb < nkb; ++kb) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.tab + (blk0 + kb) * (int64_t)(8 * SUB / 4));
+    uint4 *dstA = reinterpret_cast<uint4 *>(sA);
+    for (int t = tid; t < 8 * SUB / 16; t += blockDim.x) dstA[t] = src[t];
+    // spectral data of both parities q: rows i = kb*32 + k, n = m + q + 2 i
+    for (int t = tid; t < 2 * KB * G * 3; t += blockDim.x) {
+      const int q = t / (KB * G * 3), rem0 = t - q * (KB * G * 3);
+      const int k = rem0 / (G * 3), rem = rem0 - k * (G * 3);
+      const int bl = rem / 3, f = rem - bl * 3;
+      const int n = m + q + 2 * (kb * KB + k), b = b0 + bl;
+      double2 v = make_double2(0, 0);
+      if (n <= a.N && b < a.B) {
+        const int64_t ix = idx0 + (n - m);
+        v = a.sint[((int64_t)f * a.nspec + ix) * a.B + b];
+        if (f > 0) {
+          const double s = a.zd[ix];
+          v = make_double2(s * v.x, s * v.y);
+        }
+      }
+      uint32_t hi, lo;
+      // P-terms of parity q feed class q (B1_q); H-terms feed class 1 - q (B2_{1-q})
+      unsigned char *b1 = sB1 + q * (2 * N1 * KB * 4);
+      for (int c = 0; c < 2; ++c) {
+        const uint32_t off = core_off(8 * bl + 2 * f + c, k, N1 / 8);
+        split_tf32(c ? v.y : v.x, hi, lo);
+        *reinterpret_cast<uint32_t *>(b1 + off) = hi;
+        *reinterpret_cast<uint32_t *>(b1 + N1 * KB * 4 + off) = lo;
+      }
+      if (f == 0) {
+        for (int c = 6; c < 8; ++c) {
+          const uint32_t off = core_off(8 * bl + c, k, N1 / 8);
+          *reinterpret_cast<uint32_t *>(b1 + off) = 0u;
+          *reinterpret_cast<uint32_t *>(b1 + N1 * KB * 4 + off) = 0u;
+        }
+      } else {
+        unsigned char *b2 = sB2 + (1 - q) * (2 * N2 * KB * 4);
+        for (int c = 0; c < 2; ++c) {
+          const uint32_t off = core_off(4 * bl + 2 * (f - 1) + c, k, N2 / 8);
+          split_tf32(c ? v.y : v.x, hi, lo);
+          *reinterpret_cast<uint32_t *>(b2 + off) = hi;
+          *reinterpret_cast<uint32_t *>(b2 + N2 * KB * 4 + off) = lo;
+        }
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t idesc1 = make_idesc(TM, N1), idesc2 = make_idesc(TM, N2);
+      const uint32_t lboA = (TM / 8) * 128, lbo1 = (N1 / 8) * 128, lbo2 = (N2 / 8) * 128;
+      const uint32_t A0 = smem_u32(sA);
+      for (int cls = 0; cls < 2; ++cls) {
+        // class cls: Pbar rows of parity cls with B1_cls; H rows of parity 1 - cls with B2_cls
+        const uint32_t aP = A0 + (2 * cls) * SUB, aPl = aP + SUB;
+        const uint32_t aH = A0 + (4 + 2 * (1 - cls)) * SUB, aHl = aH + SUB;
+        const uint32_t b1 = smem_u32(sB1 + cls * (2 * N1 * KB * 4)), b1l = b1 + N1 * KB * 4;
+        const uint32_t b2 = smem_u32(sB2 + cls * (2 * N2 * KB * 4)), b2l = b2 + N2 * KB * 4;
+        const uint32_t d1 = tbase + cls * (N1 + N2), d2 = d1 + N1;
+        for (int s = 0; s < KB / 8; ++s) {
+          const uint32_t oA = 2 * s * lboA, o1 = 2 * s * lbo1, o2 = 2 * s * lbo2;
+          const uint32_t first = (kb == 0 && s == 0) ? 0u : 1u;
+          mma_tf32(d1, make_desc(aPl + oA, lboA, 128), make_desc(b1 + o1, lbo1, 128), idesc1, first);
+          mma_tf32(d1, make_desc(aP + oA, lboA, 128), make_desc(b1l + o1, lbo1, 128), idesc1, 1u);
+          mma_tf32(d1, make_desc(aP + oA, lboA, 128), make_desc(b1 + o1, lbo1, 128), idesc1, 1u);
+          mma_tf32(d2, make_desc(aHl + oA, lboA, 128), make_desc(b2 + o2, lbo2, 128), idesc2, first);
+          mma_tf32(d2, make_desc(aH + oA, lboA, 128), make_desc(b2l + o2, lbo2, 128), idesc2, 1u);
+          mma_tf32(d2, make_desc(aH + oA, lboA, 128), make_desc(b2 + o2, lbo2, 128), idesc2, 1u);
+        }
+      }
+      mma_commit(&mbar);
+    }
+    if (!mbar_wait(&mbar, (uint32_t)(kb & 1))) ok = false;
+    tc_fence_after();
+    ok = __syncthreads_and(ok) != 0;  // block-uniform, so every thread leaves the loop together
+    if (!ok) break;
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(a.err, 1);
+  } else {
+    const int j = jt * TM + warp * 32 + (tid & 31);
+    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+    const int M1 = a.N + 1, ncol = 3 * a.B;
+    const double fm = (double)m;
+    for (int bl = 0; bl < G; ++bl) {
+      double2 F[2][3];
+      for (int cls = 0; cls < 2; ++cls) {
+        float d1[8], d2[4];
+        const uint32_t base = lane_addr + cls * (N1 + N2);
+        tmem_ld4(base + 8 * bl, d1);
+        tmem_ld4(base + 8 * bl + 4, d1 + 4);
+        tmem_ld4(base + N1 + 4 * bl, d2);
+        // d1: Phi re/im, psi' re/im, chi' re/im; d2: psi' re/im, chi' re/im (H-terms)
+        F[cls][0] = make_double2(d1[0], d1[1]);
+        F[cls][1] = make_double2(-(double)d2[0] - fm * d1[5], -(double)d2[1] + fm * d1[4]);
+        F[cls][2] = make_double2(-fm * d1[3] + d2[2], fm * d1[2] + d2[3]);
+      }
+      const int b = b0 + bl;
+      if (j < a.J && b < a.B) {
+        double2 *north = a.four + ((int64_t)j * M1 + m) * ncol + 3 * b;
+        double2 *south = a.four + ((int64_t)(a.nlat - 1 - j) * M1 + m) * ncol + 3 * b;
+        for (int f = 0; f < 3; ++f) {
+          north[f] = make_double2(F[0][f].x + F[1][f].x, F[0][f].y + F[1][f].y);
+          south[f] = make_double2(F[0][f].x - F[1][f].x, F[0][f].y - F[1][f].y);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, ncols);
+}
+
+int group_size(int B) { return std::min(B, 16) + (4 - std::min(B, 16) % 4) % 4; }
+
+size_t ana_smem(int G) { return 4 * (size_t)SUB + 2 * (8 * G) * KB * 4 + 2 * (4 * G) * KB * 4; }
+size_t syn_smem(int G) { return 8 * (size_t)SUB + 2 * (2 * (8 * G) * KB * 4) + 2 * (2 * (4 * G) * KB * 4); }
+
+}  // namespace
+
+// Plan-time: work lists and packed TF32 hi/lo tables for both directions.
+cudaError_t tc_setup(Plan &pl) {
+  const int N = pl.N, J = pl.J;
+  const int nkb_ana = (J + KB - 1) / KB;
+  std::vector<int4> work_a, blk_a, work_s, blk_s;
+  int64_t nb = 0;
+  for (int m = 0; m <= N; ++m)
+    for (int p = 0; p < 2; ++p) {
+      if (m + p > N) continue;
+      const int L = (N - m - p) / 2 + 1;
+      for (int t = 0; t * TM < L; ++t) {
+        work_a.push_back(make_int4(m, p, t, (int)nb));
+        for (int kb = 0; kb < nkb_ana; ++kb) blk_a.push_back(make_int4(m, p, t, kb));
+        nb += nkb_ana;
+      }
+    }
+  int64_t ns = 0;
+  const int njt = (J + TM - 1) / TM;
+  for (int m = 0; m <= N; ++m) {
+    const int L0 = (N - m) / 2 + 1, L1 = (N - m - 1) >= 0 ? (N - m - 1) / 2 + 1 : 0;
+    const int nkb = (std::max(L0, L1) + KB - 1) / KB;
+    for (int jt = 0; jt < njt; ++jt) {
+      work_s.push_back(make_int4(m, jt, 0, (int)ns));
+      for (int kb = 0; kb < nkb; ++kb) blk_s.push_back(make_int4(m, jt, 0, kb));
+      ns += nkb;
+    }
+  }
+  auto up = [&](const std::vector<int4> &v, int4 **d) -> cudaError_t {
+    cudaError_t e = cudaMalloc(d, std::max<size_t>(1, v.size()) * sizeof(int4));
+    if (e != cudaSuccess) return e;
+    pl.bytes += v.size() * sizeof(int4);
+    return cudaMemcpy(*d, v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  };
+  cudaError_t e;
+  int4 *blk_a_dev = nullptr, *blk_s_dev = nullptr;
+  if ((e = up(work_a, &pl.tc_work_ana))) return e;
+  if ((e = up(work_s, &pl.tc_work_syn))) return e;
+  if ((e = up(blk_a, &blk_a_dev))) return e;
+  if ((e = up(blk_s, &blk_s_dev))) return e;
+  pl.tc_nwork_ana = (int)work_a.size();
+  pl.tc_nwork_syn = (int)work_s.size();
+  const size_t bytes_a = (size_t)nb * 4 * SUB, bytes_s = (size_t)ns * 8 * SUB;
+  if ((e = cudaMalloc(&pl.tc_tab_ana, bytes_a))) return e;
+  if ((e = cudaMalloc(&pl.tc_tab_syn, bytes_s))) return e;
+  pl.bytes += bytes_a + bytes_s;
+  if ((e = cudaMalloc(&pl.dev_err, sizeof(int)))) return e;
+  cudaMemset(pl.dev_err, 0, sizeof(int));
+  PackArgs pa{pl.tabP, pl.tabH, pl.tc_tab_ana, nullptr, N, J, 0, nb, blk_a_dev};
+  pack_tables_kernel<<<(unsigned)nb, 256>>>(pa);
+  if ((e = cudaGetLastError())) return e;
+  PackArgs ps{pl.tabP, pl.tabH, pl.tc_tab_syn, nullptr, N, J, 1, ns, blk_s_dev};
+  pack_tables_kernel<<<(unsigned)ns, 256>>>(ps);
+  if ((e = cudaGetLastError())) return e;
+  e = cudaDeviceSynchronize();
+  cudaFree(blk_a_dev);
+  cudaFree(blk_s_dev);
+  if (e != cudaSuccess) return e;
+  const int Gmax = group_size(pl.prm.max_batch);
+  if ((e = cudaFuncSetAttribute(leg_ana_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ana_smem(Gmax))))
+    return e;
+  return cudaFuncSetAttribute(leg_syn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syn_smem(Gmax));
+}
+
+cudaError_t launch_leg_ana_tc(Plan &pl, const double2 *four, double2 *sint, int B, const double *zd,
+                              cudaStream_t st) {
+  const int G = group_size(B);
+  TcArgs a{pl.tc_tab_ana, pl.tc_work_ana, const_cast<double2 *>(four), sint, zd, pl.dev_err, pl.N, pl.nlat,
+           pl.J, B, G, 0, pl.nspec};
+  dim3 grid((unsigned)pl.tc_nwork_ana, (unsigned)((B + G - 1) / G));
+  leg_ana_tc_kernel<<<grid, 128, ana_smem(G), st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leg_syn_tc(Plan &pl, const double2 *sint, double2 *four, int B, const double *zd,
+                              cudaStream_t st) {
+  const int G = group_size(B);
+  TcArgs a{pl.tc_tab_syn, pl.tc_work_syn, four, const_cast<double2 *>(sint), zd, pl.dev_err, pl.N, pl.nlat,
+           pl.J, B, G, 0, pl.nspec};
+  dim3 grid((unsigned)pl.tc_nwork_syn, (unsigned)((B + G - 1) / G));
+  leg_syn_tc_kernel<<<grid, 128, syn_smem(G), st>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace rexi

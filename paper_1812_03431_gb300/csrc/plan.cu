@@ -15,6 +15,7 @@ namespace rexi {
 bool fft_factor(int n, int *radix, int *nstages);
 cudaError_t fft_configure(Plan &pl);
 cudaError_t legendre_configure();
+cudaError_t tc_setup(Plan &pl);
 
 namespace {
 
@@ -254,6 +255,13 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
     if ((e = legendre_configure())) return fail("legendre configure", e);
   }
 
+  if (prm.precision == REXI_MIXED) {
+    if ((e = tc_setup(*pl))) return fail("tensor-core tables", e);
+  } else {
+    if ((e = dalloc(&pl->dev_err, 1, &bytes))) return fail("error word", e);
+    cudaMemset(pl->dev_err, 0, sizeof(int));
+  }
+
   // ---- workspaces
   const int B = prm.max_batch;
   if ((e = dalloc(&pl->four, (size_t)pl->nlat * (N + 1) * 3 * B, &bytes))) return fail("fourier", e);
@@ -339,7 +347,9 @@ void free_plan(Plan *pl) {
                   pl->tabP_hi, pl->tabP_lo, pl->tabH_hi, pl->tabH_lo, pl->scale_ana_in,
                   pl->scale_syn_out, pl->mscale_fwd, pl->mscale_c, pl->mscale_adj, pl->mscale_one,
                   pl->zd_syn, pl->zd_ana_adj, pl->zd_one, pl->zd_mone, pl->fft.tw_dev, pl->four,
-                  pl->s_in, pl->s_out, pl->partial, pl->yscratch, pl->counter};
+                  pl->s_in, pl->s_out, pl->partial, pl->yscratch, pl->counter, pl->tc_tab_ana,
+                  pl->tc_tab_syn, pl->tc_work_ana, pl->tc_work_syn, pl->dev_err};
+  for (cudaEvent_t ev : pl->prof_ev) cudaEventDestroy(ev);
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto &kv : pl->layouts)

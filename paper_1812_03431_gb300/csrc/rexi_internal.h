@@ -106,6 +106,11 @@ struct Plan {
   double *zd_one = nullptr;         // [nspec]: 1
   double *zd_mone = nullptr;        // [nspec]: -1
   FftPlan fft{};
+  // mixed precision: packed TF32 hi/lo tables and per-CTA work lists of the tensor-core kernels
+  uint32_t *tc_tab_ana = nullptr, *tc_tab_syn = nullptr;
+  int4 *tc_work_ana = nullptr, *tc_work_syn = nullptr;
+  int tc_nwork_ana = 0, tc_nwork_syn = 0;
+  int *dev_err = nullptr;  // set by a kernel whose bounded wait expired
 
   // workspaces (max_batch)
   double2 *four = nullptr;     // [nlat][N+1][3 B] complex (FP64 or FP32 pairs in mixed mode)

@@ -57,6 +57,7 @@ SIGNATURES = {
     "rexi_plan_info": (_I32, [_VP, ctypes.POINTER(ctypes.c_int64), _I32]),
     "rexi_profile_enable": (_I32, [_VP, _I32]),
     "rexi_profile_read": (_I32, [_VP, _DP, _I32, ctypes.POINTER(_I32)]),
+    "rexi_check_device": (_I32, [_VP]),
     "rexi_destroy": (None, [_VP]),
     "rexi_last_error": (ctypes.c_char_p, []),
 }
@@ -223,6 +224,10 @@ class Plan:
         _check("rexi_plan_info", load().rexi_plan_info(self._h, v, 8))
         keys = ["N", "nspec", "P", "nlat", "nlon", "max_batch", "pole_slots", "device_bytes"]
         return dict(zip(keys, list(v)))
+
+    def check_device(self):
+        """Raise RexiError(REXI_ETIMEOUT) if a bounded device wait of this plan expired."""
+        _check("rexi_check_device", load().rexi_check_device(self._h))
 
     STAGES = ["fft_fwd", "leg_ana", "solve", "reduce", "leg_syn", "fft_inv", "transpose_in", "transpose_out"]
 
