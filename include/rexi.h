@@ -68,6 +68,7 @@ enum { REXI_GRID = 0,      /* rexi_step in/out are grid states */
        REXI_SPECTRAL = 1 }; /* rexi_step in/out are spectral states */
 
 typedef struct rexi_plan rexi_plan;
+typedef struct rexi_ragged rexi_ragged;
 
 /* Plan parameters.  Defaults (rexi_params_default): earth constants of
  * Sec. 6 (a = 6.37122e6 m, Omega = 7.292e-5 1/s, g = 9.80616 m/s^2,
@@ -166,9 +167,34 @@ rexi_status rexi_solve_pole(rexi_plan *plan, int32_t k, const void *in_dev, void
 /* Copy the plan's poles to host arrays of 2P doubles each; *P receives P. */
 rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *beta, int32_t *P);
 
+/* Autotuner (no paper counterpart; a tuning knob of this implementation): times
+ * the banded-solve kernel at this batch size for 1, 2, 4, ... pole groups (the
+ * number of partial sums per coefficient, which trades load balance against
+ * reduction traffic), keeps the fastest for later steps with this batch and
+ * writes the chosen slot count to *slots.  Synchronous; uses the plan's
+ * workspaces, so no step of this plan may be in flight. */
+rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots);
+
 /* Host-side description of a plan: writes up to 8 int64 values
  * {N, nspec, P, nlat, nlon, max_batch, pole_slots, device bytes held}. */
 rexi_status rexi_plan_info(const rexi_plan *plan, int64_t *info, int32_t n);
+
+/* Ragged batches (mixed truncations and pole counts): the banded solves of
+ * every state of several plans run as ONE persistent launch over the merged
+ * work list of (m, pole group, state group, plan) items sorted longest first
+ * (Sec. 5: every (pole, m) system is independent).  Plans must use
+ * REXI_SPECTRAL; the ragged object keeps pointers to them (destroy it first).
+ * rexi_ragged_step: in_dev[s], out_dev[s] are state s's [3][nspec_p] complex128
+ * device arrays (p = state_plan[s]); at most max_batch of plan p's states per
+ * call, nstates <= max_states.  A call with a new per-plan state count
+ * allocates its work list once; after that the call allocates nothing and can
+ * be captured in a CUDA graph.  Results equal each plan's rexi_step up to the
+ * summation order of the poles. */
+rexi_status rexi_ragged_create(rexi_plan *const *plans, int32_t nplans, int32_t max_states,
+                               rexi_ragged **out);
+rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *const *out_dev,
+                             const int32_t *state_plan, int32_t nstates, void *stream);
+void rexi_ragged_destroy(rexi_ragged *rg);
 
 /* Optional per-stage timing: with max_calls > 0 the next max_calls calls of
  * rexi_step / rexi_step_adjoint record CUDA events on their stream around each

@@ -19,6 +19,7 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl);
 rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out);
 void free_plan(Plan *pl);
 rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t st);
+rexi_status tune_layout(Plan &pl, int B, int *slots_out);
 
 namespace {
 
@@ -340,6 +341,16 @@ rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *
   }
   if (P) *P = pl.P;
   return REXI_OK;
+}
+
+rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots) {
+  if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
+  Plan &pl = *plan->pl;
+  if (batch < 1 || batch > pl.prm.max_batch) { set_error("rexi_tune: batch must be in [1, max_batch]"); return REXI_EINVAL; }
+  int s = 0;
+  rexi_status r = tune_layout(pl, batch, &s);
+  if (r == REXI_OK && slots) *slots = s;
+  return r;
 }
 
 rexi_status rexi_plan_info(const rexi_plan *plan, int64_t *info, int32_t n) {

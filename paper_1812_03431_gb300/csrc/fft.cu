@@ -26,50 +26,56 @@ namespace rexi {
 
 namespace {
 
+template <typename T> struct V2;
+template <> struct V2<double> { using t = double2; };
+template <> struct V2<float> { using t = float2; };
+template <typename T> __device__ __forceinline__ typename V2<T>::t mk(T x, T y) { return {x, y}; }
+
 struct FftArgs {
-  const double2 *tw;  // n twiddles e^{-2 pi i k / n} (n = nlon)
+  const void *tw;  // n twiddles e^{-2 pi i k / n} (n = nlon), double2 or float2
   int n, h, nstages, N, nlat, ncol, np;  // h = n / 2 complex points per row; np rows per CTA
   int radix[24];
   double c3, s3, c5a, s5a, c5b, s5b;  // cos/sin of 2pi/3, 2pi/5, 4pi/5
 };
 
-__device__ __forceinline__ double2 cmulz(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 addz(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 subz(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-// -i * a
-__device__ __forceinline__ double2 mulmi(double2 a) { return make_double2(a.y, -a.x); }
+template <typename C> __device__ __forceinline__ C cmulz(C a, C b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+template <typename C> __device__ __forceinline__ C addz(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C subz(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C mulmi(C a) { return {a.y, -a.x}; }  // -i a
 
-__device__ __forceinline__ void dft_small(double2 *v, int R, const FftArgs &a) {
+template <typename T>
+__device__ __forceinline__ void dft_small(typename V2<T>::t *v, int R, const FftArgs &a) {
+  using C = typename V2<T>::t;
   if (R == 2) {
-    double2 t = v[0];
+    C t = v[0];
     v[0] = addz(t, v[1]);
     v[1] = subz(t, v[1]);
   } else if (R == 4) {
-    double2 t0 = addz(v[0], v[2]), t1 = subz(v[0], v[2]);
-    double2 t2 = addz(v[1], v[3]), t3 = mulmi(subz(v[1], v[3]));
+    C t0 = addz(v[0], v[2]), t1 = subz(v[0], v[2]);
+    C t2 = addz(v[1], v[3]), t3 = mulmi(subz(v[1], v[3]));
     v[0] = addz(t0, t2);
     v[2] = subz(t0, t2);
     v[1] = addz(t1, t3);
     v[3] = subz(t1, t3);
   } else if (R == 3) {
-    double2 s = addz(v[1], v[2]);
-    double2 d = subz(v[1], v[2]);
-    double2 y0 = addz(v[0], s);
-    double2 t = make_double2(v[0].x + a.c3 * s.x, v[0].y + a.c3 * s.y);
-    double2 u = mulmi(make_double2(a.s3 * d.x, a.s3 * d.y));
+    const T c3 = (T)a.c3, s3 = (T)a.s3;
+    C s = addz(v[1], v[2]);
+    C d = subz(v[1], v[2]);
+    C y0 = addz(v[0], s);
+    C t = {v[0].x + c3 * s.x, v[0].y + c3 * s.y};
+    C u = mulmi(C{s3 * d.x, s3 * d.y});
     v[0] = y0;
     v[1] = addz(t, u);
     v[2] = subz(t, u);
   } else {  // R == 5
-    double2 b1 = addz(v[1], v[4]), b2 = addz(v[2], v[3]);
-    double2 d1 = subz(v[1], v[4]), d2 = subz(v[2], v[3]);
-    double2 y0 = addz(v[0], addz(b1, b2));
-    double2 t1 = make_double2(v[0].x + a.c5a * b1.x + a.c5b * b2.x, v[0].y + a.c5a * b1.y + a.c5b * b2.y);
-    double2 t2 = make_double2(v[0].x + a.c5b * b1.x + a.c5a * b2.x, v[0].y + a.c5b * b1.y + a.c5a * b2.y);
-    double2 u1 = mulmi(make_double2(a.s5a * d1.x + a.s5b * d2.x, a.s5a * d1.y + a.s5b * d2.y));
-    double2 u2 = mulmi(make_double2(a.s5b * d1.x - a.s5a * d2.x, a.s5b * d1.y - a.s5a * d2.y));
+    const T c5a = (T)a.c5a, s5a = (T)a.s5a, c5b = (T)a.c5b, s5b = (T)a.s5b;
+    C b1 = addz(v[1], v[4]), b2 = addz(v[2], v[3]);
+    C d1 = subz(v[1], v[4]), d2 = subz(v[2], v[3]);
+    C y0 = addz(v[0], addz(b1, b2));
+    C t1 = {v[0].x + c5a * b1.x + c5b * b2.x, v[0].y + c5a * b1.y + c5b * b2.y};
+    C t2 = {v[0].x + c5b * b1.x + c5a * b2.x, v[0].y + c5b * b1.y + c5a * b2.y};
+    C u1 = mulmi(C{s5a * d1.x + s5b * d2.x, s5a * d1.y + s5b * d2.y});
+    C u2 = mulmi(C{s5b * d1.x - s5a * d2.x, s5b * d1.y - s5a * d2.y});
     v[0] = y0;
     v[1] = addz(t1, u1);
     v[4] = subz(t1, u1);
@@ -78,11 +84,14 @@ __device__ __forceinline__ void dft_small(double2 *v, int R, const FftArgs &a) {
   }
 }
 
-// In-shared-memory forward FFT of np rows of length n; returns the buffer
-// holding the result (buf0 or buf1).
-__device__ double2 *fft_smem(double2 *buf0, double2 *buf1, const FftArgs &a) {
+// In-shared-memory forward FFT of np rows of h points; returns the buffer holding
+// the result (buf0 or buf1).
+template <typename T>
+__device__ typename V2<T>::t *fft_smem(typename V2<T>::t *buf0, typename V2<T>::t *buf1, const FftArgs &a) {
+  using C = typename V2<T>::t;
+  const C *tw = static_cast<const C *>(a.tw);
   const int n = a.h;
-  double2 *src = buf0, *dst = buf1;
+  C *src = buf0, *dst = buf1;
   int Ns = 1;
   for (int s = 0; s < a.nstages; ++s) {
     const int R = a.radix[s];
@@ -90,21 +99,21 @@ __device__ double2 *fft_smem(double2 *buf0, double2 *buf1, const FftArgs &a) {
     const int stride = n / (Ns * R);
     for (int t = threadIdx.x; t < a.np * nb; t += blockDim.x) {
       const int q = t / nb, jb = t - q * nb;
-      const double2 *in = src + q * n;
-      double2 *out = dst + q * n;
-      double2 v[5];
+      const C *in = src + q * n;
+      C *out = dst + q * n;
+      C v[5];
       const int jm = jb % Ns;
       for (int r = 0; r < R; ++r) {
-        double2 x = in[jb + r * nb];
-        if (r > 0 && jm > 0) x = cmulz(x, __ldg(a.tw + 2 * r * jm * stride));
+        C x = in[jb + r * nb];
+        if (r > 0 && jm > 0) x = cmulz(x, tw[2 * r * jm * stride]);
         v[r] = x;
       }
-      dft_small(v, R, a);
+      dft_small<T>(v, R, a);
       const int od = (jb / Ns) * Ns * R + jm;
       for (int r = 0; r < R; ++r) out[od + r * Ns] = v[r];
     }
     __syncthreads();
-    double2 *tmp = src;
+    C *tmp = src;
     src = dst;
     dst = tmp;
     Ns *= R;
@@ -112,92 +121,101 @@ __device__ double2 *fft_smem(double2 *buf0, double2 *buf1, const FftArgs &a) {
   return src;
 }
 
+// T: arithmetic type inside the transform (double, or float in the mixed form);
+// grid and Fourier arrays stay FP64 either way.
+template <typename T>
 __global__ void fft_fwd_kernel(FftArgs a, const double *grid, double2 *four, const double *in_scale,
                                const double *m_scale) {
-  extern __shared__ double2 sm[];
+  using C = typename V2<T>::t;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C *sm = reinterpret_cast<C *>(smraw);
+  const C *tw = static_cast<const C *>(a.tw);
   const int h = a.h;
-  double2 *buf0 = sm, *buf1 = sm + a.np * h;
+  C *buf0 = sm, *buf1 = sm + a.np * h;
   const int j = blockIdx.y;
   const int c0 = blockIdx.x * a.np;
   const double2 *g2 = reinterpret_cast<const double2 *>(grid);
   for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
     const int q = t / h, k = t - q * h;
     const int c = c0 + q;
-    double2 v = make_double2(0.0, 0.0);
+    C v = {0, 0};
     if (c < a.ncol) {
       const double s = in_scale[(c % 3) * a.nlat + j];
-      v = g2[((int64_t)c * a.nlat + j) * h + k];
-      v = make_double2(s * v.x, s * v.y);
+      const double2 x = g2[((int64_t)c * a.nlat + j) * h + k];
+      v = C{(T)(s * x.x), (T)(s * x.y)};
     }
     buf0[t] = v;
   }
   __syncthreads();
-  const double2 *Z = fft_smem(buf0, buf1, a);
+  const C *Z = fft_smem<T>(buf0, buf1, a);
   const int M1 = a.N + 1;
   for (int t = threadIdx.x; t < a.np * M1; t += blockDim.x) {
     const int m = t / a.np, q = t - m * a.np;
     const int c = c0 + q;
     if (c >= a.ncol) continue;
-    const double2 zm = Z[q * h + m];
-    const double2 zr = Z[q * h + (m == 0 ? 0 : h - m)];
+    const C zm = Z[q * h + m];
+    const C zr = Z[q * h + (m == 0 ? 0 : h - m)];
     // E = (Z_m + conj Z_{h-m}) / 2,  O = (Z_m - conj Z_{h-m}) / (2 i)
-    const double2 E = make_double2(0.5 * (zm.x + zr.x), 0.5 * (zm.y - zr.y));
-    const double2 O = make_double2(0.5 * (zm.y + zr.y), -0.5 * (zm.x - zr.x));
-    const double2 w = __ldg(a.tw + m);
-    const double2 X = addz(E, cmulz(w, O));
+    const C E = {(T)0.5 * (zm.x + zr.x), (T)0.5 * (zm.y - zr.y)};
+    const C O = {(T)0.5 * (zm.y + zr.y), (T)-0.5 * (zm.x - zr.x)};
+    const C X = addz(E, cmulz(tw[m], O));
     const double s = m_scale[m];
-    four[((int64_t)j * M1 + m) * a.ncol + c] = make_double2(s * X.x, s * X.y);
+    four[((int64_t)j * M1 + m) * a.ncol + c] = make_double2(s * (double)X.x, s * (double)X.y);
   }
 }
 
+template <typename T>
 __global__ void fft_inv_kernel(FftArgs a, const double2 *four, double *grid, const double *m_scale,
                                const double *out_scale) {
-  extern __shared__ double2 sm[];
+  using C = typename V2<T>::t;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C *sm = reinterpret_cast<C *>(smraw);
+  const C *tw = static_cast<const C *>(a.tw);
   const int h = a.h;
-  double2 *buf0 = sm, *buf1 = sm + a.np * h;
+  C *buf0 = sm, *buf1 = sm + a.np * h;
   const int j = blockIdx.y;
   const int c0 = blockIdx.x * a.np;
   const int N = a.N, M1 = N + 1;
   for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
     const int q = t / h, m = t - q * h;
     const int c = c0 + q;
-    double2 A = make_double2(0, 0), Bc = make_double2(0, 0);
+    C A = {0, 0}, Bc = {0, 0};
     if (c < a.ncol) {
       if (m <= N) {
         const double s = m_scale[m];
         const double2 v = four[((int64_t)j * M1 + m) * a.ncol + c];
-        A = make_double2(s * v.x, m == 0 ? 0.0 : s * v.y);
+        A = C{(T)(s * v.x), m == 0 ? (T)0 : (T)(s * v.y)};
       }
       const int mr = h - m;  // partner X_{h-m}, present when h - m <= N
       if (m > 0 && mr <= N) {
         const double s = m_scale[mr];
         const double2 v = four[((int64_t)j * M1 + mr) * a.ncol + c];
-        Bc = make_double2(s * v.x, mr == 0 ? 0.0 : -s * v.y);  // conj(X_{h-m})
+        Bc = C{(T)(s * v.x), mr == 0 ? (T)0 : (T)(-s * v.y)};  // conj(X_{h-m})
       }
     }
     // E' = X_m + conj X_{h-m},  O' = (X_m - conj X_{h-m}) e^{+2 pi i m / n},  Z' = E' + i O'
-    const double2 E = addz(A, Bc);
-    const double2 w = __ldg(a.tw + m);
-    const double2 O = cmulz(subz(A, Bc), make_double2(w.x, -w.y));
-    const double2 Zp = make_double2(E.x - O.y, E.y + O.x);
-    buf0[t] = make_double2(Zp.x, -Zp.y);  // conj(Z') for the inverse by a forward FFT
+    const C E = addz(A, Bc);
+    const C w = tw[m];
+    const C O = cmulz(subz(A, Bc), C{w.x, -w.y});
+    const C Zp = {E.x - O.y, E.y + O.x};
+    buf0[t] = C{Zp.x, -Zp.y};  // conj(Z') for the inverse by a forward FFT
   }
   __syncthreads();
-  const double2 *r = fft_smem(buf0, buf1, a);
+  const C *r = fft_smem<T>(buf0, buf1, a);
   double2 *g2 = reinterpret_cast<double2 *>(grid);
   for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
     const int q = t / h, k = t - q * h;
     const int c = c0 + q;
     if (c >= a.ncol) continue;
     const double s = out_scale[(c % 3) * a.nlat + j];
-    const double2 v = r[t];  // conj of z_k = x_{2k} + i x_{2k+1}
-    g2[((int64_t)c * a.nlat + j) * h + k] = make_double2(s * v.x, -s * v.y);
+    const C v = r[t];  // conj of z_k = x_{2k} + i x_{2k+1}
+    g2[((int64_t)c * a.nlat + j) * h + k] = make_double2(s * (double)v.x, -s * (double)v.y);
   }
 }
 
 FftArgs make_args(const Plan &pl, int B) {
   FftArgs a;
-  a.tw = static_cast<const double2 *>(pl.fft.tw_dev);
+  a.tw = pl.prm.precision == REXI_MIXED ? pl.fft.tw32_dev : pl.fft.tw_dev;
   a.n = pl.fft.n;
   a.h = pl.fft.n / 2;
   a.nstages = pl.fft.nstages;
@@ -228,14 +246,20 @@ bool fft_factor(int n, int *radix, int *nstages) {
   return m == 1 && k < 24;
 }
 
-size_t fft_smem_bytes(const Plan &pl) { return (size_t)pl.fft.nsplit * pl.fft.n * sizeof(double2); }
+bool fft32(const Plan &pl) { return pl.prm.precision == REXI_MIXED; }
+size_t fft_smem_bytes(const Plan &pl) {
+  return (size_t)pl.fft.nsplit * pl.fft.n * (fft32(pl) ? sizeof(float2) : sizeof(double2));
+}
 
 cudaError_t launch_fft_fwd(Plan &pl, const double *grid, double2 *four, int B, const double *in_scale,
                            const double *m_scale, cudaStream_t st) {
   FftArgs a = make_args(pl, B);
   dim3 g((unsigned)((a.ncol + a.np - 1) / a.np), (unsigned)pl.nlat);
   size_t sm = fft_smem_bytes(pl);
-  fft_fwd_kernel<<<g, 256, sm, st>>>(a, grid, four, in_scale, m_scale);
+  if (fft32(pl))
+    fft_fwd_kernel<float><<<g, 256, sm, st>>>(a, grid, four, in_scale, m_scale);
+  else
+    fft_fwd_kernel<double><<<g, 256, sm, st>>>(a, grid, four, in_scale, m_scale);
   return cudaGetLastError();
 }
 
@@ -244,16 +268,22 @@ cudaError_t launch_fft_inv(Plan &pl, const double2 *four, double *grid, int B, c
   FftArgs a = make_args(pl, B);
   dim3 g((unsigned)((a.ncol + a.np - 1) / a.np), (unsigned)pl.nlat);
   size_t sm = fft_smem_bytes(pl);
-  fft_inv_kernel<<<g, 256, sm, st>>>(a, four, grid, m_scale, out_scale);
+  if (fft32(pl))
+    fft_inv_kernel<float><<<g, 256, sm, st>>>(a, four, grid, m_scale, out_scale);
+  else
+    fft_inv_kernel<double><<<g, 256, sm, st>>>(a, four, grid, m_scale, out_scale);
   return cudaGetLastError();
 }
 
 cudaError_t fft_configure(Plan &pl) {
-  cudaError_t e = cudaFuncSetAttribute(fft_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)fft_smem_bytes(pl));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fft_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)fft_smem_bytes(pl));
+  const int bytes = (int)fft_smem_bytes(pl);
+  cudaError_t e;
+  if (fft32(pl)) {
+    if ((e = cudaFuncSetAttribute(fft_fwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    return cudaFuncSetAttribute(fft_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  }
+  if ((e = cudaFuncSetAttribute(fft_fwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+  return cudaFuncSetAttribute(fft_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace rexi

@@ -251,6 +251,11 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
     double2 *twd = nullptr;
     if ((e = upload(&twd, tw, &bytes))) return fail("twiddles", e);
     f.tw_dev = twd;
+    std::vector<float2> tw32(f.n);
+    for (int k = 0; k < f.n; ++k) tw32[k] = make_float2((float)tw[k].x, (float)tw[k].y);
+    float2 *tw32d = nullptr;
+    if ((e = upload(&tw32d, tw32, &bytes))) return fail("twiddles", e);
+    f.tw32_dev = tw32d;
     if ((e = fft_configure(*pl))) return fail("fft configure", e);
     if ((e = legendre_configure())) return fail("legendre configure", e);
   }
@@ -281,26 +286,21 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   return REXI_OK;
 }
 
-// Work list for batch B: items (m, slot group, first state), longest first.
-rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out) {
-  const int key = single ? -B : B;
-  auto it = pl.layouts.find(key);
-  if (it != pl.layouts.end()) {
-    *out = &it->second;
-    return REXI_OK;
-  }
-  SolveLayout L;
+// Work list for batch B with a given number of pole groups (0: heuristic):
+// items (m, slot group, first state), longest first.
+rexi_status build_layout(Plan &pl, int B, bool single, int groups_req, SolveLayout &L) {
+  L = SolveLayout{};
   L.batch = B;
   int bw = 1;
   while (bw < B && bw < 16) bw *= 2;
   L.bw = bw;
-  int slots_cap = (int)pl.partial_cap;
+  const int slots_cap = (int)pl.partial_cap;
   // lanes kk >= L.kk stay idle, so slots = groups * kk never exceeds the partial buffer
   L.kk = single ? 1 : std::min(32 / (2 * bw), slots_cap);
   if (single) {
     L.groups = 1;
-  } else if (pl.slots_override > 0) {
-    L.groups = std::max(1, std::min(pl.slots_override, slots_cap) / L.kk);
+  } else if (groups_req > 0) {
+    L.groups = std::max(1, std::min(groups_req, slots_cap / L.kk));
   } else {
     // enough items that the longest fits ~1/2 of a warp's fair share of the work
     const int nb = (B + bw - 1) / bw;
@@ -335,8 +335,72 @@ rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out) {
     return REXI_ENOMEM;
   }
   cudaMemcpy(L.items_dev, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+  return REXI_OK;
+}
+
+rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out) {
+  const int key = single ? -B : B;
+  auto it = pl.layouts.find(key);
+  if (it != pl.layouts.end()) {
+    *out = &it->second;
+    return REXI_OK;
+  }
+  SolveLayout L;
+  rexi_status r = build_layout(pl, B, single, single ? 1 : pl.slots_override, L);
+  if (r != REXI_OK) return r;
   auto res = pl.layouts.emplace(key, L);
   *out = &res.first->second;
+  return REXI_OK;
+}
+
+// Autotuner: time the solve kernel for each candidate number of pole groups at
+// batch B and keep the fastest layout for later steps with that batch.
+rexi_status tune_layout(Plan &pl, int B, int *slots_out) {
+  cudaStream_t st = 0;
+  cudaError_t e = cudaMemsetAsync(pl.s_in, 0, (size_t)3 * pl.nspec * B * sizeof(double2), st);
+  if (e != cudaSuccess) {
+    set_error(std::string("tune: ") + cudaGetErrorString(e));
+    return REXI_ECUDA;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  SolveLayout bestL{};
+  std::vector<int> tried;
+  for (int g = 1; g <= 256; g *= 2) {
+    SolveLayout L;
+    rexi_status r = build_layout(pl, B, false, g, L);
+    if (r != REXI_OK) return r;
+    if (std::find(tried.begin(), tried.end(), L.slots) != tried.end()) {
+      cudaFree(L.items_dev);
+      continue;
+    }
+    tried.push_back(L.slots);
+    launch_solve(pl, L, false, pl.s_in, B, 0, pl.P, true, st);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 2; ++rep) launch_solve(pl, L, false, pl.s_in, B, 0, pl.P, true, st);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && ms < best) {
+      if (bestL.items_dev) cudaFree(bestL.items_dev);
+      best = ms;
+      bestL = L;
+    } else {
+      cudaFree(L.items_dev);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  auto it = pl.layouts.find(B);
+  if (it != pl.layouts.end()) {
+    cudaFree(it->second.items_dev);
+    pl.layouts.erase(it);
+  }
+  pl.layouts.emplace(B, bestL);
+  if (slots_out) *slots_out = bestL.slots;
   return REXI_OK;
 }
 
@@ -346,7 +410,7 @@ void free_plan(Plan *pl) {
                   pl->beta_dev, pl->w_fwd, pl->w_adj, pl->rflags_dev, pl->mu_dev, pl->tabP, pl->tabH,
                   pl->tabP_hi, pl->tabP_lo, pl->tabH_hi, pl->tabH_lo, pl->scale_ana_in,
                   pl->scale_syn_out, pl->mscale_fwd, pl->mscale_c, pl->mscale_adj, pl->mscale_one,
-                  pl->zd_syn, pl->zd_ana_adj, pl->zd_one, pl->zd_mone, pl->fft.tw_dev, pl->four,
+                  pl->zd_syn, pl->zd_ana_adj, pl->zd_one, pl->zd_mone, pl->fft.tw_dev, pl->fft.tw32_dev, pl->four,
                   pl->s_in, pl->s_out, pl->partial, pl->yscratch, pl->counter, pl->tc_tab_ana,
                   pl->tc_tab_syn, pl->tc_work_ana, pl->tc_work_syn, pl->dev_err};
   for (cudaEvent_t ev : pl->prof_ev) cudaEventDestroy(ev);

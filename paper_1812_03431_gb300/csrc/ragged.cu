@@ -1,0 +1,187 @@
+// Ragged batches: states of several plans (mixed truncations N and pole counts P)
+// whose banded solves run as ONE persistent launch over the union of their work
+// items, sorted longest first (the per-item plan index selects factors, layout and
+// buffers).  Inputs are gathered into each plan's internal layout and results
+// scattered back by small per-state kernels; after a first call with the same
+// per-plan state counts nothing is allocated, so the step can be captured in a
+// CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "rexi_internal.h"
+
+struct rexi_plan {
+  rexi::Plan *pl;
+};
+
+namespace rexi {
+rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out);
+}
+
+struct rexi_ragged {
+  std::vector<rexi::Plan *> plans;
+  int max_states = 0, lmax = 1, resident_warps = 0;
+  double2 *ybuf = nullptr;
+  unsigned *counter = nullptr;
+  struct Cfg {
+    rexi::SolveView *views_dev = nullptr;
+    rexi::WorkItem *items_dev = nullptr;
+    int nitems = 0;
+  };
+  std::map<std::vector<int>, Cfg> cfgs;
+};
+
+namespace rexi {
+namespace {
+
+// s_int[(f * nspec + idx) * B + b] <-> state[f * nspec + idx]
+__global__ void gather_state_kernel(const double2 *state, double2 *sint, int64_t n3, int B, int b) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += (int64_t)gridDim.x * blockDim.x)
+    sint[t * B + b] = state[t];
+}
+__global__ void scatter_state_kernel(const double2 *sint, double2 *state, int64_t n3, int B, int b) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += (int64_t)gridDim.x * blockDim.x)
+    state[t] = sint[t * B + b];
+}
+
+rexi_status fail(const std::string &what, cudaError_t e) {
+  set_error("ragged: " + what + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? REXI_ENOMEM : REXI_ECUDA;
+}
+
+}  // namespace
+}  // namespace rexi
+
+using namespace rexi;
+
+extern "C" {
+
+rexi_status rexi_ragged_create(rexi_plan *const *plans, int32_t nplans, int32_t max_states, rexi_ragged **out) {
+  if (!out || !plans || nplans < 1 || max_states < 1) {
+    set_error("rexi_ragged_create: need plans, nplans >= 1, max_states >= 1");
+    return REXI_EINVAL;
+  }
+  *out = nullptr;
+  rexi_ragged *rg = new rexi_ragged();
+  rg->max_states = max_states;
+  for (int i = 0; i < nplans; ++i) {
+    if (!plans[i] || !plans[i]->pl || plans[i]->pl->prm.layout != REXI_SPECTRAL) {
+      delete rg;
+      set_error("rexi_ragged_create: every plan must exist and use REXI_SPECTRAL");
+      return REXI_EINVAL;
+    }
+    rg->plans.push_back(plans[i]->pl);
+    rg->lmax = std::max(rg->lmax, plans[i]->pl->lmax);
+    rg->resident_warps = std::max(rg->resident_warps, plans[i]->pl->resident_warps);
+  }
+  cudaError_t e = cudaMalloc(&rg->ybuf, (size_t)rg->resident_warps * rg->lmax * 32 * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&rg->counter, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    rexi_ragged_destroy(rg);
+    return fail("allocation", e);
+  }
+  *out = rg;
+  return REXI_OK;
+}
+
+rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *const *out_dev,
+                             const int32_t *state_plan, int32_t nstates, void *stream) {
+  if (!rg || !in_dev || !out_dev || !state_plan || nstates < 1 || nstates > rg->max_states) {
+    set_error("rexi_ragged_step: bad arguments or nstates > max_states");
+    return REXI_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int np = (int)rg->plans.size();
+  std::vector<int> counts(np, 0), rank(nstates);
+  for (int s = 0; s < nstates; ++s) {
+    const int p = state_plan[s];
+    if (p < 0 || p >= np || !in_dev[s] || !out_dev[s]) {
+      set_error("rexi_ragged_step: state " + std::to_string(s) + " has a bad plan index or pointer");
+      return REXI_EINVAL;
+    }
+    rank[s] = counts[p]++;
+  }
+  for (int p = 0; p < np; ++p)
+    if (counts[p] > rg->plans[p]->prm.max_batch) {
+      set_error("rexi_ragged_step: more states for plan " + std::to_string(p) + " than its max_batch");
+      return REXI_EINVAL;
+    }
+  // per-plan layouts and the merged work list (cached per count vector)
+  std::vector<SolveLayout *> lays(np, nullptr);
+  for (int p = 0; p < np; ++p)
+    if (counts[p] > 0) {
+      rexi_status r = get_layout(*rg->plans[p], counts[p], false, &lays[p]);
+      if (r != REXI_OK) return r;
+    }
+  auto it = rg->cfgs.find(counts);
+  if (it == rg->cfgs.end()) {
+    std::vector<SolveView> views(np);
+    struct Tagged { WorkItem w; double work; };
+    std::vector<Tagged> all;
+    for (int p = 0; p < np; ++p) {
+      if (counts[p] == 0) continue;
+      Plan &pl = *rg->plans[p];
+      const SolveLayout &L = *lays[p];
+      views[p] = make_view(pl, L, false, pl.s_in, pl.partial, counts[p], 0, pl.P);
+      const int nb = (counts[p] + L.bw - 1) / L.bw;
+      const double per_slot = (double)((pl.P + L.slots - 1) / L.slots);
+      for (int m = 0; m <= pl.N; ++m) {
+        const int l = std::max(pl.sys[2 * m].len, pl.sys[2 * m + 1].len);
+        if (l == 0) continue;
+        for (int g = 0; g < L.groups; ++g)
+          for (int bb = 0; bb < nb; ++bb) all.push_back(Tagged{WorkItem{m, g, bb * L.bw, p}, l * per_slot});
+      }
+    }
+    std::stable_sort(all.begin(), all.end(), [](const Tagged &x, const Tagged &y) { return x.work > y.work; });
+    std::vector<WorkItem> items;
+    for (const Tagged &t : all) items.push_back(t.w);
+    rexi_ragged::Cfg cfg;
+    cfg.nitems = (int)items.size();
+    cudaError_t e = cudaMalloc(&cfg.views_dev, views.size() * sizeof(SolveView));
+    if (e == cudaSuccess) e = cudaMalloc(&cfg.items_dev, std::max<size_t>(1, items.size()) * sizeof(WorkItem));
+    if (e == cudaSuccess) e = cudaMemcpy(cfg.views_dev, views.data(), views.size() * sizeof(SolveView), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cfg.items_dev, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail("work list", e);
+    it = rg->cfgs.emplace(counts, cfg).first;
+  }
+  const rexi_ragged::Cfg &cfg = it->second;
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < nstates && e == cudaSuccess; ++s) {
+    Plan &pl = *rg->plans[state_plan[s]];
+    const int64_t n3 = 3 * pl.nspec;
+    gather_state_kernel<<<(unsigned)std::min<int64_t>((n3 + 255) / 256, 1024), 256, 0, st>>>(
+        static_cast<const double2 *>(in_dev[s]), pl.s_in, n3, counts[state_plan[s]], rank[s]);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = launch_solve_ragged(cfg.views_dev, cfg.items_dev, cfg.nitems, rg->ybuf, rg->lmax, rg->counter,
+                            rg->resident_warps, st);
+  for (int p = 0; p < np && e == cudaSuccess; ++p)
+    if (counts[p] > 0)
+      e = launch_reduce(*rg->plans[p], *lays[p], false, rg->plans[p]->s_in, rg->plans[p]->s_out, counts[p], false, 0, st);
+  for (int s = 0; s < nstates && e == cudaSuccess; ++s) {
+    Plan &pl = *rg->plans[state_plan[s]];
+    const int64_t n3 = 3 * pl.nspec;
+    scatter_state_kernel<<<(unsigned)std::min<int64_t>((n3 + 255) / 256, 1024), 256, 0, st>>>(
+        pl.s_out, static_cast<double2 *>(out_dev[s]), n3, counts[state_plan[s]], rank[s]);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? REXI_OK : fail("launch", e);
+}
+
+void rexi_ragged_destroy(rexi_ragged *rg) {
+  if (!rg) return;
+  for (auto &kv : rg->cfgs) {
+    if (kv.second.views_dev) cudaFree(kv.second.views_dev);
+    if (kv.second.items_dev) cudaFree(kv.second.items_dev);
+  }
+  if (rg->ybuf) cudaFree(rg->ybuf);
+  if (rg->counter) cudaFree(rg->counter);
+  delete rg;
+}
+
+}  // extern "C"

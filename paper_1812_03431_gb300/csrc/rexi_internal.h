@@ -59,7 +59,8 @@ struct FftPlan {
   int nstages;
   int radix[24];
   int nsplit;     // rows per CTA (pairs of real rows packed as one complex row)
-  void *tw_dev;   // n twiddles e^{-2 pi i k/n} in the plan's precision
+  void *tw_dev;   // n twiddles e^{-2 pi i k/n}, double2
+  void *tw32_dev; // the same as float2 (mixed form)
 };
 
 enum FacComp { F_L = 0, F_G, F_E, F_F, F_C, F_BD, F_BAD, F_ZP, F_ZM, F_NCOMP };
@@ -140,6 +141,20 @@ enum Stage { ST_FFT_FWD = 0, ST_LEG_ANA, ST_SOLVE, ST_REDUCE, ST_LEG_SYN, ST_FFT
 cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st);
 cudaError_t launch_solve(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin,
                          int B, int pole_begin, int pole_end, bool use_beta, cudaStream_t st);
+// One plan's view for the solve kernels: factors, internal states, partial sums,
+// systems and the lane layout of its batch.
+struct SolveView {
+  const double2 *fac;   // [F_NCOMP][nrows][P]
+  const double2 *sin;   // [3][nspec][B]
+  double2 *part;        // [3][nspec][slots][B]
+  const int4 *sys;      // per (m, p): {m, n0, len, row0}
+  int P, N, B, bw, kk, slots, pole_begin, pole_end;
+  int64_t nspec, nrows;
+};
+SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, double2 *part, int B,
+                    int pole_begin, int pole_end);
+cudaError_t launch_solve_ragged(const SolveView *views_dev, const WorkItem *items, int nitems, double2 *ybuf,
+                                int lmax, unsigned *counter, int resident_warps, cudaStream_t st);
 cudaError_t launch_reduce(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin,
                           double2 *sout, int B, bool single_pole, int pole, cudaStream_t st);
 cudaError_t launch_transpose_in(const double2 *user, double2 *sint, int64_t nspec, int B,

@@ -185,103 +185,134 @@ __global__ void factor_setup_kernel(SetupArgs a) {
 }
 
 struct SolveArgs {
-  const double2 *fac;   // [F_NCOMP][nrows][P]
-  const double2 *sin;   // [3][nspec][B]
-  double2 *part;        // [3][nspec][slots][B]
+  SolveView v;
   double2 *ybuf;        // [resident warps][lmax][32]
   const WorkItem *items;
-  const int4 *sys;      // per (m, p): {m, n0, len, row0}
   unsigned *counter;
-  int nitems, B, bw, kk, slots, P, N, lmax, pole_begin, pole_end;
-  int64_t nspec, nrows;
+  int nitems, lmax;
 };
 
 __device__ __forceinline__ double2 ld(const double2 *p) { return __ldg(p); }
 
-// Persistent kernel: each warp takes (m, pole group, first state) items from an
-// atomic counter (items are sorted longest first) and runs one tridiagonal
-// forward/backward sweep per (lane, pole).  Lane = (state b, parity p, slot kk).
-__global__ void __launch_bounds__(128) solve_kernel(SolveArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int wslot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  double2 *ybuf = a.ybuf + (int64_t)wslot * a.lmax * 32 + lane;
+// Forward/backward sweeps of one work item (m, pole group g, states from b0) for this
+// lane = (state b, parity p, slot kk), accumulating its poles into its slot's partials.
+__device__ __forceinline__ void solve_item(const SolveView &a, int wm, int wg, int wb0, int lane,
+                                           double2 *ybuf) {
   const int bl = lane % a.bw;
   const int p = (lane / a.bw) & 1;
   const int kk = lane / (2 * a.bw);
   const int64_t NR = a.nrows, P = a.P, NS = a.nspec;
   const int N = a.N, B = a.B, S = a.slots;
+  const int b = wb0 + bl;
+  const int4 sy = a.sys[2 * wm + p];
+  const int m = sy.x, n0 = sy.y, len = sy.z;
+  const int64_t row0 = sy.w;
+  const int slot = wg * a.kk + kk;
+  if (kk >= a.kk || b >= B || len <= 0 || slot >= S) return;
+  const int nmin = m > 1 ? m : 1;
+  const int64_t base_idx = (int64_t)m * (2 * N + 3 - m) / 2 - m;  // idx(m, n) = base_idx + n
+  const double2 *sPhi = a.sin + b;
+  const double2 *sZeta = a.sin + NS * B + b;
+  const double2 *sDel = a.sin + 2 * NS * B + b;
+  double2 *pPhi = a.part + (int64_t)slot * B + b;
+  double2 *pZeta = pPhi + NS * S * B;
+  double2 *pDel = pPhi + 2 * NS * S * B;
+  const int64_t rstride = (int64_t)S * B;  // partial stride per idx
+  bool first = true;
+  for (int k = a.pole_begin + slot; k < a.pole_end; k += S) {
+    // ---- forward sweep
+    const double2 *fL = a.fac + ((int64_t)F_L * NR + row0) * P + k;
+    const double2 *fG = a.fac + ((int64_t)F_G * NR + row0) * P + k;
+    const double2 *fE = a.fac + ((int64_t)F_E * NR + row0) * P + k;
+    const double2 *fF = a.fac + ((int64_t)F_F * NR + row0) * P + k;
+    double2 yprev = make_double2(0, 0);
+    double2 zprev = (n0 - 1 >= nmin) ? ld(sZeta + (base_idx + n0 - 1) * B) : make_double2(0, 0);
+    for (int i = 0; i < len; ++i) {
+      const int n = n0 + 2 * i;
+      const int64_t ix = base_idx + n;
+      const double2 zn = (n + 1 <= N) ? ld(sZeta + (ix + 1) * B) : make_double2(0, 0);
+      double2 y = ld(sDel + ix * B);
+      y = cfms(y, ld(fG + (int64_t)i * P), ld(sPhi + ix * B));
+      y = cfms(y, ld(fE + (int64_t)i * P), zprev);
+      y = cfms(y, ld(fF + (int64_t)i * P), zn);
+      y = cfms(y, ld(fL + (int64_t)i * P), yprev);
+      ybuf[(int64_t)i * 32] = y;
+      yprev = y;
+      zprev = zn;
+    }
+    // ---- backward sweep with the beta-weighted accumulation
+    const double2 *fC = a.fac + ((int64_t)F_C * NR + row0) * P + k;
+    const double2 *fBD = a.fac + ((int64_t)F_BD * NR + row0) * P + k;
+    const double2 *fBAD = a.fac + ((int64_t)F_BAD * NR + row0) * P + k;
+    const double2 *fZP = a.fac + ((int64_t)F_ZP * NR + row0) * P + k;
+    const double2 *fZM = a.fac + ((int64_t)F_ZM * NR + row0) * P + k;
+    // zeta_{n+1} collects Zp_i w_i (row i) and Zm_{i+1} w_{i+1} (row i + 1): both are
+    // folded in as complex FMAs, with row i + 1's weight and w kept in registers.
+    double2 wnext = make_double2(0, 0), zmnext = make_double2(0, 0);
+    for (int i = len - 1; i >= 0; --i) {
+      const int n = n0 + 2 * i;
+      const int64_t ix = base_idx + n;
+      const double2 y = ybuf[(int64_t)i * 32];
+      const double2 wv = cfms(y, ld(fC + (int64_t)i * P), wnext);
+      double2 accD = first ? make_double2(0, 0) : pDel[ix * rstride];
+      double2 accP = first ? make_double2(0, 0) : pPhi[ix * rstride];
+      pDel[ix * rstride] = cfma(accD, ld(fBD + (int64_t)i * P), wv);
+      pPhi[ix * rstride] = cfma(accP, ld(fBAD + (int64_t)i * P), wv);
+      if (n + 1 <= N) {
+        double2 accZ = first ? make_double2(0, 0) : pZeta[(ix + 1) * rstride];
+        accZ = cfma(accZ, ld(fZP + (int64_t)i * P), wv);
+        pZeta[(ix + 1) * rstride] = cfma(accZ, zmnext, wnext);
+      }
+      zmnext = ld(fZM + (int64_t)i * P);
+      wnext = wv;
+    }
+    if (n0 - 1 >= nmin) {
+      const int64_t ix = base_idx + n0 - 1;
+      pZeta[ix * rstride] = cfma(first ? make_double2(0, 0) : pZeta[ix * rstride], zmnext, wnext);
+    }
+    first = false;
+  }
+}
+
+// Persistent kernel: each warp takes (m, pole group, first state) items from an
+// atomic counter (items are sorted longest first) and runs one tridiagonal
+// forward/backward sweep per (lane, pole).
+__global__ void __launch_bounds__(128) solve_kernel(SolveArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int wslot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  double2 *ybuf = a.ybuf + (int64_t)wslot * a.lmax * 32 + lane;
   for (;;) {
     unsigned it = 0;
     if (lane == 0) it = atomicAdd(a.counter, 1u);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= (unsigned)a.nitems) break;
     const WorkItem w = a.items[it];
-    const int b = w.b0 + bl;
-    const int4 sy = a.sys[2 * w.m + p];
-    const int m = sy.x, n0 = sy.y, len = sy.z;
-    const int64_t row0 = sy.w;
-    const int slot = w.g * a.kk + kk;
-    if (kk >= a.kk || b >= B || len <= 0 || slot >= S) continue;
-    const int nmin = m > 1 ? m : 1;
-    const int64_t base_idx = (int64_t)m * (2 * N + 3 - m) / 2 - m;  // idx(m, n) = base_idx + n
-    const double2 *sPhi = a.sin + b;
-    const double2 *sZeta = a.sin + NS * B + b;
-    const double2 *sDel = a.sin + 2 * NS * B + b;
-    double2 *pPhi = a.part + (int64_t)slot * B + b;
-    double2 *pZeta = pPhi + NS * S * B;
-    double2 *pDel = pPhi + 2 * NS * S * B;
-    const int64_t rstride = (int64_t)S * B;  // partial stride per idx
-    bool first = true;
-    for (int k = a.pole_begin + slot; k < a.pole_end; k += S) {
-      // ---- forward sweep
-      const double2 *fL = a.fac + ((int64_t)F_L * NR + row0) * P + k;
-      const double2 *fG = a.fac + ((int64_t)F_G * NR + row0) * P + k;
-      const double2 *fE = a.fac + ((int64_t)F_E * NR + row0) * P + k;
-      const double2 *fF = a.fac + ((int64_t)F_F * NR + row0) * P + k;
-      double2 yprev = make_double2(0, 0);
-      double2 zprev = (n0 - 1 >= nmin) ? ld(sZeta + (base_idx + n0 - 1) * B) : make_double2(0, 0);
-      for (int i = 0; i < len; ++i) {
-        const int n = n0 + 2 * i;
-        const int64_t ix = base_idx + n;
-        const double2 zn = (n + 1 <= N) ? ld(sZeta + (ix + 1) * B) : make_double2(0, 0);
-        double2 y = ld(sDel + ix * B);
-        y = cfms(y, ld(fG + (int64_t)i * P), ld(sPhi + ix * B));
-        y = cfms(y, ld(fE + (int64_t)i * P), zprev);
-        y = cfms(y, ld(fF + (int64_t)i * P), zn);
-        y = cfms(y, ld(fL + (int64_t)i * P), yprev);
-        ybuf[(int64_t)i * 32] = y;
-        yprev = y;
-        zprev = zn;
-      }
-      // ---- backward sweep with the beta-weighted accumulation
-      const double2 *fC = a.fac + ((int64_t)F_C * NR + row0) * P + k;
-      const double2 *fBD = a.fac + ((int64_t)F_BD * NR + row0) * P + k;
-      const double2 *fBAD = a.fac + ((int64_t)F_BAD * NR + row0) * P + k;
-      const double2 *fZP = a.fac + ((int64_t)F_ZP * NR + row0) * P + k;
-      const double2 *fZM = a.fac + ((int64_t)F_ZM * NR + row0) * P + k;
-      double2 wnext = make_double2(0, 0), carry = make_double2(0, 0);
-      for (int i = len - 1; i >= 0; --i) {
-        const int n = n0 + 2 * i;
-        const int64_t ix = base_idx + n;
-        const double2 y = ybuf[(int64_t)i * 32];
-        const double2 wv = cfms(y, ld(fC + (int64_t)i * P), wnext);
-        double2 accD = first ? make_double2(0, 0) : pDel[ix * rstride];
-        double2 accP = first ? make_double2(0, 0) : pPhi[ix * rstride];
-        pDel[ix * rstride] = cfma(accD, ld(fBD + (int64_t)i * P), wv);
-        pPhi[ix * rstride] = cfma(accP, ld(fBAD + (int64_t)i * P), wv);
-        if (n + 1 <= N) {
-          double2 accZ = first ? carry : cadd(pZeta[(ix + 1) * rstride], carry);
-          pZeta[(ix + 1) * rstride] = cfma(accZ, ld(fZP + (int64_t)i * P), wv);
-        }
-        carry = cmul(ld(fZM + (int64_t)i * P), wv);
-        wnext = wv;
-      }
-      if (n0 - 1 >= nmin) {
-        const int64_t ix = base_idx + n0 - 1;
-        pZeta[ix * rstride] = first ? carry : cadd(pZeta[ix * rstride], carry);
-      }
-      first = false;
-    }
+    solve_item(a.v, w.m, w.g, w.b0, lane, ybuf);
+  }
+}
+
+// The same over a ragged work list spanning several plans (mixed truncations and
+// pole counts): item = (m, pole group, first state, plan index), longest first.
+struct RaggedArgs {
+  const SolveView *views;
+  const WorkItem *items;  // len field carries the plan index
+  double2 *ybuf;
+  unsigned *counter;
+  int nitems, lmax;
+};
+
+__global__ void __launch_bounds__(128) solve_ragged_kernel(RaggedArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int wslot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  double2 *ybuf = a.ybuf + (int64_t)wslot * a.lmax * 32 + lane;
+  for (;;) {
+    unsigned it = 0;
+    if (lane == 0) it = atomicAdd(a.counter, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= (unsigned)a.nitems) break;
+    const WorkItem w = a.items[it];
+    const SolveView v = a.views[w.len];
+    solve_item(v, w.m, w.g, w.b0, lane, ybuf);
   }
 }
 
@@ -374,31 +405,47 @@ cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, double2 *part, int B,
+                    int pole_begin, int pole_end) {
+  SolveView v;
+  v.fac = adjoint ? pl.fac_adj : pl.fac_fwd;
+  v.sin = sin;
+  v.part = part;
+  v.sys = pl.sys_dev;
+  v.P = pl.P;
+  v.N = pl.N;
+  v.B = B;
+  v.bw = lay.bw;
+  v.kk = lay.kk;
+  v.slots = lay.slots;
+  v.pole_begin = pole_begin;
+  v.pole_end = pole_end;
+  v.nspec = pl.nspec;
+  v.nrows = pl.nrows;
+  return v;
+}
+
 cudaError_t launch_solve(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, int B,
                          int pole_begin, int pole_end, bool, cudaStream_t st) {
   SolveArgs a;
-  a.fac = adjoint ? pl.fac_adj : pl.fac_fwd;
-  a.sin = sin;
-  a.part = pl.partial;
+  a.v = make_view(pl, lay, adjoint, sin, pl.partial, B, pole_begin, pole_end);
   a.ybuf = pl.yscratch;
   a.items = lay.items_dev;
-  a.sys = pl.sys_dev;
   a.counter = pl.counter;
   a.nitems = lay.nitems;
-  a.B = B;
-  a.bw = lay.bw;
-  a.kk = lay.kk;
-  a.slots = lay.slots;
-  a.P = pl.P;
-  a.N = pl.N;
   a.lmax = pl.lmax;
-  a.pole_begin = pole_begin;
-  a.pole_end = pole_end;
-  a.nspec = pl.nspec;
-  a.nrows = pl.nrows;
   cudaError_t e = cudaMemsetAsync(pl.counter, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   solve_kernel<<<pl.resident_warps / 4, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_ragged(const SolveView *views_dev, const WorkItem *items, int nitems, double2 *ybuf,
+                                int lmax, unsigned *counter, int resident_warps, cudaStream_t st) {
+  RaggedArgs a{views_dev, items, ybuf, counter, nitems, lmax};
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  solve_ragged_kernel<<<resident_warps / 4, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -527,25 +574,25 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
   if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);  // the work counter starts at zero
   if (e == cudaSuccess) {
     SolveArgs a;
-    a.fac = pl.fac_fwd;
-    a.sin = s_in;
-    a.part = part;
+    a.v.fac = pl.fac_fwd;
+    a.v.sin = s_in;
+    a.v.part = part;
+    a.v.sys = pl.sys_dev;
+    a.v.P = pl.P;
+    a.v.N = pl.N;
+    a.v.B = B;
+    a.v.bw = bw;
+    a.v.kk = slots;
+    a.v.slots = slots;
+    a.v.pole_begin = 0;
+    a.v.pole_end = pl.P;
+    a.v.nspec = pl.nspec;
+    a.v.nrows = pl.nrows;
     a.ybuf = ybuf;
     a.items = items;
-    a.sys = pl.sys_dev;
     a.counter = counter;
     a.nitems = nitems;
-    a.B = B;
-    a.bw = bw;
-    a.kk = slots;
-    a.slots = slots;
-    a.P = pl.P;
-    a.N = pl.N;
     a.lmax = pl.lmax;
-    a.pole_begin = 0;
-    a.pole_end = pl.P;
-    a.nspec = pl.nspec;
-    a.nrows = pl.nrows;
     solve_kernel<<<warps / 4, 128, 0, st>>>(a);
     e = cudaGetLastError();
   }

@@ -55,6 +55,10 @@ SIGNATURES = {
     "rexi_solve_pole": (_I32, [_VP, _I32, _VP, _VP, _I32, _VP]),
     "rexi_get_coefficients": (_I32, [_VP, _DP, _DP, ctypes.POINTER(_I32)]),
     "rexi_plan_info": (_I32, [_VP, ctypes.POINTER(ctypes.c_int64), _I32]),
+    "rexi_tune": (_I32, [_VP, _I32, ctypes.POINTER(_I32)]),
+    "rexi_ragged_create": (_I32, [ctypes.POINTER(_VP), _I32, _I32, ctypes.POINTER(_VP)]),
+    "rexi_ragged_step": (_I32, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_I32), _I32, _VP]),
+    "rexi_ragged_destroy": (None, [_VP]),
     "rexi_profile_enable": (_I32, [_VP, _I32]),
     "rexi_profile_read": (_I32, [_VP, _DP, _I32, ctypes.POINTER(_I32)]),
     "rexi_check_device": (_I32, [_VP]),
@@ -219,6 +223,13 @@ class Plan:
             self._h, al.ctypes.data_as(_DP), be.ctypes.data_as(_DP), ctypes.byref(n)))
         return al.view(np.complex128).copy(), be.view(np.complex128).copy()
 
+    def tune(self, batch):
+        """rexi_tune: time the solve kernel for several pole-group counts at this batch size
+        and keep the fastest; returns the chosen number of pole slots."""
+        n = _I32()
+        _check("rexi_tune", load().rexi_tune(self._h, batch, ctypes.byref(n)))
+        return n.value
+
     def info(self):
         v = (ctypes.c_int64 * 8)()
         _check("rexi_plan_info", load().rexi_plan_info(self._h, v, 8))
@@ -243,6 +254,37 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             load().rexi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ragged:
+    """Ragged batch over several REXI_SPECTRAL plans: one persistent solve launch for all states."""
+
+    def __init__(self, plans, max_states):
+        arr = (_VP * len(plans))(*[p._h for p in plans])
+        h = _VP()
+        _check("rexi_ragged_create", load().rexi_ragged_create(arr, len(plans), max_states, ctypes.byref(h)))
+        self._h = h
+        self.plans = list(plans)
+
+    def step(self, states, outs, state_plan, stream=None):
+        """states/outs: lists of complex128 CUDA tensors [3, nspec_p]; state_plan: plan index per state."""
+        n = len(states)
+        ins = (_VP * n)(*[t.data_ptr() for t in states])
+        ous = (_VP * n)(*[t.data_ptr() for t in outs])
+        sp = (_I32 * n)(*state_plan)
+        _check("rexi_ragged_step", load().rexi_ragged_step(self._h, ins, ous, sp, n, _stream_handle(stream)))
+        return outs
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rexi_ragged_destroy(self._h)
             self._h = None
 
     def __del__(self):
