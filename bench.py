@@ -29,7 +29,11 @@ sys.path.insert(0, ROOT)
 
 WORK = dict(N=341, nlat=512, nlon=1024, M=256, h=0.2, tau=1200.0, batch=16, seed=1005)
 METRIC = "REXI steps/s at T341, K=256 poles: chosen vs plain FP64 form at stated error"
-FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve
+FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve: 36 FMAs
+# DRAM bytes (read + write) of one solve_kernel launch from the ncu capture at T170,
+# K=256, batch 16 (profiles/solve_kernel_t170_b16.md); traffic per row is constant, so a
+# launch of the bench workload moves this times rows(T341) / rows(T170).
+SOLVE_TRAFFIC_T170 = 7.815846e9 + 7.787691e9
 
 
 def rows_of(N):
@@ -264,7 +268,9 @@ def main():
         "data": "synthetic", "config": {**workload_config(), "form": chosen},
         "roofline": {"bound": "alu", "kernel": "solve_kernel (FP64 banded solves + pole sum)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz",
+                     "traffic": SOLVE_TRAFFIC_T170 * rows_of(W["N"]) / rows_of(170),
+                     "traffic_source": "ncu dram bytes at T170/K256/B16 scaled by rows to T341",
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz",
                      "flops_per_launch": flops, "launch_ms": solve_ms},
         "stage_ms": r["stages"],
         "e2e": {"value": world * 1e3 / r["ms_e2e"], "unit": "steps/s", "h2d_bytes_per_step": r["bytes"],
