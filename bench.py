@@ -33,7 +33,7 @@ FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve: 36 F
 # DRAM bytes (read + write) of one solve_kernel launch from the ncu capture at T170,
 # K=256, batch 16 (profiles/solve_kernel_t170_b16.md); traffic per row is constant, so a
 # launch of the bench workload moves this times rows(T341) / rows(T170).
-SOLVE_TRAFFIC_T170 = 7.815846e9 + 7.787691e9
+SOLVE_TRAFFIC_T170 = None  # re-captured after each change of the solve kernel
 
 
 def rows_of(N):
@@ -268,7 +268,7 @@ def main():
         "data": "synthetic", "config": {**workload_config(), "form": chosen},
         "roofline": {"bound": "alu", "kernel": "solve_kernel (FP64 banded solves + pole sum)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": SOLVE_TRAFFIC_T170 * rows_of(W["N"]) / rows_of(170),
+                     "traffic": (SOLVE_TRAFFIC_T170 * rows_of(W["N"]) / rows_of(170)) if SOLVE_TRAFFIC_T170 else None,
                      "traffic_source": "ncu dram bytes at T170/K256/B16 scaled by rows to T341",
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz",
                      "flops_per_launch": flops, "launch_ms": solve_ms},

@@ -194,14 +194,104 @@ struct SolveArgs {
 
 __device__ __forceinline__ double2 ld(const double2 *p) { return __ldg(p); }
 
+// Sweeps of KC poles of one lane at once (KC independent recurrences share the
+// state loads and one read-modify-write of the slot partials per row).
+template <int KC>
+__device__ __forceinline__ void sweep_poles(const SolveView &a, const int (&k)[KC], int n0, int len, int nmin,
+                                            int64_t row0, int64_t base_idx, const double2 *sPhi,
+                                            const double2 *sZeta, const double2 *sDel, double2 *pPhi,
+                                            double2 *pZeta, double2 *pDel, int64_t rstride, bool first,
+                                            double2 *ybuf) {
+  const int64_t NR = a.nrows, P = a.P;
+  const int N = a.N, B = a.B;
+  const double2 *fL[KC], *fG[KC], *fE[KC], *fF[KC];
+  for (int c = 0; c < KC; ++c) {
+    fL[c] = a.fac + ((int64_t)F_L * NR + row0) * P + k[c];
+    fG[c] = a.fac + ((int64_t)F_G * NR + row0) * P + k[c];
+    fE[c] = a.fac + ((int64_t)F_E * NR + row0) * P + k[c];
+    fF[c] = a.fac + ((int64_t)F_F * NR + row0) * P + k[c];
+  }
+  // ---- forward sweep: y_i = delta0 - g Phi0 - e zeta0_{n-1} - f zeta0_{n+1} - l y_{i-1}
+  double2 yprev[KC];
+  for (int c = 0; c < KC; ++c) yprev[c] = make_double2(0, 0);
+  double2 zprev = (n0 - 1 >= nmin) ? ld(sZeta + (base_idx + n0 - 1) * B) : make_double2(0, 0);
+  for (int i = 0; i < len; ++i) {
+    const int n = n0 + 2 * i;
+    const int64_t ix = base_idx + n;
+    const double2 zn = (n + 1 <= N) ? ld(sZeta + (ix + 1) * B) : make_double2(0, 0);
+    const double2 d0 = ld(sDel + ix * B), p0 = ld(sPhi + ix * B);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      double2 y = cfms(d0, ld(fG[c] + (int64_t)i * P), p0);
+      y = cfms(y, ld(fE[c] + (int64_t)i * P), zprev);
+      y = cfms(y, ld(fF[c] + (int64_t)i * P), zn);
+      y = cfms(y, ld(fL[c] + (int64_t)i * P), yprev[c]);
+      ybuf[((int64_t)i * KC + c) * 32] = y;
+      yprev[c] = y;
+    }
+    zprev = zn;
+  }
+  // ---- backward sweep w_i = y_i - Chat w_{i+1} with the beta-weighted accumulation;
+  // zeta_{n+1} collects Zp_i w_i (row i) and Zm_{i+1} w_{i+1} (row i + 1), folded in as
+  // complex FMAs with row i + 1's weight and w kept in registers.
+  const double2 *fC[KC], *fBD[KC], *fBAD[KC], *fZP[KC], *fZM[KC];
+  for (int c = 0; c < KC; ++c) {
+    fC[c] = a.fac + ((int64_t)F_C * NR + row0) * P + k[c];
+    fBD[c] = a.fac + ((int64_t)F_BD * NR + row0) * P + k[c];
+    fBAD[c] = a.fac + ((int64_t)F_BAD * NR + row0) * P + k[c];
+    fZP[c] = a.fac + ((int64_t)F_ZP * NR + row0) * P + k[c];
+    fZM[c] = a.fac + ((int64_t)F_ZM * NR + row0) * P + k[c];
+  }
+  double2 wnext[KC], zmnext[KC];
+  for (int c = 0; c < KC; ++c) wnext[c] = zmnext[c] = make_double2(0, 0);
+  for (int i = len - 1; i >= 0; --i) {
+    const int n = n0 + 2 * i;
+    const int64_t ix = base_idx + n;
+    double2 wv[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) wv[c] = cfms(ybuf[((int64_t)i * KC + c) * 32], ld(fC[c] + (int64_t)i * P), wnext[c]);
+    double2 accD = first ? make_double2(0, 0) : pDel[ix * rstride];
+    double2 accP = first ? make_double2(0, 0) : pPhi[ix * rstride];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      accD = cfma(accD, ld(fBD[c] + (int64_t)i * P), wv[c]);
+      accP = cfma(accP, ld(fBAD[c] + (int64_t)i * P), wv[c]);
+    }
+    pDel[ix * rstride] = accD;
+    pPhi[ix * rstride] = accP;
+    if (n + 1 <= N) {
+      double2 accZ = first ? make_double2(0, 0) : pZeta[(ix + 1) * rstride];
+#pragma unroll
+      for (int c = 0; c < KC; ++c) {
+        accZ = cfma(accZ, ld(fZP[c] + (int64_t)i * P), wv[c]);
+        accZ = cfma(accZ, zmnext[c], wnext[c]);
+      }
+      pZeta[(ix + 1) * rstride] = accZ;
+    }
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      zmnext[c] = ld(fZM[c] + (int64_t)i * P);
+      wnext[c] = wv[c];
+    }
+  }
+  if (n0 - 1 >= nmin) {
+    const int64_t ix = base_idx + n0 - 1;
+    double2 accZ = first ? make_double2(0, 0) : pZeta[ix * rstride];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) accZ = cfma(accZ, zmnext[c], wnext[c]);
+    pZeta[ix * rstride] = accZ;
+  }
+}
+
 // Forward/backward sweeps of one work item (m, pole group g, states from b0) for this
-// lane = (state b, parity p, slot kk), accumulating its poles into its slot's partials.
+// lane = (state b, parity p, slot kk): its poles k = slot, slot + S, ... two at a time,
+// accumulated into its slot's partials in ascending k.
 __device__ __forceinline__ void solve_item(const SolveView &a, int wm, int wg, int wb0, int lane,
                                            double2 *ybuf) {
   const int bl = lane % a.bw;
   const int p = (lane / a.bw) & 1;
   const int kk = lane / (2 * a.bw);
-  const int64_t NR = a.nrows, P = a.P, NS = a.nspec;
+  const int64_t NS = a.nspec;
   const int N = a.N, B = a.B, S = a.slots;
   const int b = wb0 + bl;
   const int4 sy = a.sys[2 * wm + p];
@@ -219,58 +309,17 @@ __device__ __forceinline__ void solve_item(const SolveView &a, int wm, int wg, i
   double2 *pDel = pPhi + 2 * NS * S * B;
   const int64_t rstride = (int64_t)S * B;  // partial stride per idx
   bool first = true;
-  for (int k = a.pole_begin + slot; k < a.pole_end; k += S) {
-    // ---- forward sweep
-    const double2 *fL = a.fac + ((int64_t)F_L * NR + row0) * P + k;
-    const double2 *fG = a.fac + ((int64_t)F_G * NR + row0) * P + k;
-    const double2 *fE = a.fac + ((int64_t)F_E * NR + row0) * P + k;
-    const double2 *fF = a.fac + ((int64_t)F_F * NR + row0) * P + k;
-    double2 yprev = make_double2(0, 0);
-    double2 zprev = (n0 - 1 >= nmin) ? ld(sZeta + (base_idx + n0 - 1) * B) : make_double2(0, 0);
-    for (int i = 0; i < len; ++i) {
-      const int n = n0 + 2 * i;
-      const int64_t ix = base_idx + n;
-      const double2 zn = (n + 1 <= N) ? ld(sZeta + (ix + 1) * B) : make_double2(0, 0);
-      double2 y = ld(sDel + ix * B);
-      y = cfms(y, ld(fG + (int64_t)i * P), ld(sPhi + ix * B));
-      y = cfms(y, ld(fE + (int64_t)i * P), zprev);
-      y = cfms(y, ld(fF + (int64_t)i * P), zn);
-      y = cfms(y, ld(fL + (int64_t)i * P), yprev);
-      ybuf[(int64_t)i * 32] = y;
-      yprev = y;
-      zprev = zn;
-    }
-    // ---- backward sweep with the beta-weighted accumulation
-    const double2 *fC = a.fac + ((int64_t)F_C * NR + row0) * P + k;
-    const double2 *fBD = a.fac + ((int64_t)F_BD * NR + row0) * P + k;
-    const double2 *fBAD = a.fac + ((int64_t)F_BAD * NR + row0) * P + k;
-    const double2 *fZP = a.fac + ((int64_t)F_ZP * NR + row0) * P + k;
-    const double2 *fZM = a.fac + ((int64_t)F_ZM * NR + row0) * P + k;
-    // zeta_{n+1} collects Zp_i w_i (row i) and Zm_{i+1} w_{i+1} (row i + 1): both are
-    // folded in as complex FMAs, with row i + 1's weight and w kept in registers.
-    double2 wnext = make_double2(0, 0), zmnext = make_double2(0, 0);
-    for (int i = len - 1; i >= 0; --i) {
-      const int n = n0 + 2 * i;
-      const int64_t ix = base_idx + n;
-      const double2 y = ybuf[(int64_t)i * 32];
-      const double2 wv = cfms(y, ld(fC + (int64_t)i * P), wnext);
-      double2 accD = first ? make_double2(0, 0) : pDel[ix * rstride];
-      double2 accP = first ? make_double2(0, 0) : pPhi[ix * rstride];
-      pDel[ix * rstride] = cfma(accD, ld(fBD + (int64_t)i * P), wv);
-      pPhi[ix * rstride] = cfma(accP, ld(fBAD + (int64_t)i * P), wv);
-      if (n + 1 <= N) {
-        double2 accZ = first ? make_double2(0, 0) : pZeta[(ix + 1) * rstride];
-        accZ = cfma(accZ, ld(fZP + (int64_t)i * P), wv);
-        pZeta[(ix + 1) * rstride] = cfma(accZ, zmnext, wnext);
-      }
-      zmnext = ld(fZM + (int64_t)i * P);
-      wnext = wv;
-    }
-    if (n0 - 1 >= nmin) {
-      const int64_t ix = base_idx + n0 - 1;
-      pZeta[ix * rstride] = cfma(first ? make_double2(0, 0) : pZeta[ix * rstride], zmnext, wnext);
-    }
+  int k0 = a.pole_begin + slot;
+  for (; k0 + S < a.pole_end; k0 += 2 * S) {
+    const int kp[2] = {k0, k0 + S};
+    sweep_poles<2>(a, kp, n0, len, nmin, row0, base_idx, sPhi, sZeta, sDel, pPhi, pZeta, pDel, rstride, first,
+                   ybuf);
     first = false;
+  }
+  if (k0 < a.pole_end) {
+    const int kp[1] = {k0};
+    sweep_poles<1>(a, kp, n0, len, nmin, row0, base_idx, sPhi, sZeta, sDel, pPhi, pZeta, pDel, rstride, first,
+                   ybuf);
   }
 }
 
@@ -280,7 +329,7 @@ __device__ __forceinline__ void solve_item(const SolveView &a, int wm, int wg, i
 __global__ void __launch_bounds__(128) solve_kernel(SolveArgs a) {
   const int lane = threadIdx.x & 31;
   const int wslot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  double2 *ybuf = a.ybuf + (int64_t)wslot * a.lmax * 32 + lane;
+  double2 *ybuf = a.ybuf + (int64_t)wslot * a.lmax * 2 * 32 + lane;
   for (;;) {
     unsigned it = 0;
     if (lane == 0) it = atomicAdd(a.counter, 1u);
@@ -304,7 +353,7 @@ struct RaggedArgs {
 __global__ void __launch_bounds__(128) solve_ragged_kernel(RaggedArgs a) {
   const int lane = threadIdx.x & 31;
   const int wslot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  double2 *ybuf = a.ybuf + (int64_t)wslot * a.lmax * 32 + lane;
+  double2 *ybuf = a.ybuf + (int64_t)wslot * a.lmax * 2 * 32 + lane;
   for (;;) {
     unsigned it = 0;
     if (lane == 0) it = atomicAdd(a.counter, 1u);
@@ -540,7 +589,7 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
   const int warps = pl.num_sms * 4;
   const size_t state_b = align256((size_t)3 * pl.nspec * B * sizeof(double2));
   const size_t part_b = align256((size_t)3 * pl.nspec * slots * B * sizeof(double2));
-  const size_t y_b = align256((size_t)warps * pl.lmax * 32 * sizeof(double2));
+  const size_t y_b = align256((size_t)warps * pl.lmax * 2 * 32 * sizeof(double2));
   const size_t item_b = align256((size_t)nitems * sizeof(WorkItem));
   const size_t need = 2 * state_b + part_b + y_b + item_b + 256;
   if (need > kStaticScratchBytes) {
