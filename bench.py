@@ -149,6 +149,17 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def replica_max_ms(ms, dist):
+    """Max of a per-rank time over all ranks (the slowest replica sets the job's time)."""
+    if dist is None:
+        return ms
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_config():
     return {"workload": "T-REXI step, linear SWE on the sphere: T341, 1024x512 Gaussian grid, K=M=256 "
                         "(P=535 poles), h=0.2, tau=1200 s, 16 seeded n^-3 states, grid layout",
@@ -220,10 +231,7 @@ def main():
         stages, ncalls = plan.profile_read()
         plan.profile_enable(0)
         ck = clocks.stop()
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = replica_max_ms(ms, dist)
         # e2e through the public API with pinned host buffers, copies inside the timed region
         xh = x.cpu().pin_memory()
         yh = torch.empty(y.shape, dtype=y.dtype).pin_memory()
@@ -244,10 +252,7 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = f0.elapsed_time(f1) / args.steps
-        if dist:
-            t = torch.tensor([ms_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+        ms_e2e = replica_max_ms(ms_e2e, dist)
         results[prec] = dict(ms=ms, ms_e2e=ms_e2e, stages={k: v / max(ncalls, 1) for k, v in stages.items()},
                              clocks=ck, y=y, bytes=x.numel() * 8, info=plan.info())
         plan.close()

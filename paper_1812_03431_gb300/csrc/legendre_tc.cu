@@ -37,6 +37,7 @@ constexpr int TM = 128;              // rows (analysis: degrees; synthesis: lati
 constexpr int KB = 32;               // K per staged block (latitudes or degrees)
 constexpr int SUB = TM * KB * 4;     // bytes of one packed 128 x 32 tf32 sub-tile (16 KiB)
 constexpr unsigned kSpinLimit = 1u << 26;
+constexpr int THREADS = 256;         // 8 warps: all stage; warp 0 allocates TMEM, thread 0 issues MMAs
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -113,6 +114,14 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *v) {
   v[1] = __uint_as_float(r1);
   v[2] = __uint_as_float(r2);
   v[3] = __uint_as_float(r3);
+}
+
+// 16-byte asynchronous global -> shared copy (completion: cp_async_wait_all)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
@@ -207,7 +216,7 @@ struct TcArgs {
 
 // ---- analysis -------------------------------------------------------------------------
 // dynamic smem: [A: 4 x 16 KiB][B1 hi, B1 lo: 8G x 32 tf32 each][B2 hi, B2 lo: 4G x 32 each]
-__global__ void __launch_bounds__(128) leg_ana_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(THREADS) leg_ana_tc_kernel(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -235,49 +244,64 @@ __global__ void __launch_bounds__(128) leg_ana_tc_kernel(TcArgs a) {
   const int M1 = a.N + 1, ncol = 3 * a.B;
   bool ok = true;
   for (int kb = 0; kb < nkb; ++kb) {
-    // tables: a straight copy of the packed 64 KiB block
+    // tables: the packed 64 KiB block, copied asynchronously while the data are staged
     const uint4 *src = reinterpret_cast<const uint4 *>(a.tab + (blk0 + kb) * (int64_t)(4 * SUB / 4));
     uint4 *dstA = reinterpret_cast<uint4 *>(sA);
-    for (int t = tid; t < 4 * SUB / 16; t += blockDim.x) dstA[t] = src[t];
-    // data: fold, split, pack
-    for (int t = tid; t < KB * G * 3; t += blockDim.x) {
-      const int k = t / (G * 3), rem = t - k * (G * 3);
-      const int bl = rem / 3, f = rem - bl * 3;
-      const int j = kb * KB + k, b = b0 + bl;
-      double2 e = make_double2(0, 0), o = e;
-      if (j < a.J && b < a.B) {
-        const double2 x1 = a.four[((int64_t)j * M1 + m) * ncol + 3 * b + f];
-        const double2 x2 = a.four[((int64_t)(a.nlat - 1 - j) * M1 + m) * ncol + 3 * b + f];
-        e = make_double2(x1.x + x2.x, x1.y + x2.y);
-        o = make_double2(x1.x - x2.x, x1.y - x2.y);
-      }
-      const double2 vp = p ? o : e;  // class of Pbar_n
-      const double2 vh = p ? e : o;  // class of H_n
-      uint32_t hi, lo;
-      for (int c = 0; c < 2; ++c) {
-        const int col = 8 * bl + 2 * f + c;
-        const uint32_t off = core_off(col, k, N1 / 8);
-        split_tf32(c ? vp.y : vp.x, hi, lo);
-        *reinterpret_cast<uint32_t *>(sB1 + off) = hi;
-        *reinterpret_cast<uint32_t *>(sB1 + N1 * KB * 4 + off) = lo;
-      }
-      if (f > 0) {
-        for (int c = 0; c < 2; ++c) {
-          const int col = 4 * bl + 2 * (f - 1) + c;
-          const uint32_t off = core_off(col, k, N2 / 8);
-          split_tf32(c ? vh.y : vh.x, hi, lo);
-          *reinterpret_cast<uint32_t *>(sB2 + off) = hi;
-          *reinterpret_cast<uint32_t *>(sB2 + N2 * KB * 4 + off) = lo;
+    for (int t = tid; t < 4 * SUB / 16; t += THREADS) cp_async16(dstA + t, src + t);
+    // data: unit = (4 latitudes kq, state bl, field f in Phi, U, V, pad); every load of
+    // the thread is issued before any use (one memory latency per block).  A unit
+    // writes B1 columns 8 bl + 2 f + {re, im} (class of Pbar_n) and, for U and V,
+    // B2 columns 4 bl + 2 (f - 1) + {re, im} (class of H_n), as 16-byte rows.
+    {
+      constexpr int RMAX = 512 / THREADS;  // units per thread: 8 kq x 4 G <= 512
+      const int nun = (KB / 4) * 4 * G;
+      double2 xn[RMAX][4], xs[RMAX][4];
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        const int u = tid + r * THREADS;
+        const int kq = u / (4 * G), rem = u - kq * (4 * G), bl = rem >> 2, f = rem & 3;
+        const int b = b0 + bl;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = kb * KB + 4 * kq + q;
+          xn[r][q] = xs[r][q] = make_double2(0, 0);
+          if (u < nun && f < 3 && j < a.J && b < a.B) {
+            xn[r][q] = a.four[((int64_t)j * M1 + m) * ncol + 3 * b + f];
+            xs[r][q] = a.four[((int64_t)(a.nlat - 1 - j) * M1 + m) * ncol + 3 * b + f];
+          }
         }
-      } else {
-        // zero padding columns 8 bl + 6, 8 bl + 7 of B1
-        for (int c = 6; c < 8; ++c) {
-          const uint32_t off = core_off(8 * bl + c, k, N1 / 8);
-          *reinterpret_cast<uint32_t *>(sB1 + off) = 0u;
-          *reinterpret_cast<uint32_t *>(sB1 + N1 * KB * 4 + off) = 0u;
+      }
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        const int u = tid + r * THREADS;
+        if (u >= nun) continue;
+        const int kq = u / (4 * G), rem = u - kq * (4 * G), bl = rem >> 2, f = rem & 3;
+        uint32_t eh[2][4], el[2][4], oh[2][4], ol[2][4];  // [re/im][latitude]
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          split_tf32(xn[r][q].x + xs[r][q].x, eh[0][q], el[0][q]);
+          split_tf32(xn[r][q].y + xs[r][q].y, eh[1][q], el[1][q]);
+          split_tf32(xn[r][q].x - xs[r][q].x, oh[0][q], ol[0][q]);
+          split_tf32(xn[r][q].y - xs[r][q].y, oh[1][q], ol[1][q]);
+        }
+        // Pbar_n has the class of p (E for p = 0); H_n the other one
+        uint32_t(*ph)[4] = p ? oh : eh, (*pl)[4] = p ? ol : el;
+        uint32_t(*hh)[4] = p ? eh : oh, (*hl)[4] = p ? el : ol;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const uint32_t off = core_off(8 * bl + 2 * f + c, 4 * kq, N1 / 8);
+          *reinterpret_cast<uint4 *>(sB1 + off) = make_uint4(ph[c][0], ph[c][1], ph[c][2], ph[c][3]);
+          *reinterpret_cast<uint4 *>(sB1 + N1 * KB * 4 + off) = make_uint4(pl[c][0], pl[c][1], pl[c][2], pl[c][3]);
+          if (f == 1 || f == 2) {
+            const uint32_t off2 = core_off(4 * bl + 2 * (f - 1) + c, 4 * kq, N2 / 8);
+            *reinterpret_cast<uint4 *>(sB2 + off2) = make_uint4(hh[c][0], hh[c][1], hh[c][2], hh[c][3]);
+            *reinterpret_cast<uint4 *>(sB2 + N2 * KB * 4 + off2) =
+                make_uint4(hl[c][0], hl[c][1], hl[c][2], hl[c][3]);
+          }
         }
       }
     }
+    cp_async_wait_all();
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -309,10 +333,12 @@ __global__ void __launch_bounds__(128) leg_ana_tc_kernel(TcArgs a) {
     if (tid == 0) atomicExch(a.err, 1);
   } else {
     // epilogue: TMEM lane = row of the tile (warp w owns lanes 32w .. 32w + 31)
-    const int r = tile * TM + warp * 32 + (tid & 31);
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile) for half w / 4 of the states
+    const int wq = warp & 3, half = warp >> 2;
+    const int r = tile * TM + wq * 32 + (tid & 31);
     const int n = m + p + 2 * r;
-    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
-    for (int bl = 0; bl < G; ++bl) {
+    const uint32_t lane_addr = tbase + ((uint32_t)(wq * 32) << 16);
+    for (int bl = half * (G / 2); bl < (half + 1) * (G / 2); ++bl) {
       float d1[8], d2[4];
       tmem_ld4(lane_addr + 8 * bl, d1);
       tmem_ld4(lane_addr + 8 * bl + 4, d1 + 4);
@@ -337,7 +363,7 @@ __global__ void __launch_bounds__(128) leg_ana_tc_kernel(TcArgs a) {
 
 // ---- synthesis ------------------------------------------------------------------------
 // dynamic smem: [A: 8 x 16 KiB][B1_0, B1_1: (hi, lo) 8G x 32][B2_0, B2_1: (hi, lo) 4G x 32]
-__global__ void __launch_bounds__(128) leg_syn_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(THREADS) leg_syn_tc_kernel(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -369,47 +395,61 @@ __global__ void __launch_bounds__(128) leg_syn_tc_kernel(TcArgs a) {
   for (int kb = 0; kb < nkb; ++kb) {
     const uint4 *src = reinterpret_cast<const uint4 *>(a.tab + (blk0 + kb) * (int64_t)(8 * SUB / 4));
     uint4 *dstA = reinterpret_cast<uint4 *>(sA);
-    for (int t = tid; t < 8 * SUB / 16; t += blockDim.x) dstA[t] = src[t];
-    // spectral data of both parities q: rows i = kb*32 + k, n = m + q + 2 i
-    for (int t = tid; t < 2 * KB * G * 3; t += blockDim.x) {
-      const int q = t / (KB * G * 3), rem0 = t - q * (KB * G * 3);
-      const int k = rem0 / (G * 3), rem = rem0 - k * (G * 3);
-      const int bl = rem / 3, f = rem - bl * 3;
-      const int n = m + q + 2 * (kb * KB + k), b = b0 + bl;
-      double2 v = make_double2(0, 0);
-      if (n <= a.N && b < a.B) {
-        const int64_t ix = idx0 + (n - m);
-        v = a.sint[((int64_t)f * a.nspec + ix) * a.B + b];
-        if (f > 0) {
-          const double s = a.zd[ix];
-          v = make_double2(s * v.x, s * v.y);
+    for (int t = tid; t < 8 * SUB / 16; t += THREADS) cp_async16(dstA + t, src + t);
+    // spectral data: unit = (parity q, 4 degrees kq, state bl, field f in Phi, psi', chi',
+    // pad); rows i = kb*32 + 4 kq + r have n = m + q + 2 i.  P-terms feed class q (B1_q),
+    // H-terms (psi', chi') class 1 - q (B2_{1-q}); all loads are issued first.
+    {
+      constexpr int RMAX = 1024 / THREADS;  // 2 q x 8 kq x 4 G <= 1024
+      const int nun = 2 * (KB / 4) * 4 * G;
+      double2 xv[RMAX][4];
+#pragma unroll
+      for (int rr = 0; rr < RMAX; ++rr) {
+        const int u = tid + rr * THREADS;
+        const int q = u / ((KB / 4) * 4 * G), u2 = u - q * ((KB / 4) * 4 * G);
+        const int kq = u2 / (4 * G), rem = u2 - kq * (4 * G), bl = rem >> 2, f = rem & 3;
+        const int b = b0 + bl;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int n = m + q + 2 * (kb * KB + 4 * kq + r);
+          xv[rr][r] = make_double2(0, 0);
+          if (u < nun && f < 3 && n <= a.N && b < a.B) {
+            const int64_t ix = idx0 + (n - m);
+            const double2 x = a.sint[((int64_t)f * a.nspec + ix) * a.B + b];
+            const double sc = f > 0 ? a.zd[ix] : 1.0;
+            xv[rr][r] = make_double2(sc * x.x, sc * x.y);
+          }
         }
       }
-      uint32_t hi, lo;
-      // P-terms of parity q feed class q (B1_q); H-terms feed class 1 - q (B2_{1-q})
-      unsigned char *b1 = sB1 + q * (2 * N1 * KB * 4);
-      for (int c = 0; c < 2; ++c) {
-        const uint32_t off = core_off(8 * bl + 2 * f + c, k, N1 / 8);
-        split_tf32(c ? v.y : v.x, hi, lo);
-        *reinterpret_cast<uint32_t *>(b1 + off) = hi;
-        *reinterpret_cast<uint32_t *>(b1 + N1 * KB * 4 + off) = lo;
-      }
-      if (f == 0) {
-        for (int c = 6; c < 8; ++c) {
-          const uint32_t off = core_off(8 * bl + c, k, N1 / 8);
-          *reinterpret_cast<uint32_t *>(b1 + off) = 0u;
-          *reinterpret_cast<uint32_t *>(b1 + N1 * KB * 4 + off) = 0u;
+#pragma unroll
+      for (int rr = 0; rr < RMAX; ++rr) {
+        const int u = tid + rr * THREADS;
+        if (u >= nun) continue;
+        const int q = u / ((KB / 4) * 4 * G), u2 = u - q * ((KB / 4) * 4 * G);
+        const int kq = u2 / (4 * G), rem = u2 - kq * (4 * G), bl = rem >> 2, f = rem & 3;
+        uint32_t hi[2][4], lo[2][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          split_tf32(xv[rr][r].x, hi[0][r], lo[0][r]);
+          split_tf32(xv[rr][r].y, hi[1][r], lo[1][r]);
         }
-      } else {
+        unsigned char *b1 = sB1 + q * (2 * N1 * KB * 4);
         unsigned char *b2 = sB2 + (1 - q) * (2 * N2 * KB * 4);
+#pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const uint32_t off = core_off(4 * bl + 2 * (f - 1) + c, k, N2 / 8);
-          split_tf32(c ? v.y : v.x, hi, lo);
-          *reinterpret_cast<uint32_t *>(b2 + off) = hi;
-          *reinterpret_cast<uint32_t *>(b2 + N2 * KB * 4 + off) = lo;
+          const uint32_t off = core_off(8 * bl + 2 * f + c, 4 * kq, N1 / 8);
+          *reinterpret_cast<uint4 *>(b1 + off) = make_uint4(hi[c][0], hi[c][1], hi[c][2], hi[c][3]);
+          *reinterpret_cast<uint4 *>(b1 + N1 * KB * 4 + off) = make_uint4(lo[c][0], lo[c][1], lo[c][2], lo[c][3]);
+          if (f == 1 || f == 2) {
+            const uint32_t off2 = core_off(4 * bl + 2 * (f - 1) + c, 4 * kq, N2 / 8);
+            *reinterpret_cast<uint4 *>(b2 + off2) = make_uint4(hi[c][0], hi[c][1], hi[c][2], hi[c][3]);
+            *reinterpret_cast<uint4 *>(b2 + N2 * KB * 4 + off2) =
+                make_uint4(lo[c][0], lo[c][1], lo[c][2], lo[c][3]);
+          }
         }
       }
     }
+    cp_async_wait_all();
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -445,11 +485,12 @@ __global__ void __launch_bounds__(128) leg_syn_tc_kernel(TcArgs a) {
   if (!ok) {
     if (tid == 0) atomicExch(a.err, 1);
   } else {
-    const int j = jt * TM + warp * 32 + (tid & 31);
-    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+    const int wq = warp & 3, half = warp >> 2;
+    const int j = jt * TM + wq * 32 + (tid & 31);
+    const uint32_t lane_addr = tbase + ((uint32_t)(wq * 32) << 16);
     const int M1 = a.N + 1, ncol = 3 * a.B;
     const double fm = (double)m;
-    for (int bl = 0; bl < G; ++bl) {
+    for (int bl = half * (G / 2); bl < (half + 1) * (G / 2); ++bl) {
       double2 F[2][3];
       for (int cls = 0; cls < 2; ++cls) {
         float d1[8], d2[4];
@@ -555,7 +596,7 @@ cudaError_t launch_leg_ana_tc(Plan &pl, const double2 *four, double2 *sint, int 
   TcArgs a{pl.tc_tab_ana, pl.tc_work_ana, const_cast<double2 *>(four), sint, zd, pl.dev_err, pl.N, pl.nlat,
            pl.J, B, G, 0, pl.nspec};
   dim3 grid((unsigned)pl.tc_nwork_ana, (unsigned)((B + G - 1) / G));
-  leg_ana_tc_kernel<<<grid, 128, ana_smem(G), st>>>(a);
+  leg_ana_tc_kernel<<<grid, THREADS, ana_smem(G), st>>>(a);
   return cudaGetLastError();
 }
 
@@ -565,7 +606,7 @@ cudaError_t launch_leg_syn_tc(Plan &pl, const double2 *sint, double2 *four, int 
   TcArgs a{pl.tc_tab_syn, pl.tc_work_syn, four, const_cast<double2 *>(sint), zd, pl.dev_err, pl.N, pl.nlat,
            pl.J, B, G, 0, pl.nspec};
   dim3 grid((unsigned)pl.tc_nwork_syn, (unsigned)((B + G - 1) / G));
-  leg_syn_tc_kernel<<<grid, 128, syn_smem(G), st>>>(a);
+  leg_syn_tc_kernel<<<grid, THREADS, syn_smem(G), st>>>(a);
   return cudaGetLastError();
 }
 

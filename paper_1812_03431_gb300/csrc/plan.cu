@@ -40,26 +40,59 @@ double eps_nm(int n, int m) {
   return std::sqrt(((double)n * n - (double)m * m) / (4.0 * n * n - 1.0));
 }
 
-// Orthonormal Pbar_n^m and H_n^m = (1-mu^2) dPbar/dmu for n = m..N at one mu,
-// by the standard m-diagonal seed and the three-term recurrence in n.
-void alp_column(int m, int N, double mu, double *P, double *H) {
-  const double s = std::sqrt(1.0 - mu * mu);
-  double pmm = 1.0 / std::sqrt(2.0);
-  for (int k = 1; k <= m; ++k) pmm *= std::sqrt((2.0 * k + 1.0) / (2.0 * k)) * s;
-  const int K = N - m + 2;  // one extra degree for H_N
-  std::vector<double> p(K);
-  p[0] = pmm;
-  if (K > 1) p[1] = std::sqrt(2.0 * m + 3.0) * mu * pmm;
-  for (int i = 2; i < K; ++i) {
-    const int n = m + i;
-    p[i] = (mu * p[i - 1] - eps_nm(n - 1, m) * p[i - 2]) / eps_nm(n, m);
+// Pole-independent zeta weights W_n = sum_k beta_k / (alpha_k + i tau sigma_n) and the
+// adjoint's sum_k conj(beta_k) / (conj(alpha_k) - i tau sigma_n); zero for rows that
+// are not state (zeta_0^0).
+__global__ void zeta_weights_kernel(const double *coef, const int32_t *m_of, const double2 *alpha,
+                                    const double2 *beta, int P, int64_t NS, double tau, double2 *wf, double2 *wa) {
+  const int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= NS) return;
+  const double sig = coef[4 * ix + 0];
+  const double G = coef[4 * ix + 3];  // n (n + 1) / a^2, zero only at n = 0
+  double2 sf = make_double2(0, 0), sa = make_double2(0, 0);
+  if (G > 0.0 || m_of[ix] > 0) {
+    for (int k = 0; k < P; ++k) {
+      const double2 al = alpha[k], be = beta[k];
+      // beta / (alpha + i tau sigma)
+      double dr = al.x, di = al.y + tau * sig, d = dr * dr + di * di;
+      sf.x += (be.x * dr + be.y * di) / d;
+      sf.y += (be.y * dr - be.x * di) / d;
+      // conj(beta) / (conj(alpha) - i tau sigma)
+      dr = al.x;
+      di = -al.y - tau * sig;
+      d = dr * dr + di * di;
+      sa.x += (be.x * dr - be.y * di) / d;
+      sa.y += (-be.y * dr - be.x * di) / d;
+    }
   }
-  for (int i = 0; i <= N - m; ++i) {
-    const int n = m + i;
-    P[i] = p[i];
-    double h = -n * eps_nm(n + 1, m) * p[i + 1];
-    if (i > 0) h += (n + 1) * eps_nm(n, m) * p[i - 1];
-    H[i] = h;
+  wf[ix] = sf;
+  wa[ix] = sa;
+}
+
+// Orthonormal Pbar_n^m(mu_j) and H_n^m(mu_j) for the northern latitudes j < J, one
+// thread per (m, j): the m-diagonal seed and the three-term recurrence in n (the same
+// recurrences as the oracle's tables, written independently).  Layout [idx(m, n)][J].
+__global__ void alp_tables_kernel(const double *mu_all, int N, int J, double *tabP, double *tabH) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)(N + 1) * J) return;
+  const int m = (int)(t / J), j = (int)(t - (int64_t)m * J);
+  const double mu = mu_all[j];
+  const double s = sqrt(1.0 - mu * mu);
+  double pmm = 1.0 / sqrt(2.0);
+  for (int k = 1; k <= m; ++k) pmm *= sqrt((2.0 * k + 1.0) / (2.0 * k)) * s;
+  const int64_t idx0 = (int64_t)m * (2 * N + 3 - m) / 2;
+  auto eps = [m](int n) { return n <= m ? 0.0 : sqrt(((double)n * n - (double)m * m) / (4.0 * n * n - 1.0)); };
+  // p_{n-1}, p_n, p_{n+1} rolling; H_n needs p_{n-1} and p_{n+1}
+  double pm1 = 0.0, p0 = pmm;
+  double p1 = sqrt(2.0 * m + 3.0) * mu * pmm;  // degree m + 1
+  for (int n = m; n <= N; ++n) {
+    const double h = -n * eps(n + 1) * p1 + (n > m ? (n + 1) * eps(n) * pm1 : 0.0);
+    tabP[(idx0 + n - m) * J + j] = p0;
+    tabH[(idx0 + n - m) * J + j] = h;
+    const double p2 = (mu * p1 - eps(n + 1) * p0) / eps(n + 2);  // degree n + 2
+    pm1 = p0;
+    p0 = p1;
+    p1 = p2;
   }
 }
 
@@ -140,7 +173,6 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   std::vector<double> coef(4 * NS, 0.0);
   std::vector<int32_t> m_of(NS);
   std::vector<uint8_t> rflags(3 * NS, 0);
-  std::vector<double2> wf(NS, make_double2(0, 0)), wa(NS, make_double2(0, 0));
   std::vector<double> zd_syn(NS), zd_ana_adj(NS), zd_one(NS, 1.0), zd_mone(NS, -1.0);
   for (int m = 0; m <= N; ++m) {
     const int nmin = std::max(m, 1);
@@ -166,15 +198,6 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
       rflags[2 * NS + ix] = staterow ? 1 : 2;
       bool zp = staterow && ((n - 1 >= nmin) || (n + 1 <= N));
       rflags[1 * NS + ix] = staterow ? (zp ? 1 : 0) : 2;
-      if (staterow) {
-        cplx sf(0, 0), sa(0, 0);
-        for (int k = 0; k < P; ++k) {
-          sf += pl->beta[k] / (pl->alpha[k] + cplx(0, tau * sig));
-          sa += std::conj(pl->beta[k]) / (std::conj(pl->alpha[k]) - cplx(0, tau * sig));
-        }
-        wf[ix] = make_double2(sf.real(), sf.imag());
-        wa[ix] = make_double2(sa.real(), sa.imag());
-      }
     }
   }
   cplx sphf(0, 0), spha(0, 0);
@@ -187,8 +210,11 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   if ((e = upload(&pl->coef_dev, coef, &bytes))) return fail("coef", e);
   if ((e = upload(&pl->m_of_dev, m_of, &bytes))) return fail("m_of", e);
   if ((e = upload(&pl->rflags_dev, rflags, &bytes))) return fail("rflags", e);
-  if ((e = upload(&pl->w_fwd, wf, &bytes))) return fail("w", e);
-  if ((e = upload(&pl->w_adj, wa, &bytes))) return fail("w", e);
+  if ((e = dalloc(&pl->w_fwd, NS, &bytes))) return fail("w", e);
+  if ((e = dalloc(&pl->w_adj, NS, &bytes))) return fail("w", e);
+  zeta_weights_kernel<<<(unsigned)((NS + 127) / 128), 128>>>(pl->coef_dev, pl->m_of_dev, pl->alpha_dev,
+                                                             pl->beta_dev, P, NS, tau, pl->w_fwd, pl->w_adj);
+  if ((e = cudaGetLastError())) return fail("zeta weights", e);
   if ((e = upload(&pl->zd_syn, zd_syn, &bytes))) return fail("zd", e);
   if ((e = upload(&pl->zd_ana_adj, zd_ana_adj, &bytes))) return fail("zd", e);
   if ((e = upload(&pl->zd_one, zd_one, &bytes))) return fail("zd", e);
@@ -205,18 +231,13 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
     gauss_legendre_host(pl->nlat, mu, w);
     if ((e = upload(&pl->mu_dev, mu, &bytes))) return fail("mu", e);
     const int J = pl->J, nlat = pl->nlat;
-    std::vector<double> tP((size_t)NS * J), tH((size_t)NS * J);
-    std::vector<double> colP(N + 1), colH(N + 1);
-    for (int m = 0; m <= N; ++m)
-      for (int j = 0; j < J; ++j) {
-        alp_column(m, N, mu[j], colP.data(), colH.data());
-        for (int n = m; n <= N; ++n) {
-          tP[(size_t)spec_idx(N, m, n) * J + j] = colP[n - m];
-          tH[(size_t)spec_idx(N, m, n) * J + j] = colH[n - m];
-        }
-      }
-    if ((e = upload(&pl->tabP, tP, &bytes))) return fail("tables", e);
-    if ((e = upload(&pl->tabH, tH, &bytes))) return fail("tables", e);
+    if ((e = dalloc(&pl->tabP, (size_t)NS * J, &bytes))) return fail("tables", e);
+    if ((e = dalloc(&pl->tabH, (size_t)NS * J, &bytes))) return fail("tables", e);
+    {
+      const int64_t cols = (int64_t)(N + 1) * J;
+      alp_tables_kernel<<<(unsigned)((cols + 127) / 128), 128>>>(pl->mu_dev, N, J, pl->tabP, pl->tabH);
+      if ((e = cudaGetLastError())) return fail("tables", e);
+    }
     std::vector<double> sin_(3 * nlat), sout(3 * nlat);
     for (int j = 0; j < nlat; ++j) {
       const double cl = std::sqrt(1.0 - mu[j] * mu[j]);

@@ -417,10 +417,12 @@ __global__ void reduce_kernel(ReduceArgs a) {
   }
 }
 
-// [rows][cols] -> [cols][rows] of double2 via 32x32 shared tiles.
+// [rows][cols] -> [cols][rows] of double2 via 32x32 shared tiles (tiles indexed
+// linearly in blockIdx.x, so neither dimension is limited by gridDim.y).
 __global__ void transpose_kernel(const double2 *in, double2 *out, int64_t rows, int64_t cols) {
   __shared__ double2 tile[32][33];
-  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  const int64_t tiles_c = (cols + 31) / 32;
+  const int64_t c0 = (int64_t)(blockIdx.x % tiles_c) * 32, r0 = (int64_t)(blockIdx.x / tiles_c) * 32;
   for (int j = threadIdx.y; j < 32; j += blockDim.y) {
     int64_t r = r0 + j, c = c0 + threadIdx.x;
     if (r < rows && c < cols) tile[j][threadIdx.x] = in[r * cols + c];
@@ -529,16 +531,16 @@ cudaError_t launch_transpose_in(const double2 *user, double2 *sint, int64_t nspe
                                 cudaStream_t st) {
   // user [B][3 nspec] -> sint [3 nspec][B]
   int64_t rows = B, cols = 3 * nspec;
-  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(user, sint, rows, cols);
+  const int64_t tiles = ((cols + 31) / 32) * ((rows + 31) / 32);
+  transpose_kernel<<<(unsigned)tiles, dim3(32, 8), 0, st>>>(user, sint, rows, cols);
   return cudaGetLastError();
 }
 
 cudaError_t launch_transpose_out(const double2 *sint, double2 *user, int64_t nspec, int B, int,
                                  cudaStream_t st) {
   int64_t rows = 3 * nspec, cols = B;
-  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(sint, user, rows, cols);
+  const int64_t tiles = ((cols + 31) / 32) * ((rows + 31) / 32);
+  transpose_kernel<<<(unsigned)tiles, dim3(32, 8), 0, st>>>(sint, user, rows, cols);
   return cudaGetLastError();
 }
 
