@@ -399,9 +399,14 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out) {
       continue;
     }
     tried.push_back(L.slots);
+    // time the solve and the slot reduction together (more slots balance the solve
+    // better but make the reduction read more partial sums)
     launch_solve(pl, L, false, pl.s_in, B, 0, pl.P, true, st);  // warm-up
     cudaEventRecord(e0, st);
-    for (int rep = 0; rep < 2; ++rep) launch_solve(pl, L, false, pl.s_in, B, 0, pl.P, true, st);
+    for (int rep = 0; rep < 2; ++rep) {
+      launch_solve(pl, L, false, pl.s_in, B, 0, pl.P, true, st);
+      launch_reduce(pl, L, false, pl.s_in, pl.s_out, B, false, 0, st);
+    }
     cudaEventRecord(e1, st);
     e = cudaEventSynchronize(e1);
     float ms = 0;

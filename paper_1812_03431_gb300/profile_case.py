@@ -27,6 +27,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="pick the pole-slot layout by timing, as bench.py does")
     args = ap.parse_args()
     import torch
 
@@ -37,14 +38,15 @@ def main():
     nlat = args.nlat or nlon // 2
     plan = rexi.Plan(args.N, nlat, nlon, M=args.M, tau=args.tau, max_batch=args.batch, layout=args.layout,
                      precision=args.precision)
+    slots = plan.tune(args.batch) if args.tune else plan.info()["pole_slots"]
     S = torch.from_numpy(inputs.random_spectral(args.N, args.batch, 3)).cuda()
     x = plan.synthesize(S) if args.layout == "grid" else S
     y = None
     for _ in range(args.steps):
         y = plan.step_adjoint(x) if args.adjoint else plan.step(x)
     torch.cuda.synchronize()
-    print("profile_case ok: N=%d nlat=%d nlon=%d batch=%d layout=%s checksum=%.12e"
-          % (args.N, nlat, nlon, args.batch, args.layout, float(y.abs().sum())))
+    print("profile_case ok: N=%d nlat=%d nlon=%d batch=%d layout=%s pole_slots=%d checksum=%.12e"
+          % (args.N, nlat, nlon, args.batch, args.layout, slots, float(y.abs().sum())))
     plan.close()
 
 

@@ -186,3 +186,26 @@ def test_full_size_sampled_orders(torch, rexi):
     from oracle.sphere import idx
     sel = np.concatenate([np.arange(idx(m, m, N), idx(m, N, N) + 1) for m in ms])
     assert fieldwise(got[:2][..., sel], ref[..., sel]) < TOL
+
+
+@pytest.fixture(scope="module")
+def full_size_case():
+    """Inputs and the oracle's grid-layout step of state 0 at the bench's workload."""
+    N, nlat, nlon, M, B, tau = 341, 512, 1024, 256, 16, 1200.0
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    gs = ostep.GridStep(N, nlat, nlon, al, be, tau, C)
+    x0 = gs.synthesise(spectral_state(N, 1, 1005))
+    x = np.concatenate([x0, inputs.random_grid(B - 1, nlat, nlon, 5)])
+    return dict(N=N, nlat=nlat, nlon=nlon, B=B, tau=tau, al=al, be=be, x=x, ref=gs(x0))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("mixed", 1e-5)])
+def test_full_size_grid_step_bench_launch(torch, rexi, full_size_case, precision, tol):
+    """The bench's launch: T341, 1024x512, K=256, tau=1200 s, batch 16, grid layout.
+    The oracle computes the whole grid-layout step for state 0 of the batch."""
+    c = full_size_case
+    plan = rexi.Plan(c["N"], c["nlat"], c["nlon"], tau=c["tau"], max_batch=c["B"], alpha=c["al"], beta=c["be"],
+                     precision=precision)
+    got = plan.step(torch.from_numpy(c["x"]).cuda()).cpu().numpy()
+    plan.close()
+    assert fieldwise(got[:1], c["ref"], axis_f=-3) < tol
