@@ -33,7 +33,8 @@ FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve: 36 F
 # DRAM bytes (read + write) of one solve_kernel launch from the ncu capture at T170,
 # K=256, batch 16 (profiles/solve_kernel_t170_b16.md); traffic per row is constant, so a
 # launch of the bench workload moves this times rows(T341) / rows(T170).
-SOLVE_TRAFFIC_T170 = None  # re-captured after each change of the solve kernel
+SOLVE_TRAFFIC_T170 = 10.47e9  # re-captured after each change of the solve kernel
+SOLVE_TRAFFIC_SLOTS = 47      # pole-slot layout of that capture (traffic depends on it)
 
 
 def rows_of(N):
@@ -274,8 +275,10 @@ def main():
         "data": "synthetic", "config": {**workload_config(), "form": chosen, "pole_slots": r["slots"]},
         "roofline": {"bound": "alu", "kernel": "solve_kernel (FP64 banded solves + pole sum)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": (SOLVE_TRAFFIC_T170 * rows_of(W["N"]) / rows_of(170)) if SOLVE_TRAFFIC_T170 else None,
-                     "traffic_source": "ncu dram bytes at T170/K256/B16 scaled by rows to T341",
+                     "traffic": (SOLVE_TRAFFIC_T170 * rows_of(W["N"]) / rows_of(170))
+                     if SOLVE_TRAFFIC_T170 and r["slots"] == SOLVE_TRAFFIC_SLOTS else None,
+                     "traffic_source": "ncu dram bytes at T170/K256/B16, %d pole slots, scaled by rows to T341"
+                                       % SOLVE_TRAFFIC_SLOTS,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz",
                      "flops_per_launch": flops, "launch_ms": solve_ms},
         "stage_ms": r["stages"],
