@@ -104,3 +104,20 @@ def random_grid(batch, nlat, nlon, seed, scale=(50.0, 5.0, 5.0)):
     rng = np.random.default_rng(seed)
     x = rng.standard_normal((batch, 3, nlat, nlon))
     return x * np.asarray(scale)[None, :, None, None]
+
+
+BUMPS = ((0.2 * np.pi, np.pi / 3.0, 20.0), (1.2 * np.pi, -np.pi / 5.0, 80.0), (1.6 * np.pi, -np.pi / 4.0, 360.0))
+
+
+def gaussian_bumps(mu, nlon, consts=EARTH, bumps=BUMPS):
+    """The three-bump initial state of Sec. 6.2 on a grid with latitudes mu: (h', u, v)
+    [3, nlat, nlon], at rest, h' = sum of 0.1 Hbar exp(-p d^2) with d the great-circle
+    angle to the bump centre (lambda_c, phi_c)."""
+    phi = np.arcsin(np.asarray(mu))[:, None]
+    lam = 2.0 * np.pi * np.arange(nlon)[None, :] / nlon
+    h = np.zeros((phi.shape[0], nlon))
+    for lc, pc, p in bumps:
+        c = np.sin(pc) * np.sin(phi) + np.cos(pc) * np.cos(phi) * np.cos(lam - lc)
+        d = np.arccos(np.clip(c, -1.0, 1.0))
+        h += 0.1 * consts["mean_depth"] * np.exp(-d * d * p)
+    return np.stack([h, np.zeros_like(h), np.zeros_like(h)])
