@@ -93,6 +93,11 @@ typedef struct {
   const double *alpha;  /* optional: P complex poles (re, im interleaved); NULL -> computed */
   const double *beta;   /* optional: P complex weights, used as given (no renormalisation) */
   int32_t npoles;       /* P when alpha/beta are given */
+  int32_t fsphere;      /* 1: constant Coriolis parameter f = 2 Omega (the f-sphere of Sec. 4,
+                           used for the eigenvalue analysis of Sec. 6.3): every degree n is a
+                           closed 3x3 system solved in closed form, no banded solves; 0: the
+                           rotating sphere, f = 2 Omega mu (default).  rexi_ragged_create
+                           rejects f-sphere plans. */
 } rexi_params;
 
 /* Fill *p with the defaults above (ntrunc = 63, nlat = 96, nlon = 192, M = 128,

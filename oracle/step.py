@@ -67,7 +67,8 @@ def _check_band(A):
     return n
 
 
-def rexi_step_spectral(U, N, alpha, beta, tau, c=Consts(), adjoint=False, ms=None, real_m0=True):
+def rexi_step_spectral(U, N, alpha, beta, tau, c=Consts(), adjoint=False, ms=None, real_m0=True,
+                       fsphere=False):
     """Apply sum_n beta_n (alpha_n + tau L)^{-1} to spectral states.
 
     U: [..., 3, nspec] complex (Phi, zeta, delta).  With ``adjoint`` the
@@ -75,13 +76,14 @@ def rexi_step_spectral(U, N, alpha, beta, tau, c=Consts(), adjoint=False, ms=Non
     ``ms`` restricts the work to a subset of zonal orders (other m left zero).
     ``real_m0=False`` keeps the m = 0 result complex (a single pole is not a
     conjugate-symmetric set, so its m = 0 response is complex).
+    ``fsphere`` uses the constant-f operator of Sec. 4 (eigenvalue analysis).
     """
     U = np.asarray(U, dtype=np.complex128)
     out = np.zeros_like(U)
     lead = U.shape[:-2]
     ms = range(N + 1) if ms is None else ms
     for m in ms:
-        A = tau * operator_m(m, N, c)
+        A = tau * operator_m(m, N, c, fsphere)
         if adjoint:
             A = A.conj().T
         _check_band(A)
@@ -105,9 +107,10 @@ def rexi_step_spectral(U, N, alpha, beta, tau, c=Consts(), adjoint=False, ms=Non
 class GridStep:
     """REXI step in grid layout: (h', u, v) on an nlat x nlon Gaussian grid."""
 
-    def __init__(self, N, nlat, nlon, alpha, beta, tau, c=Consts()):
+    def __init__(self, N, nlat, nlon, alpha, beta, tau, c=Consts(), fsphere=False):
         self.N, self.g = N, Grid(N, nlat, nlon)
         self.alpha, self.beta, self.tau, self.c = alpha, beta, tau, c
+        self.fsphere = fsphere
 
     # grid (h', u, v) -> spectral (Phi, zeta, delta)
     def analyse(self, x):
@@ -127,7 +130,7 @@ class GridStep:
 
     def __call__(self, x):
         S = self.analyse(np.asarray(x, dtype=np.float64))
-        S = rexi_step_spectral(S, self.N, self.alpha, self.beta, self.tau, self.c)
+        S = rexi_step_spectral(S, self.N, self.alpha, self.beta, self.tau, self.c, fsphere=self.fsphere)
         return self.synthesise(S)
 
     # ---- transposes of the grid-layout stages --------------------------------
@@ -193,5 +196,6 @@ class GridStep:
         S = self.synthesise_T(y)
         m0 = slice(0, self.N + 1)
         S[..., m0] = S[..., m0].real  # m = 0 cotangents of a real field are real
-        S = rexi_step_spectral(S, self.N, self.alpha, self.beta, self.tau, self.c, adjoint=True)
+        S = rexi_step_spectral(S, self.N, self.alpha, self.beta, self.tau, self.c, adjoint=True,
+                               fsphere=self.fsphere)
         return self.analyse_T(S)

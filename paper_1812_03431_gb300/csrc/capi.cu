@@ -84,7 +84,7 @@ rexi_status check_io2(const Plan &pl, const void *in, const void *out, int B, bo
 }
 
 rexi_status ensure_adjoint_factors(Plan &pl) {
-  if (pl.fac_adj) return REXI_OK;
+  if (pl.fac_adj || pl.prm.fsphere) return REXI_OK;
   const size_t n = (size_t)F_NCOMP * pl.nrows * pl.P;
   cudaError_t e = cudaMalloc(&pl.fac_adj, n * sizeof(double2));
   if (e != cudaSuccess) {
@@ -101,6 +101,11 @@ rexi_status ensure_adjoint_factors(Plan &pl) {
 
 // Spectral REXI core on the plan's internal layout: s_in -> s_out.
 rexi_status core(Plan &pl, int B, bool adjoint, cudaStream_t st, Marks &mk) {
+  if (pl.prm.fsphere) {
+    mk.mark(ST_SOLVE);
+    cudaError_t e = launch_fsphere(pl, adjoint, pl.s_in, pl.s_out, B, false, 0, st);
+    return e == cudaSuccess ? REXI_OK : cuda_fail("f-sphere solve", e);
+  }
   SolveLayout *lay = nullptr;
   rexi_status r = get_layout(pl, B, false, &lay);
   if (r != REXI_OK) return r;
@@ -310,10 +315,14 @@ rexi_status rexi_solve_pole(rexi_plan *plan, int32_t k, const void *in_dev, void
   if (r != REXI_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SolveLayout *lay = nullptr;
-  if ((r = get_layout(pl, B, true, &lay)) != REXI_OK) return r;
+  if (!pl.prm.fsphere && (r = get_layout(pl, B, true, &lay)) != REXI_OK) return r;
   cudaError_t e = launch_transpose_in(static_cast<const double2 *>(in_dev), pl.s_in, pl.nspec, B, st);
-  if (e == cudaSuccess) e = launch_solve(pl, *lay, false, pl.s_in, B, k, k + 1, true, st);
-  if (e == cudaSuccess) e = launch_reduce(pl, *lay, false, pl.s_in, pl.s_out, B, true, k, st);
+  if (pl.prm.fsphere) {
+    if (e == cudaSuccess) e = launch_fsphere(pl, false, pl.s_in, pl.s_out, B, true, k, st);
+  } else {
+    if (e == cudaSuccess) e = launch_solve(pl, *lay, false, pl.s_in, B, k, k + 1, true, st);
+    if (e == cudaSuccess) e = launch_reduce(pl, *lay, false, pl.s_in, pl.s_out, B, true, k, st);
+  }
   if (e == cudaSuccess) e = launch_transpose_out(pl.s_out, static_cast<double2 *>(out_dev), pl.nspec, B, pl.N, st);
   return e == cudaSuccess ? REXI_OK : cuda_fail("solve_pole", e);
 }
@@ -348,6 +357,10 @@ rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots) {
   Plan &pl = *plan->pl;
   if (batch < 1 || batch > pl.prm.max_batch) { set_error("rexi_tune: batch must be in [1, max_batch]"); return REXI_EINVAL; }
   int s = 0;
+  if (pl.prm.fsphere) {  // no banded solves, nothing to tune
+    if (slots) *slots = 0;
+    return REXI_OK;
+  }
   rexi_status r = tune_layout(pl, batch, &s);
   if (r == REXI_OK && slots) *slots = s;
   return r;

@@ -69,9 +69,9 @@ rexi_status rexi_ragged_create(rexi_plan *const *plans, int32_t nplans, int32_t 
   rexi_ragged *rg = new rexi_ragged();
   rg->max_states = max_states;
   for (int i = 0; i < nplans; ++i) {
-    if (!plans[i] || !plans[i]->pl || plans[i]->pl->prm.layout != REXI_SPECTRAL) {
+    if (!plans[i] || !plans[i]->pl || plans[i]->pl->prm.layout != REXI_SPECTRAL || plans[i]->pl->prm.fsphere) {
       delete rg;
-      set_error("rexi_ragged_create: every plan must exist and use REXI_SPECTRAL");
+      set_error("rexi_ragged_create: every plan must exist, use REXI_SPECTRAL and the rotating sphere");
       return REXI_EINVAL;
     }
     rg->plans.push_back(plans[i]->pl);

@@ -139,6 +139,9 @@ enum Stage { ST_FFT_FWD = 0, ST_LEG_ANA, ST_SOLVE, ST_REDUCE, ST_LEG_SYN, ST_FFT
 
 // ---- kernels (launchers) ------------------------------------------------------------
 cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st);
+// f-sphere plans: closed-form per-degree solves and the pole sum, sin -> sout ([3][nspec][B])
+cudaError_t launch_fsphere(Plan &pl, bool adjoint, const double2 *sin, double2 *sout, int B, bool single,
+                           int pole, cudaStream_t st);
 cudaError_t launch_solve(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin,
                          int B, int pole_begin, int pole_end, bool use_beta, cudaStream_t st);
 // One plan's view for the solve kernels: factors, internal states, partial sums,

@@ -417,6 +417,67 @@ __global__ void reduce_kernel(ReduceArgs a) {
   }
 }
 
+// f-sphere (constant f = 2 Omega): per degree n the shifted system of the forward map
+//   s Phi - tau Phibar delta = rP,  s zeta - q delta = rZ,  s delta + q zeta + tau G Phi = rD
+// (q = 2 Omega tau, G = n(n+1)/a^2) closes in closed form:
+//   delta = (s rD - q rZ - tau G rP) / (s^2 + q^2 + tau^2 Phibar G),
+//   Phi = (rP + tau Phibar delta) / s,  zeta = (rZ + q delta) / s.
+// The adjoint map uses conj(s) and L^T:
+//   delta = (s rD + q rZ + tau Phibar rP) / (...),  Phi = (rP - tau G delta) / s,
+//   zeta = (rZ - q delta) / s.
+// One thread per (idx, state) sums beta_k x_k over the poles in ascending k.
+struct FsphereArgs {
+  const double2 *sin, *alpha, *beta;
+  double2 *sout;
+  const uint8_t *rflags;
+  const double *coef;
+  const int32_t *m_of;
+  int64_t nspec;
+  int B, k0, k1, single, realm0, adjoint;
+  double tau, q, phibar;
+};
+
+__global__ void fsphere_kernel(FsphereArgs a) {
+  const int64_t total = a.nspec * a.B;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ix = t / a.B;
+    const int64_t NB = a.nspec * a.B;
+    const double2 rP = a.sin[t], rZ = a.sin[NB + t], rD = a.sin[2 * NB + t];
+    const double G = a.coef[4 * ix + 3];
+    const double tg = a.tau * G, tp = a.tau * a.phibar, q = a.q;
+    double2 aP = make_double2(0, 0), aZ = aP, aD = aP;
+    for (int k = a.k0; k < a.k1; ++k) {
+      double2 s = a.alpha[k], be = a.single ? make_double2(1.0, 0.0) : a.beta[k];
+      if (a.adjoint) { s = cconj(s); be = cconj(be); }
+      double2 den = cmul(s, s);
+      den.x += q * q + tp * tg;
+      double2 num = cmul(s, rD);
+      double2 dl, ph, ze;
+      if (!a.adjoint) {
+        num = csub(num, cadd(cscale(rZ, q), cscale(rP, tg)));
+        dl = cdiv(num, den);
+        ph = cdiv(cadd(rP, cscale(dl, tp)), s);
+        ze = cdiv(cadd(rZ, cscale(dl, q)), s);
+      } else {
+        num = cadd(num, cadd(cscale(rZ, q), cscale(rP, tp)));
+        dl = cdiv(num, den);
+        ph = cdiv(csub(rP, cscale(dl, tg)), s);
+        ze = cdiv(csub(rZ, cscale(dl, q)), s);
+      }
+      aP = cfma(aP, be, ph);
+      aZ = cfma(aZ, be, ze);
+      aD = cfma(aD, be, dl);
+    }
+    double2 acc[3] = {aP, aZ, aD};
+    for (int f = 0; f < 3; ++f) {
+      if (a.rflags[f * a.nspec + ix] & 2) acc[f] = make_double2(0, 0);
+      if (a.realm0 && a.m_of[ix] == 0) acc[f].y = 0.0;
+      a.sout[f * NB + t] = acc[f];
+    }
+  }
+}
+
 // [rows][cols] -> [cols][rows] of double2 via 32x32 shared tiles (tiles indexed
 // linearly in blockIdx.x, so neither dimension is limited by gridDim.y).
 __global__ void transpose_kernel(const double2 *in, double2 *out, int64_t rows, int64_t cols) {
@@ -435,6 +496,32 @@ __global__ void transpose_kernel(const double2 *in, double2 *out, int64_t rows, 
 }
 
 }  // namespace
+
+cudaError_t launch_fsphere(Plan &pl, bool adjoint, const double2 *sin, double2 *sout, int B, bool single,
+                           int pole, cudaStream_t st) {
+  FsphereArgs a;
+  a.sin = sin;
+  a.sout = sout;
+  a.alpha = pl.alpha_dev;
+  a.beta = pl.beta_dev;
+  a.rflags = pl.rflags_dev;
+  a.coef = pl.coef_dev;
+  a.m_of = pl.m_of_dev;
+  a.nspec = pl.nspec;
+  a.B = B;
+  a.k0 = single ? pole : 0;
+  a.k1 = single ? pole + 1 : pl.P;
+  a.single = single ? 1 : 0;
+  a.realm0 = single ? 0 : 1;
+  a.adjoint = adjoint ? 1 : 0;
+  a.tau = pl.prm.tau;
+  a.q = 2.0 * pl.prm.omega * pl.prm.tau;
+  a.phibar = pl.prm.gravity * pl.prm.mean_depth;
+  const int64_t total = pl.nspec * B;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 127) / 128, (int64_t)pl.num_sms * 16));
+  fsphere_kernel<<<blocks, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st) {
   SetupArgs a;
@@ -617,6 +704,16 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
   WorkItem *items = reinterpret_cast<WorkItem *>(base + 2 * state_b + part_b + y_b);
   unsigned *counter = reinterpret_cast<unsigned *>(base + 2 * state_b + part_b + y_b + item_b);
 
+  if (pl.prm.fsphere) {  // closed-form per-degree solves: only the two state buffers are used
+    e = launch_transpose_in(static_cast<const double2 *>(in), s_in, pl.nspec, B, st);
+    if (e == cudaSuccess) e = launch_fsphere(pl, false, s_in, s_out, B, false, 0, st);
+    if (e == cudaSuccess) e = launch_transpose_out(s_out, static_cast<double2 *>(out), pl.nspec, B, pl.N, st);
+    if (e != cudaSuccess) {
+      set_error(std::string("rexi_step_static: ") + cudaGetErrorString(e));
+      return REXI_ECUDA;
+    }
+    return REXI_OK;
+  }
   e = launch_transpose_in(static_cast<const double2 *>(in), s_in, pl.nspec, B, st);
   if (e == cudaSuccess) {
     static_items_kernel<<<(nitems + 127) / 128, 128, 0, st>>>(items, nitems, nb, bw, pl.sys_dev);

@@ -213,14 +213,7 @@ def test_fsphere_closed_form_projectors():
         if mm == 0:
             ref[0, 0] = np.sum(be / al) * S[0, 0]
     ref[:, : N + 1] = ref[:, : N + 1].real
-    out = np.zeros_like(S)
-    import oracle.step as st
-    orig = swe.operator_m
-    try:
-        st.operator_m = lambda m, N_, c: orig(m, N_, c, fsphere=True)
-        out = rexi_step_spectral(S, N, al, be, tau, C)
-    finally:
-        st.operator_m = orig
+    out = rexi_step_spectral(S, N, al, be, tau, C, fsphere=True)
     for i in range(3):
         np.testing.assert_allclose(out[i], ref[i], rtol=0, atol=1e-12 * np.abs(ref[i]).max())
 
