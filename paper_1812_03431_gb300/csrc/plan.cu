@@ -220,10 +220,12 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   if ((e = upload(&pl->zd_one, zd_one, &bytes))) return fail("zd", e);
   if ((e = upload(&pl->zd_mone, zd_mone, &bytes))) return fail("zd", e);
 
-  // ---- solve factors (forward now; adjoint on first use)
-  const size_t nfac = (size_t)F_NCOMP * pl->nrows * P;
-  if ((e = dalloc(&pl->fac_fwd, nfac, &bytes))) return fail("factors", e);
-  if ((e = launch_factor_setup(*pl, false, 0))) return fail("factor setup", e);
+  // ---- solve factors (forward now; adjoint on first use); the f-sphere needs none
+  if (!prm.fsphere) {
+    const size_t nfac = (size_t)F_NCOMP * pl->nrows * P;
+    if ((e = dalloc(&pl->fac_fwd, nfac, &bytes))) return fail("factors", e);
+    if ((e = launch_factor_setup(*pl, false, 0))) return fail("factor setup", e);
+  }
 
   // ---- grid, Legendre tables, FFT
   {  // tables serve the grid layout and rexi_analyze / rexi_synthesize
@@ -293,9 +295,10 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   if ((e = dalloc(&pl->four, (size_t)pl->nlat * (N + 1) * 3 * B, &bytes))) return fail("fourier", e);
   if ((e = dalloc(&pl->s_in, (size_t)3 * NS * B, &bytes))) return fail("spectral", e);
   if ((e = dalloc(&pl->s_out, (size_t)3 * NS * B, &bytes))) return fail("spectral", e);
-  // partial sums: at most 64 slots and ~2 GiB
+  // partial sums: at most 1024 slots and ~4 GiB (small batches need many slots to spread
+  // the poles over enough warps; the reduction reads every slot once per step)
   size_t per_slot = (size_t)3 * NS * B * sizeof(double2);
-  int cap = (int)std::min<size_t>(64, std::max<size_t>(1, (size_t)(2ull << 30) / per_slot));
+  int cap = (int)std::min<size_t>(1024, std::max<size_t>(1, (size_t)(4ull << 30) / per_slot));
   cap = std::min(cap, P);
   pl->partial_cap = (size_t)cap;
   if ((e = dalloc(&pl->partial, (size_t)cap * 3 * NS * B, &bytes))) return fail("partials", e);
