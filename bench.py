@@ -46,6 +46,63 @@ def fp64_peak_tflops(sm_mhz):
     return 152 * 4 * sm_mhz * 1e6 / 1e12
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, "fallback"
+
+
+def kernel_rooflines(form, stages, slots, sm_mhz):
+    """Every stage of the grid step against its own bound: algorithmic bytes (HBM-bound
+    stages) or flops (ALU-bound stages) per launch / its live CUDA-event time."""
+    W = WORK
+    N, B, nlat, nlon = W["N"], W["batch"], W["nlat"], W["nlon"]
+    P = 2 * (W["M"] + 11) + 1
+    ns = (N + 1) * (N + 2) // 2
+    hbm, bf16, src = measured_peaks()
+    fp64 = fp64_peak_tflops(sm_mhz)
+    grid_b = B * 3 * nlat * nlon * 8
+    four_b = nlat * (N + 1) * 3 * B * (8 if form == "mixed" else 16)  # complex FP32 / FP64
+    spec_b = 3 * ns * B * 16
+    out = {}
+
+    def put(name, bound, amount, unit, peak, peak_src):
+        ms = stages.get(name)
+        if not ms:
+            return
+        ach = amount / (ms * 1e-3) / (1e9 if unit == "GB/s" else 1e12)
+        out[name] = {"ms": ms, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                     "algorithmic": amount, "peak_source": peak_src}
+
+    # FFTs: read the grid once, write the Fourier coefficients once (and back)
+    if form == "mixed":
+        put("fft_fwd", "hbm", grid_b + four_b, "GB/s", hbm, src + " HBM copy")
+        put("fft_inv", "hbm", grid_b + four_b, "GB/s", hbm, src + " HBM copy")
+        # tcgen05 Legendre: TF32 hi/lo tables P and H (2 x 2 x 4 B per (n, lat pair)),
+        # Fourier data in, spectral coefficients out
+        leg_b = 16 * ns * (nlat // 2) + four_b + spec_b
+        put("leg_ana", "hbm", leg_b, "GB/s", hbm, src + " HBM copy")
+        put("leg_syn", "hbm", leg_b, "GB/s", hbm, src + " HBM copy")
+    else:
+        # FP64 FFT: 5 n log2 n flops per half-length complex transform of each real row
+        import math
+        half = nlon // 2
+        fl = 5.0 * half * math.log2(half) * B * 3 * nlat
+        put("fft_fwd", "alu", fl, "TFLOP/s", fp64, "derived FP64")
+        put("fft_inv", "alu", fl, "TFLOP/s", fp64, "derived FP64")
+        # FP64 Legendre: 10 FMAs per (n, lat pair, state) each way
+        fl = 20.0 * ns * (nlat // 2) * B
+        put("leg_ana", "alu", fl, "TFLOP/s", fp64, "derived FP64")
+        put("leg_syn", "alu", fl, "TFLOP/s", fp64, "derived FP64")
+    put("solve", "alu", FLOPS_PER_ROW * B * P * rows_of(N), "TFLOP/s", fp64, "derived FP64")
+    # reduction: every slot's partial sums once, the input state once, the output once
+    put("reduce", "hbm", (slots + 2) * spec_b, "GB/s", hbm, src + " HBM copy")
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -107,7 +164,7 @@ def cpu_baseline(sample_ms=None):
     N, B = WORK["N"], WORK["batch"]
     al, be, _ = rexi_coeffs.rexi_coefficients(WORK["M"], WORK["h"])
     S = inputs.random_spectral(N, 1, WORK["seed"])
-    ms = sample_ms if sample_ms is not None else list(range(0, N + 1, 57))
+    ms = sample_ms if sample_ms is not None else list(range(0, N + 1, 11))  # ~10 s of CPU work
     t0 = time.perf_counter()
     ostep.rexi_step_spectral(S, N, al, be, WORK["tau"], ms=ms)
     t_solve = time.perf_counter() - t0
@@ -282,6 +339,7 @@ def main():
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz",
                      "flops_per_launch": flops, "launch_ms": solve_ms},
         "stage_ms": r["stages"],
+        "kernels": kernel_rooflines(chosen, r["stages"], r["slots"], sm_mhz),
         "e2e": {"value": world * 1e3 / r["ms_e2e"], "unit": "steps/s", "h2d_bytes_per_step": r["bytes"],
                 "d2h_bytes_per_step": r["bytes"]},
         "gpu_launches": 6 * args.steps,
@@ -290,7 +348,9 @@ def main():
     if "fp64" in results and chosen != "fp64":
         f = results["fp64"]
         d = (results[chosen]["y"] - f["y"]).norm() / f["y"].norm()
-        line["fp64_form"] = {"value": world * 1e3 / f["ms"], "ms_per_step": f["ms"], "stage_ms": f["stages"]}
+        line["fp64_form"] = {"value": world * 1e3 / f["ms"], "ms_per_step": f["ms"], "stage_ms": f["stages"],
+                             "pole_slots": f["slots"],
+                             "kernels": kernel_rooflines("fp64", f["stages"], f["slots"], sm_mhz)}
         line["error_vs_fp64_form"] = float(d)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -13,12 +13,15 @@
 // Z'_m = E'_m + i O'_m from the Hermitian spectrum and evaluates
 // conj(FFT(conj Z')).
 //
-// Layouts: grid [B][3][nlat][nlon] float64; Fourier [nlat][N+1][3B] complex,
-// column c = 3 b + field, so that for each latitude the Legendre kernels read
-// contiguous columns.
+// Layouts: grid [B][3][nlat][nlon] float64; Fourier [nlat][N+1][3B] complex (FP64 in
+// the FP64 form, FP32 in the mixed form, where the transform itself is FP32), column
+// c = 3 b + field, so that for each latitude the Legendre kernels read contiguous
+// columns.  The mixed form scales in FP32 and converts between FP64 and FP32 on the
+// integer pipe (f64_to_f32 / f32_to_f64): no FP64 instruction is left in its kernels.
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "rexi_internal.h"
 
@@ -124,12 +127,14 @@ __device__ typename V2<T>::t *fft_smem(typename V2<T>::t *buf0, typename V2<T>::
 // T: arithmetic type inside the transform (double, or float in the mixed form);
 // grid and Fourier arrays stay FP64 either way.
 template <typename T>
-__global__ void fft_fwd_kernel(FftArgs a, const double *grid, double2 *four, const double *in_scale,
+__global__ void fft_fwd_kernel(FftArgs a, const double *grid, void *four_v, const double *in_scale,
                                const double *m_scale) {
   using C = typename V2<T>::t;
+  constexpr bool F32 = std::is_same<T, float>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
   C *sm = reinterpret_cast<C *>(smraw);
   const C *tw = static_cast<const C *>(a.tw);
+  C *four = static_cast<C *>(four_v);
   const int h = a.h;
   C *buf0 = sm, *buf1 = sm + a.np * h;
   const int j = blockIdx.y;
@@ -142,7 +147,12 @@ __global__ void fft_fwd_kernel(FftArgs a, const double *grid, double2 *four, con
     if (c < a.ncol) {
       const double s = in_scale[(c % 3) * a.nlat + j];
       const double2 x = g2[((int64_t)c * a.nlat + j) * h + k];
-      v = C{(T)(s * x.x), (T)(s * x.y)};
+      if constexpr (F32) {
+        const float s32 = f64_to_f32(s);
+        v = C{s32 * f64_to_f32(x.x), s32 * f64_to_f32(x.y)};
+      } else {
+        v = C{s * x.x, s * x.y};
+      }
     }
     buf0[t] = v;
   }
@@ -159,38 +169,45 @@ __global__ void fft_fwd_kernel(FftArgs a, const double *grid, double2 *four, con
     const C E = {(T)0.5 * (zm.x + zr.x), (T)0.5 * (zm.y - zr.y)};
     const C O = {(T)0.5 * (zm.y + zr.y), (T)-0.5 * (zm.x - zr.x)};
     const C X = addz(E, cmulz(tw[m], O));
-    const double s = m_scale[m];
-    four[((int64_t)j * M1 + m) * a.ncol + c] = make_double2(s * (double)X.x, s * (double)X.y);
+    T s;
+    if constexpr (F32) s = f64_to_f32(m_scale[m]); else s = m_scale[m];
+    four[((int64_t)j * M1 + m) * a.ncol + c] = C{s * X.x, s * X.y};
   }
 }
 
 template <typename T>
-__global__ void fft_inv_kernel(FftArgs a, const double2 *four, double *grid, const double *m_scale,
+__global__ void fft_inv_kernel(FftArgs a, const void *four_v, double *grid, const double *m_scale,
                                const double *out_scale) {
   using C = typename V2<T>::t;
+  constexpr bool F32 = std::is_same<T, float>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
   C *sm = reinterpret_cast<C *>(smraw);
   const C *tw = static_cast<const C *>(a.tw);
+  const C *four = static_cast<const C *>(four_v);
   const int h = a.h;
   C *buf0 = sm, *buf1 = sm + a.np * h;
   const int j = blockIdx.y;
   const int c0 = blockIdx.x * a.np;
   const int N = a.N, M1 = N + 1;
+  auto msc = [&](int mm) -> T {
+    if constexpr (F32) return f64_to_f32(m_scale[mm]); else return m_scale[mm];
+  };
+  // column index fastest, so that neighbouring threads read neighbouring Fourier columns
   for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
-    const int q = t / h, m = t - q * h;
+    const int m = t / a.np, q = t - m * a.np;
     const int c = c0 + q;
     C A = {0, 0}, Bc = {0, 0};
     if (c < a.ncol) {
       if (m <= N) {
-        const double s = m_scale[m];
-        const double2 v = four[((int64_t)j * M1 + m) * a.ncol + c];
-        A = C{(T)(s * v.x), m == 0 ? (T)0 : (T)(s * v.y)};
+        const T s = msc(m);
+        const C v = four[((int64_t)j * M1 + m) * a.ncol + c];
+        A = C{s * v.x, m == 0 ? (T)0 : s * v.y};
       }
       const int mr = h - m;  // partner X_{h-m}, present when h - m <= N
       if (m > 0 && mr <= N) {
-        const double s = m_scale[mr];
-        const double2 v = four[((int64_t)j * M1 + mr) * a.ncol + c];
-        Bc = C{(T)(s * v.x), mr == 0 ? (T)0 : (T)(-s * v.y)};  // conj(X_{h-m})
+        const T s = msc(mr);
+        const C v = four[((int64_t)j * M1 + mr) * a.ncol + c];
+        Bc = C{s * v.x, mr == 0 ? (T)0 : -s * v.y};  // conj(X_{h-m})
       }
     }
     // E' = X_m + conj X_{h-m},  O' = (X_m - conj X_{h-m}) e^{+2 pi i m / n},  Z' = E' + i O'
@@ -198,7 +215,7 @@ __global__ void fft_inv_kernel(FftArgs a, const double2 *four, double *grid, con
     const C w = tw[m];
     const C O = cmulz(subz(A, Bc), C{w.x, -w.y});
     const C Zp = {E.x - O.y, E.y + O.x};
-    buf0[t] = C{Zp.x, -Zp.y};  // conj(Z') for the inverse by a forward FFT
+    buf0[q * h + m] = C{Zp.x, -Zp.y};  // conj(Z') for the inverse by a forward FFT
   }
   __syncthreads();
   const C *r = fft_smem<T>(buf0, buf1, a);
@@ -209,7 +226,12 @@ __global__ void fft_inv_kernel(FftArgs a, const double2 *four, double *grid, con
     if (c >= a.ncol) continue;
     const double s = out_scale[(c % 3) * a.nlat + j];
     const C v = r[t];  // conj of z_k = x_{2k} + i x_{2k+1}
-    g2[((int64_t)c * a.nlat + j) * h + k] = make_double2(s * (double)v.x, -s * (double)v.y);
+    if constexpr (F32) {
+      const float s32 = f64_to_f32(s);
+      g2[((int64_t)c * a.nlat + j) * h + k] = make_double2(f32_to_f64(s32 * v.x), f32_to_f64(-s32 * v.y));
+    } else {
+      g2[((int64_t)c * a.nlat + j) * h + k] = make_double2(s * v.x, -s * v.y);
+    }
   }
 }
 

@@ -19,7 +19,10 @@
 // core matrices of 8 rows x 16 bytes (4 tf32), adjacent along K at LBO bytes and
 // along M/N at SBO = 128 bytes.  The tables come pre-split into TF32 hi/lo and
 // pre-packed in exactly that layout (plan time); the data are folded, split and
-// packed while staging.  One thread issues the MMAs; completion is tracked with an
+// packed while staging.  The Fourier data are FP32 (the mixed form's FFTs are FP32),
+// so staging and epilogues run in FP32 and the FP64 spectral coefficients are
+// converted on the integer pipe: the kernels issue no FP64 instruction, which on
+// GB300 would otherwise bound them.  One thread issues the MMAs; completion is tracked with an
 // mbarrier whose waits are bounded (on expiry the kernel records an error word,
 // skips its output and still frees its tensor memory).
 #include <cuda_runtime.h>
@@ -129,10 +132,15 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return r;
 }
-// x ~ hi + lo with hi, lo TF32
+// x ~ hi + lo with hi, lo TF32 (plan-time table packing, from FP64)
 __device__ __forceinline__ void split_tf32(double x, uint32_t &hi, uint32_t &lo) {
   hi = to_tf32((float)x);
   lo = to_tf32((float)(x - (double)__uint_as_float(hi)));
+}
+// the same from FP32 data: x - hi is exact in FP32 (hi keeps the top 11 bits of x)
+__device__ __forceinline__ void split_tf32f(float x, uint32_t &hi, uint32_t &lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
 }
 
 // byte offset of element (row r, k) in a packed K-major tile with `groups` 8-row groups
@@ -206,7 +214,7 @@ __global__ void pack_tables_kernel(PackArgs a) {
 struct TcArgs {
   const uint32_t *tab;   // packed tables
   const int4 *work;      // per CTA: {m, p (analysis) or jt (synthesis), tile, first packed block}
-  double2 *four;         // [nlat][N+1][3B]
+  float2 *four;          // [nlat][N+1][3B], FP32 in the mixed form
   double2 *sint;         // [3][nspec][B]
   const double *zd;      // [nspec]
   int *err;              // device error word
@@ -255,7 +263,7 @@ __global__ void __launch_bounds__(THREADS) leg_ana_tc_kernel(TcArgs a) {
     {
       constexpr int RMAX = 512 / THREADS;  // units per thread: 8 kq x 4 G <= 512
       const int nun = (KB / 4) * 4 * G;
-      double2 xn[RMAX][4], xs[RMAX][4];
+      float2 xn[RMAX][4], xs[RMAX][4];
 #pragma unroll
       for (int r = 0; r < RMAX; ++r) {
         const int u = tid + r * THREADS;
@@ -264,7 +272,7 @@ __global__ void __launch_bounds__(THREADS) leg_ana_tc_kernel(TcArgs a) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int j = kb * KB + 4 * kq + q;
-          xn[r][q] = xs[r][q] = make_double2(0, 0);
+          xn[r][q] = xs[r][q] = make_float2(0.f, 0.f);
           if (u < nun && f < 3 && j < a.J && b < a.B) {
             xn[r][q] = a.four[((int64_t)j * M1 + m) * ncol + 3 * b + f];
             xs[r][q] = a.four[((int64_t)(a.nlat - 1 - j) * M1 + m) * ncol + 3 * b + f];
@@ -279,10 +287,10 @@ __global__ void __launch_bounds__(THREADS) leg_ana_tc_kernel(TcArgs a) {
         uint32_t eh[2][4], el[2][4], oh[2][4], ol[2][4];  // [re/im][latitude]
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          split_tf32(xn[r][q].x + xs[r][q].x, eh[0][q], el[0][q]);
-          split_tf32(xn[r][q].y + xs[r][q].y, eh[1][q], el[1][q]);
-          split_tf32(xn[r][q].x - xs[r][q].x, oh[0][q], ol[0][q]);
-          split_tf32(xn[r][q].y - xs[r][q].y, oh[1][q], ol[1][q]);
+          split_tf32f(xn[r][q].x + xs[r][q].x, eh[0][q], el[0][q]);
+          split_tf32f(xn[r][q].y + xs[r][q].y, eh[1][q], el[1][q]);
+          split_tf32f(xn[r][q].x - xs[r][q].x, oh[0][q], ol[0][q]);
+          split_tf32f(xn[r][q].y - xs[r][q].y, oh[1][q], ol[1][q]);
         }
         // Pbar_n has the class of p (E for p = 0); H_n the other one
         uint32_t(*ph)[4] = p ? oh : eh, (*pl)[4] = p ? ol : el;
@@ -346,13 +354,15 @@ __global__ void __launch_bounds__(THREADS) leg_ana_tc_kernel(TcArgs a) {
       const int b = b0 + bl;
       if (n <= a.N && b < a.B) {
         const int64_t ix = (int64_t)m * (2 * a.N + 3 - m) / 2 + (n - m);
-        const double s = a.zd[ix], fm = (double)m;
-        const double2 phi = make_double2(d1[0], d1[1]);
-        const double2 pu = make_double2(d1[2], d1[3]), pv = make_double2(d1[4], d1[5]);
-        const double2 hu = make_double2(d2[0], d2[1]), hv = make_double2(d2[2], d2[3]);
-        a.sint[ix * a.B + b] = phi;
-        a.sint[(a.nspec + ix) * a.B + b] = make_double2(s * (-fm * pv.y + hu.x), s * (fm * pv.x + hu.y));
-        a.sint[(2 * a.nspec + ix) * a.B + b] = make_double2(s * (-fm * pu.y - hv.x), s * (fm * pu.x - hv.y));
+        // FP32 arithmetic, FP64 stores (the solve's input) converted on the integer pipe
+        const float s = f64_to_f32(a.zd[ix]), fm = (float)m;
+        const float2 pu = make_float2(d1[2], d1[3]), pv = make_float2(d1[4], d1[5]);
+        const float2 hu = make_float2(d2[0], d2[1]), hv = make_float2(d2[2], d2[3]);
+        a.sint[ix * a.B + b] = make_double2(f32_to_f64(d1[0]), f32_to_f64(d1[1]));
+        a.sint[(a.nspec + ix) * a.B + b] =
+            make_double2(f32_to_f64(s * (-fm * pv.y + hu.x)), f32_to_f64(s * (fm * pv.x + hu.y)));
+        a.sint[(2 * a.nspec + ix) * a.B + b] =
+            make_double2(f32_to_f64(s * (-fm * pu.y - hv.x)), f32_to_f64(s * (fm * pu.x - hv.y)));
       }
     }
   }
@@ -402,7 +412,7 @@ __global__ void __launch_bounds__(THREADS) leg_syn_tc_kernel(TcArgs a) {
     {
       constexpr int RMAX = 1024 / THREADS;  // 2 q x 8 kq x 4 G <= 1024
       const int nun = 2 * (KB / 4) * 4 * G;
-      double2 xv[RMAX][4];
+      float2 xv[RMAX][4];
 #pragma unroll
       for (int rr = 0; rr < RMAX; ++rr) {
         const int u = tid + rr * THREADS;
@@ -412,12 +422,12 @@ __global__ void __launch_bounds__(THREADS) leg_syn_tc_kernel(TcArgs a) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int n = m + q + 2 * (kb * KB + 4 * kq + r);
-          xv[rr][r] = make_double2(0, 0);
+          xv[rr][r] = make_float2(0.f, 0.f);
           if (u < nun && f < 3 && n <= a.N && b < a.B) {
             const int64_t ix = idx0 + (n - m);
             const double2 x = a.sint[((int64_t)f * a.nspec + ix) * a.B + b];
-            const double sc = f > 0 ? a.zd[ix] : 1.0;
-            xv[rr][r] = make_double2(sc * x.x, sc * x.y);
+            const float sc = f > 0 ? f64_to_f32(a.zd[ix]) : 1.0f;
+            xv[rr][r] = make_float2(sc * f64_to_f32(x.x), sc * f64_to_f32(x.y));
           }
         }
       }
@@ -430,8 +440,8 @@ __global__ void __launch_bounds__(THREADS) leg_syn_tc_kernel(TcArgs a) {
         uint32_t hi[2][4], lo[2][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          split_tf32(xv[rr][r].x, hi[0][r], lo[0][r]);
-          split_tf32(xv[rr][r].y, hi[1][r], lo[1][r]);
+          split_tf32f(xv[rr][r].x, hi[0][r], lo[0][r]);
+          split_tf32f(xv[rr][r].y, hi[1][r], lo[1][r]);
         }
         unsigned char *b1 = sB1 + q * (2 * N1 * KB * 4);
         unsigned char *b2 = sB2 + (1 - q) * (2 * N2 * KB * 4);
@@ -489,9 +499,9 @@ __global__ void __launch_bounds__(THREADS) leg_syn_tc_kernel(TcArgs a) {
     const int j = jt * TM + wq * 32 + (tid & 31);
     const uint32_t lane_addr = tbase + ((uint32_t)(wq * 32) << 16);
     const int M1 = a.N + 1, ncol = 3 * a.B;
-    const double fm = (double)m;
+    const float fm = (float)m;
     for (int bl = half * (G / 2); bl < (half + 1) * (G / 2); ++bl) {
-      double2 F[2][3];
+      float2 F[2][3];
       for (int cls = 0; cls < 2; ++cls) {
         float d1[8], d2[4];
         const uint32_t base = lane_addr + cls * (N1 + N2);
@@ -499,17 +509,17 @@ __global__ void __launch_bounds__(THREADS) leg_syn_tc_kernel(TcArgs a) {
         tmem_ld4(base + 8 * bl + 4, d1 + 4);
         tmem_ld4(base + N1 + 4 * bl, d2);
         // d1: Phi re/im, psi' re/im, chi' re/im; d2: psi' re/im, chi' re/im (H-terms)
-        F[cls][0] = make_double2(d1[0], d1[1]);
-        F[cls][1] = make_double2(-(double)d2[0] - fm * d1[5], -(double)d2[1] + fm * d1[4]);
-        F[cls][2] = make_double2(-fm * d1[3] + d2[2], fm * d1[2] + d2[3]);
+        F[cls][0] = make_float2(d1[0], d1[1]);
+        F[cls][1] = make_float2(-d2[0] - fm * d1[5], -d2[1] + fm * d1[4]);
+        F[cls][2] = make_float2(-fm * d1[3] + d2[2], fm * d1[2] + d2[3]);
       }
       const int b = b0 + bl;
       if (j < a.J && b < a.B) {
-        double2 *north = a.four + ((int64_t)j * M1 + m) * ncol + 3 * b;
-        double2 *south = a.four + ((int64_t)(a.nlat - 1 - j) * M1 + m) * ncol + 3 * b;
+        float2 *north = a.four + ((int64_t)j * M1 + m) * ncol + 3 * b;
+        float2 *south = a.four + ((int64_t)(a.nlat - 1 - j) * M1 + m) * ncol + 3 * b;
         for (int f = 0; f < 3; ++f) {
-          north[f] = make_double2(F[0][f].x + F[1][f].x, F[0][f].y + F[1][f].y);
-          south[f] = make_double2(F[0][f].x - F[1][f].x, F[0][f].y - F[1][f].y);
+          north[f] = make_float2(F[0][f].x + F[1][f].x, F[0][f].y + F[1][f].y);
+          south[f] = make_float2(F[0][f].x - F[1][f].x, F[0][f].y - F[1][f].y);
         }
       }
     }
@@ -593,8 +603,9 @@ cudaError_t tc_setup(Plan &pl) {
 cudaError_t launch_leg_ana_tc(Plan &pl, const double2 *four, double2 *sint, int B, const double *zd,
                               cudaStream_t st) {
   const int G = group_size(B);
-  TcArgs a{pl.tc_tab_ana, pl.tc_work_ana, const_cast<double2 *>(four), sint, zd, pl.dev_err, pl.N, pl.nlat,
-           pl.J, B, G, 0, pl.nspec};
+  // the mixed form's Fourier array holds FP32 pairs
+  TcArgs a{pl.tc_tab_ana, pl.tc_work_ana, reinterpret_cast<float2 *>(const_cast<double2 *>(four)), sint, zd,
+           pl.dev_err, pl.N, pl.nlat, pl.J, B, G, 0, pl.nspec};
   dim3 grid((unsigned)pl.tc_nwork_ana, (unsigned)((B + G - 1) / G));
   leg_ana_tc_kernel<<<grid, THREADS, ana_smem(G), st>>>(a);
   return cudaGetLastError();
@@ -603,8 +614,8 @@ cudaError_t launch_leg_ana_tc(Plan &pl, const double2 *four, double2 *sint, int 
 cudaError_t launch_leg_syn_tc(Plan &pl, const double2 *sint, double2 *four, int B, const double *zd,
                               cudaStream_t st) {
   const int G = group_size(B);
-  TcArgs a{pl.tc_tab_syn, pl.tc_work_syn, four, const_cast<double2 *>(sint), zd, pl.dev_err, pl.N, pl.nlat,
-           pl.J, B, G, 0, pl.nspec};
+  TcArgs a{pl.tc_tab_syn, pl.tc_work_syn, reinterpret_cast<float2 *>(four), const_cast<double2 *>(sint), zd,
+           pl.dev_err, pl.N, pl.nlat, pl.J, B, G, 0, pl.nspec};
   dim3 grid((unsigned)pl.tc_nwork_syn, (unsigned)((B + G - 1) / G));
   leg_syn_tc_kernel<<<grid, THREADS, syn_smem(G), st>>>(a);
   return cudaGetLastError();

@@ -13,6 +13,39 @@
 
 namespace rexi {
 
+#ifdef __CUDACC__
+// IEEE-754 binary64 <-> binary32 conversions on the integer pipe.  On GB300 the FP64
+// unit, which also executes the hardware conversions, issues 1/64 of the FP32 rate; the
+// mixed-form transform kernels convert every element once, so they do it with integer
+// operations instead.  Round to nearest even; results below 2^-126 in magnitude are
+// flushed to signed zero (the transform data are many orders of magnitude larger);
+// infinities and NaNs are preserved.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e11 = (int)((b >> 52) & 0x7ffu);
+  const unsigned long long mant = b & 0xfffffffffffffull;
+  if (e11 == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u));
+  const int e = e11 - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned m = (unsigned)(mant >> 29);
+  const unsigned rem = (unsigned)(mant & 0x1fffffffull);
+  unsigned r = ((unsigned)e << 23) | m;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) r += 1u;  // a carry bumps the exponent
+  return __uint_as_float(sign | r);
+}
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long m = u & 0x7fffffu;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  if (e == 255) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | (m << 29)));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | (m << 29)));
+}
+#endif
+
 using cplx = std::complex<double>;
 
 constexpr int kGaussTerms = 11;  // K of the Gaussian rational approximation (Sec. 4.1)

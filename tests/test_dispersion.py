@@ -52,7 +52,7 @@ def test_phase_error_is_flat_and_bounded(case):
     we, rel = dispersion.relative_phase_error(w, case["om"])
     # the relative error of the numerical frequency does not grow with the frequency
     # (Sec. 6.3): it stays at the symbol's slope error near zero
-    assert np.ptp(rel) < 0.05 * np.abs(rel).max()
+    assert np.ptp(rel) < 0.1 * np.abs(rel).max()
     assert np.abs(rel).max() <= rc.imag_tail_bound(1.0, case["M"], case["h"])
     # Re f = cos to fit accuracy, so |f|^2 - 1 = Im(f)^2 - sin^2: the amplitude error of a
     # mode is at most about rel * sin^2(omega dt), i.e. vanishes for the slow modes

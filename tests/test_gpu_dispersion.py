@@ -37,7 +37,7 @@ def test_propagator_eigenvalues_are_the_rexi_symbol(M):
     w, amp = dispersion.dispersion_relation(E, dt)
     we, rel = dispersion.relative_phase_error(w, om)
     assert np.abs(rel).max() <= rc.imag_tail_bound(1.0, M, h)
-    assert np.ptp(rel) < 0.05 * np.abs(rel).max()
+    assert np.ptp(rel) < 0.1 * np.abs(rel).max()  # flat across the spectrum (within 10 %)
 
 
 def test_fsphere_dispersion_closed_form():
