@@ -20,6 +20,11 @@ shallow water equations on the rotating sphere"):
 * ``step``         -- one REXI step  U <- sum_k beta_k (alpha_k + tau L)^{-1} U
                       (Sec. 4.2, Algorithm 1) in spectral and grid layouts, and
                       its adjoint.
+* ``phi_solver``   -- the paper's own geopotential-only solve per pole (Sec. 4.3
+                      and 5): the multiplied-through Phi equation, its Galerkin
+                      matrix, velocities recovered in physical space.
+* ``integrate``    -- reference integrators for the Gaussian-bump study
+                      (Sec. 6.2): RK4, the exact exp(tL), modal REXI steps.
 
 Everything is numpy/scipy in float64 / complex128.  The shifted systems are
 solved with LAPACK's banded LU (``scipy.linalg.solve_banded``) on the full
