@@ -6,7 +6,7 @@
 //
 // Each real row of even length n is transformed on its own: its even and odd
 // samples form one complex sequence z_k = x_{2k} + i x_{2k+1} of length n/2,
-// transformed by a mixed-radix (2, 3, 4, 5) Stockham autosort FFT in shared
+// transformed by a mixed-radix (2, 3, 4, 5, 8) Stockham autosort FFT in shared
 // memory; X_m = E_m + e^{-2 pi i m/n} O_m with E_m = (Z_m + conj Z_{n/2-m})/2,
 // O_m = (Z_m - conj Z_{n/2-m})/(2i).  (Packing two different rows instead would
 // let the rounding of a large row leak into a small one.)  The inverse builds
@@ -38,29 +38,57 @@ struct FftArgs {
   const void *tw;  // n twiddles e^{-2 pi i k / n} (n = nlon), double2 or float2
   int n, h, nstages, N, nlat, ncol, np;  // h = n / 2 complex points per row; np rows per CTA
   int radix[24];
+  // division by run-time sizes as a multiply-high: x / d = umulhi(x, mag) for x, d < 2^16
+  uint32_t mag_nb[24], mag_ns[24], mag_h, mag_np;
   double c3, s3, c5a, s5a, c5b, s5b;  // cos/sin of 2pi/3, 2pi/5, 4pi/5
 };
+
+__host__ __device__ inline uint32_t div_magic(int d) { return d > 1 ? (uint32_t)((1ull << 32) / (unsigned)d + 1) : 0u; }
+// exact for 0 <= x < 2^16 and 1 <= d < 2^16 (x d < 2^32)
+__device__ __forceinline__ int fdiv(int x, uint32_t mag, int d) {
+  return d == 1 ? x : (int)__umulhi((uint32_t)x, mag);
+}
 
 template <typename C> __device__ __forceinline__ C cmulz(C a, C b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
 template <typename C> __device__ __forceinline__ C addz(C a, C b) { return {a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C subz(C a, C b) { return {a.x - b.x, a.y - b.y}; }
 template <typename C> __device__ __forceinline__ C mulmi(C a) { return {a.y, -a.x}; }  // -i a
 
-template <typename T>
-__device__ __forceinline__ void dft_small(typename V2<T>::t *v, int R, const FftArgs &a) {
+// In-register DFT of R points (forward, e^{-2 pi i jk/R}); R is a compile-time constant
+// so v[] stays in registers and the loops unroll.
+template <typename T, int R>
+__device__ __forceinline__ void dft_small(typename V2<T>::t *v, const FftArgs &a) {
   using C = typename V2<T>::t;
-  if (R == 2) {
+  if constexpr (R == 2) {
     C t = v[0];
     v[0] = addz(t, v[1]);
     v[1] = subz(t, v[1]);
-  } else if (R == 4) {
+  } else if constexpr (R == 4) {
     C t0 = addz(v[0], v[2]), t1 = subz(v[0], v[2]);
     C t2 = addz(v[1], v[3]), t3 = mulmi(subz(v[1], v[3]));
     v[0] = addz(t0, t2);
     v[2] = subz(t0, t2);
     v[1] = addz(t1, t3);
     v[3] = subz(t1, t3);
-  } else if (R == 3) {
+  } else if constexpr (R == 8) {
+    // two 4-point DFTs (even and odd samples) and the w8^k butterflies
+    C a0 = addz(v[0], v[4]), a1 = subz(v[0], v[4]), a2 = addz(v[2], v[6]), a3 = mulmi(subz(v[2], v[6]));
+    C b0 = addz(v[1], v[5]), b1 = subz(v[1], v[5]), b2 = addz(v[3], v[7]), b3 = mulmi(subz(v[3], v[7]));
+    C e0 = addz(a0, a2), e2 = subz(a0, a2), e1 = addz(a1, a3), e3 = subz(a1, a3);
+    C o0 = addz(b0, b2), o2 = subz(b0, b2), o1 = addz(b1, b3), o3 = subz(b1, b3);
+    const T r2 = (T)0.70710678118654752440;  // 1/sqrt(2)
+    C w1 = {r2 * (o1.x + o1.y), r2 * (o1.y - o1.x)};   // o1 (1 - i)/sqrt(2)
+    C w2 = mulmi(o2);                                  // o2 (-i)
+    C w3 = {r2 * (o3.y - o3.x), -r2 * (o3.x + o3.y)};  // o3 (-1 - i)/sqrt(2)
+    v[0] = addz(e0, o0);
+    v[4] = subz(e0, o0);
+    v[1] = addz(e1, w1);
+    v[5] = subz(e1, w1);
+    v[2] = addz(e2, w2);
+    v[6] = subz(e2, w2);
+    v[3] = addz(e3, w3);
+    v[7] = subz(e3, w3);
+  } else if constexpr (R == 3) {
     const T c3 = (T)a.c3, s3 = (T)a.s3;
     C s = addz(v[1], v[2]);
     C d = subz(v[1], v[2]);
@@ -87,33 +115,47 @@ __device__ __forceinline__ void dft_small(typename V2<T>::t *v, int R, const Fft
   }
 }
 
+// One Stockham pass of radix R over np rows of n points: src -> dst.
+template <typename T, int R>
+__device__ __forceinline__ void stockham_pass(const typename V2<T>::t *src, typename V2<T>::t *dst, int n, int Ns,
+                                              uint32_t mnb, uint32_t mns, const FftArgs &a) {
+  using C = typename V2<T>::t;
+  const C *tw = static_cast<const C *>(a.tw);
+  const int nb = n / R;
+  const int tstep = 2 * (n / (Ns * R));  // twiddle e^{-2 pi i jm r / (Ns R)} = tw[r jm tstep]
+  for (int t = threadIdx.x; t < a.np * nb; t += blockDim.x) {
+    const int q = fdiv(t, mnb, nb), jb = t - q * nb;
+    const C *in = src + q * n;
+    C *out = dst + q * n;
+    const int jd = fdiv(jb, mns, Ns), jm = jb - jd * Ns;
+    C v[R];
+    v[0] = in[jb];
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmulz(in[jb + r * nb], tw[r * jm * tstep]);  // tw[0] = 1 exactly
+    dft_small<T, R>(v, a);
+    const int od = jd * Ns * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[od + r * Ns] = v[r];
+  }
+}
+
 // In-shared-memory forward FFT of np rows of h points; returns the buffer holding
 // the result (buf0 or buf1).
 template <typename T>
 __device__ typename V2<T>::t *fft_smem(typename V2<T>::t *buf0, typename V2<T>::t *buf1, const FftArgs &a) {
   using C = typename V2<T>::t;
-  const C *tw = static_cast<const C *>(a.tw);
   const int n = a.h;
   C *src = buf0, *dst = buf1;
   int Ns = 1;
   for (int s = 0; s < a.nstages; ++s) {
     const int R = a.radix[s];
-    const int nb = n / R;
-    const int stride = n / (Ns * R);
-    for (int t = threadIdx.x; t < a.np * nb; t += blockDim.x) {
-      const int q = t / nb, jb = t - q * nb;
-      const C *in = src + q * n;
-      C *out = dst + q * n;
-      C v[5];
-      const int jm = jb % Ns;
-      for (int r = 0; r < R; ++r) {
-        C x = in[jb + r * nb];
-        if (r > 0 && jm > 0) x = cmulz(x, tw[2 * r * jm * stride]);
-        v[r] = x;
-      }
-      dft_small<T>(v, R, a);
-      const int od = (jb / Ns) * Ns * R + jm;
-      for (int r = 0; r < R; ++r) out[od + r * Ns] = v[r];
+    const uint32_t mnb = a.mag_nb[s], mns = a.mag_ns[s];
+    switch (R) {  // uniform across the block
+      case 8: stockham_pass<T, 8>(src, dst, n, Ns, mnb, mns, a); break;
+      case 4: stockham_pass<T, 4>(src, dst, n, Ns, mnb, mns, a); break;
+      case 2: stockham_pass<T, 2>(src, dst, n, Ns, mnb, mns, a); break;
+      case 3: stockham_pass<T, 3>(src, dst, n, Ns, mnb, mns, a); break;
+      default: stockham_pass<T, 5>(src, dst, n, Ns, mnb, mns, a); break;
     }
     __syncthreads();
     C *tmp = src;
@@ -141,7 +183,7 @@ __global__ void fft_fwd_kernel(FftArgs a, const double *grid, void *four_v, cons
   const int c0 = blockIdx.x * a.np;
   const double2 *g2 = reinterpret_cast<const double2 *>(grid);
   for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
-    const int q = t / h, k = t - q * h;
+    const int q = fdiv(t, a.mag_h, h), k = t - q * h;
     const int c = c0 + q;
     C v = {0, 0};
     if (c < a.ncol) {
@@ -160,7 +202,7 @@ __global__ void fft_fwd_kernel(FftArgs a, const double *grid, void *four_v, cons
   const C *Z = fft_smem<T>(buf0, buf1, a);
   const int M1 = a.N + 1;
   for (int t = threadIdx.x; t < a.np * M1; t += blockDim.x) {
-    const int m = t / a.np, q = t - m * a.np;
+    const int m = fdiv(t, a.mag_np, a.np), q = t - m * a.np;
     const int c = c0 + q;
     if (c >= a.ncol) continue;
     const C zm = Z[q * h + m];
@@ -194,7 +236,7 @@ __global__ void fft_inv_kernel(FftArgs a, const void *four_v, double *grid, cons
   };
   // column index fastest, so that neighbouring threads read neighbouring Fourier columns
   for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
-    const int m = t / a.np, q = t - m * a.np;
+    const int m = fdiv(t, a.mag_np, a.np), q = t - m * a.np;
     const int c = c0 + q;
     C A = {0, 0}, Bc = {0, 0};
     if (c < a.ncol) {
@@ -221,7 +263,7 @@ __global__ void fft_inv_kernel(FftArgs a, const void *four_v, double *grid, cons
   const C *r = fft_smem<T>(buf0, buf1, a);
   double2 *g2 = reinterpret_cast<double2 *>(grid);
   for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
-    const int q = t / h, k = t - q * h;
+    const int q = fdiv(t, a.mag_h, h), k = t - q * h;
     const int c = c0 + q;
     if (c >= a.ncol) continue;
     const double s = out_scale[(c % 3) * a.nlat + j];
@@ -246,6 +288,16 @@ FftArgs make_args(const Plan &pl, int B) {
   a.nlat = pl.nlat;
   a.ncol = 3 * B;
   a.np = pl.fft.nsplit;
+  {
+    int Ns = 1;
+    for (int s = 0; s < a.nstages; ++s) {
+      a.mag_nb[s] = div_magic(a.h / a.radix[s]);
+      a.mag_ns[s] = div_magic(Ns);
+      Ns *= a.radix[s];
+    }
+    a.mag_h = div_magic(a.h);
+    a.mag_np = div_magic(a.np);
+  }
   a.c3 = std::cos(2.0 * M_PI / 3.0);
   a.s3 = std::sin(2.0 * M_PI / 3.0);
   a.c5a = std::cos(2.0 * M_PI / 5.0);
@@ -257,9 +309,11 @@ FftArgs make_args(const Plan &pl, int B) {
 
 }  // namespace
 
-// Factor n into radices 4, 2, 3, 5 (4s first); false if another prime divides n.
+// Factor n into radices 8, 4, 2, 3, 5 (largest powers of two first); false if another
+// prime divides n.
 bool fft_factor(int n, int *radix, int *nstages) {
   int k = 0, m = n;
+  while (m % 8 == 0) { radix[k++] = 8; m /= 8; }
   while (m % 4 == 0) { radix[k++] = 4; m /= 4; }
   while (m % 2 == 0) { radix[k++] = 2; m /= 2; }
   while (m % 3 == 0) { radix[k++] = 3; m /= 3; }

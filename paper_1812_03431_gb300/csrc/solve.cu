@@ -393,8 +393,17 @@ __global__ void reduce_kernel(ReduceArgs a) {
     double2 acc = make_double2(0, 0);
     if (!(fl & 2)) {
       if (fl & 1) {
+        // loads issued eight at a time, added strictly in slot order (bit-reproducible)
         const double2 *p = a.part + fi * a.slots * a.B + b;
-        for (int s = 0; s < a.slots; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
+        int s = 0;
+        for (; s + 8 <= a.slots; s += 8) {
+          double2 v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + (int64_t)(s + u) * a.B);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc = cadd(acc, v[u]);
+        }
+        for (; s < a.slots; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
       }
       const double2 x0 = a.sin[t];
       if (!a.single) {
