@@ -30,11 +30,11 @@ sys.path.insert(0, ROOT)
 WORK = dict(N=341, nlat=512, nlon=1024, M=256, h=0.2, tau=1200.0, batch=16, seed=1005)
 METRIC = "REXI steps/s at T341, K=256 poles: chosen vs plain FP64 form at stated error"
 FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve: 36 FMAs
-# DRAM bytes (read + write) of one solve_kernel launch from the ncu capture at T170,
-# K=256, batch 16 (profiles/solve_kernel_t170_b16.md); traffic per row is constant, so a
-# launch of the bench workload moves this times rows(T341) / rows(T170).
-SOLVE_TRAFFIC_T170 = 10.47e9  # re-captured after each change of the solve kernel
-SOLVE_TRAFFIC_SLOTS = 47      # pole-slot layout of that capture (traffic depends on it)
+# DRAM bytes (read + write) of one solve_kernel launch from ncu captures at T170, K=256,
+# batch 16, by pole-slot count (profiles/solve_kernel_t170_b16.md); traffic per row is
+# constant, so a launch of the bench workload moves this times rows(T341) / rows(T170).
+# Re-captured after each change of the solve kernel.
+SOLVE_TRAFFIC_T170 = {47: 10.47e9, 64: 10.23e9}
 
 
 def rows_of(N):
@@ -235,6 +235,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-phi-solver", action="store_true",
+                    help="skip timing the paper's geopotential-only solver next to the default one")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -347,6 +349,36 @@ def main():
                              e2e_same=e2e_same)
         plan.close()
 
+    # the paper's geopotential-only solver on the same workload (FP64 form), for comparison
+    phi = None
+    if not args.no_phi_solver and "fp64" in results:
+        plan = rexi.Plan(W["N"], W["nlat"], W["nlon"], M=W["M"], h=W["h"], tau=W["tau"], max_batch=B,
+                         precision="fp64", solver="phi")
+        pslots = plan.tune(B)
+        x = plan.synthesize(S)
+        y = torch.empty_like(x)
+        for _ in range(args.warmup):
+            plan.step(x, out=y)
+        plan.profile_enable(args.steps)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.step(x, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = replica_max_ms(e0.elapsed_time(e1) / args.steps, dist)
+        stages, ncalls = plan.profile_read()
+        f = results["fp64"]["y"]
+        phi = {"value": world * 1e3 / pms, "ms_per_step": pms, "pole_slots": pslots,
+               "stage_ms": {k: v / max(ncalls, 1) for k, v in stages.items()},
+               "difference_vs_delta_form": float((y - f).norm() / f.norm()),
+               "note": "REXI_SOLVER_PHI: the paper's Phi-only system (Sec. 4.3, 5), pentadiagonal per "
+                       "(pole, m, parity); a different truncation, so it differs at the highest degrees"}
+        plan.close()
+
     chosen = precisions[0]
     r = results[chosen]
     P = 2 * (W["M"] + 11) + 1
@@ -355,6 +387,7 @@ def main():
     sm_mhz = (r["clocks"] or {}).get("sm_max_mhz") or 2070.0
     peak = fp64_peak_tflops(sm_mhz)
     achieved = flops / (solve_ms * 1e-3) / 1e12
+    tslots = min(SOLVE_TRAFFIC_T170, key=lambda k: abs(k - r["slots"]))
     line = {
         "metric": METRIC, "value": world * 1e3 / r["ms"], "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
@@ -363,10 +396,9 @@ def main():
         "data": "synthetic", "config": {**workload_config(), "form": chosen, "pole_slots": r["slots"]},
         "roofline": {"bound": "alu", "kernel": "solve_kernel (FP64 banded solves + pole sum)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": (SOLVE_TRAFFIC_T170 * rows_of(W["N"]) / rows_of(170))
-                     if SOLVE_TRAFFIC_T170 and r["slots"] == SOLVE_TRAFFIC_SLOTS else None,
-                     "traffic_source": "ncu dram bytes at T170/K256/B16, %d pole slots, scaled by rows to T341"
-                                       % SOLVE_TRAFFIC_SLOTS,
+                     "traffic": SOLVE_TRAFFIC_T170[tslots] * rows_of(W["N"]) / rows_of(170),
+                     "traffic_source": "ncu dram bytes at T170/K256/B16 with %d pole slots (the captured "
+                                       "layout nearest the bench's %d), scaled by rows to T341" % (tslots, r["slots"]),
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz",
                      "flops_per_launch": flops, "launch_ms": solve_ms},
         "stage_ms": r["stages"],
@@ -384,6 +416,8 @@ def main():
                              "pole_slots": f["slots"],
                              "kernels": kernel_rooflines("fp64", f["stages"], f["slots"], sm_mhz)}
         line["error_vs_fp64_form"] = float(d)
+    if phi is not None:
+        line["phi_solver_form"] = phi
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

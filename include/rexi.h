@@ -66,6 +66,17 @@ enum { REXI_FP64 = 0,      /* every stage in FP64 */
                               beta-weighted pole sum stay FP64 */
 enum { REXI_GRID = 0,      /* rexi_step in/out are grid states */
        REXI_SPECTRAL = 1 }; /* rexi_step in/out are spectral states */
+enum { REXI_SOLVER_DELTA = 0, /* per (pole, m, parity): Phi and zeta eliminated, a tridiagonal
+                                 system in delta (default) */
+       REXI_SOLVER_PHI = 1 };  /* the paper's geopotential-only system (Sec. 4.3 and 5): the Phi
+                                 equation multiplied through by D^2, D = alpha^2 + tau^2 f^2, so
+                                 that its coefficients are polynomials in mu; Galerkin-truncated
+                                 it couples degrees n, n +- 2, n +- 4 (a pentadiagonal system
+                                 per parity).  delta and zeta follow from the Phi and zeta rows
+                                 of the system in spectral space.  Truncating the multiplied
+                                 equation is a different discretisation from truncating L, so
+                                 the result differs from REXI_SOLVER_DELTA at the highest
+                                 degrees (it agrees in the interior of a band-limited state). */
 
 typedef struct rexi_plan rexi_plan;
 typedef struct rexi_ragged rexi_ragged;
@@ -98,6 +109,11 @@ typedef struct {
                            closed 3x3 system solved in closed form, no banded solves; 0: the
                            rotating sphere, f = 2 Omega mu (default).  rexi_ragged_create
                            rejects f-sphere plans. */
+  int32_t solver;       /* REXI_SOLVER_DELTA | REXI_SOLVER_PHI.  REXI_SOLVER_PHI needs the
+                           rotating sphere (fsphere = 0) and serves rexi_step,
+                           rexi_analyze / rexi_synthesize and rexi_tune only:
+                           rexi_step_adjoint, rexi_step_static, rexi_solve_pole and
+                           rexi_ragged_create return REXI_EINVAL for such plans. */
 } rexi_params;
 
 /* Fill *p with the defaults above (ntrunc = 63, nlat = 96, nlon = 192, M = 128,

@@ -29,6 +29,8 @@ assembled on the latitudes from the synthesised (Phi0, zeta0, delta0, U0, V0) an
 projected, the system is solved, the velocities are recovered pointwise in
 latitude from V = A^{-1} (V0 + tau grad Phi), and zeta, delta are their curl and
 divergence projected back; beta_k times the result is summed over the poles.
+A second recovery, in spectral space from the Phi and zeta rows of the system, is
+the GPU path's form (``recover="spectral"``).
 
 Truncating the multiplied-through equation is a different discretisation from
 truncating L itself, so this result equals ``step.rexi_step_spectral`` only where
@@ -40,7 +42,7 @@ without rotation, and in the low degrees otherwise.  Those are its pins
 import numpy as np
 
 from .sphere import alp, gauss_legendre, idx
-from .swe import Consts
+from .swe import Consts, coupling
 
 
 def phi_matrix_and_rhs(m, N, mu, w, alpha, tau, c, U_m, fsphere=False):
@@ -77,30 +79,54 @@ def phi_matrix_and_rhs(m, N, mu, w, alpha, tau, c, U_m, fsphere=False):
     return Bm, rhs, (P, H, f, D, U0, V0)
 
 
-def rexi_step_phi(U, N, nlat, alpha, beta, tau, c=Consts(), fsphere=False, ms=None):
+def rexi_step_phi(U, N, nlat, alpha, beta, tau, c=Consts(), fsphere=False, ms=None, recover="physical"):
     """sum_k beta_k (alpha_k + tau L)^{-1} U through the geopotential-only system, for
-    spectral states U [..., 3, nspec]; the m = 0 result is made real."""
+    spectral states U [..., 3, nspec]; the m = 0 result is made real.
+
+    ``recover="physical"`` follows the paper: velocities V = A^{-1}(V0 + tau grad Phi)
+    pointwise in latitude, then their curl and divergence.  ``recover="spectral"`` takes
+    delta from the Phi row of the system, delta = (alpha Phi - Phi0) / (tau Phibar), and
+    zeta from its zeta row, zeta_n = (zeta0_n + 2 Omega tau (c_n delta_{n-1} + d_n delta_{n+1}))
+    / (alpha + i tau sigma_n) (the spectral operator of Eq. (1)); this is the form the GPU
+    path uses, with no per-pole transforms."""
     U = np.asarray(U, dtype=np.complex128)
     mu, w = gauss_legendre(nlat)
     a = c.radius
     out = np.zeros_like(U)
     ms = range(N + 1) if ms is None else ms
     sc = w / (1.0 - mu * mu) / a
+    q = 2.0 * c.omega * tau
     for m in ms:
         sl = slice(idx(m, m, N), idx(m, N, N) + 1)
         U_m = U[..., :, sl]
         acc = np.zeros_like(U_m)
+        ns, sig, ct, dt, _ = coupling(m, N, c)
+        if fsphere:
+            sig = np.zeros_like(sig)
         for al, be in zip(alpha, beta):
             Bm, rhs, (P, H, f, D, U0, V0) = phi_matrix_and_rhs(m, N, mu, w, al, tau, c, U_m, fsphere)
             Phi = np.linalg.solve(Bm, rhs.reshape(-1, rhs.shape[-1]).T).T.reshape(rhs.shape)
-            # velocities pointwise in latitude: V = A^{-1} (V0 + tau grad Phi), Robert-scaled
-            Phg = Phi @ P
-            Wu = U0 + tau * (1j * m) * Phg / a
-            Wv = V0 + tau * (Phi @ H) / a
-            Uk = (al * Wu - tau * f * Wv) / D
-            Vk = (tau * f * Wu + al * Wv) / D
-            zeta = 1j * m * (Vk @ (P * sc).T) + Uk @ (H * sc).T
-            delta = 1j * m * (Uk @ (P * sc).T) - Vk @ (H * sc).T
+            if recover == "physical":
+                # velocities pointwise in latitude: V = A^{-1} (V0 + tau grad Phi), Robert-scaled
+                Phg = Phi @ P
+                Wu = U0 + tau * (1j * m) * Phg / a
+                Wv = V0 + tau * (Phi @ H) / a
+                Uk = (al * Wu - tau * f * Wv) / D
+                Vk = (tau * f * Wu + al * Wv) / D
+                zeta = 1j * m * (Vk @ (P * sc).T) + Uk @ (H * sc).T
+                delta = 1j * m * (Uk @ (P * sc).T) - Vk @ (H * sc).T
+            else:
+                delta = (al * Phi - U_m[..., 0, :]) / (tau * c.phibar)
+                delta[..., ns == 0] = 0.0
+                dm = np.zeros_like(delta)
+                dp = np.zeros_like(delta)
+                dm[..., 1:] = delta[..., :-1]
+                dp[..., :-1] = delta[..., 1:]
+                if fsphere:
+                    zeta = (U_m[..., 1, :] + q * delta) / al
+                else:
+                    zeta = (U_m[..., 1, :] + q * (ct * dm + dt * dp)) / (al + 1j * tau * sig)
+                zeta[..., ns == 0] = 0.0
             acc[..., 0, :] += be * Phi
             acc[..., 1, :] += be * zeta
             acc[..., 2, :] += be * delta

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librexi.so")
-SOURCES = ["coeffs.cpp", "plan.cu", "solve.cu", "fft.cu", "legendre.cu", "legendre_tc.cu", "capi.cu", "ragged.cu"]
+SOURCES = ["coeffs.cpp", "plan.cu", "solve.cu", "phi.cu", "fft.cu", "legendre.cu", "legendre_tc.cu", "capi.cu",
+           "ragged.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -109,6 +109,14 @@ rexi_status core(Plan &pl, int B, bool adjoint, cudaStream_t st, Marks &mk) {
   SolveLayout *lay = nullptr;
   rexi_status r = get_layout(pl, B, false, &lay);
   if (r != REXI_OK) return r;
+  if (pl.prm.solver == REXI_SOLVER_PHI) {
+    mk.mark(ST_SOLVE);
+    cudaError_t e = launch_phi_solve(pl, *lay, pl.s_in, B, st);
+    if (e != cudaSuccess) return cuda_fail("phi solve", e);
+    mk.mark(ST_REDUCE);
+    e = launch_phi_reduce(pl, *lay, pl.s_in, pl.s_out, B, st);
+    return e == cudaSuccess ? REXI_OK : cuda_fail("phi reduce", e);
+  }
   mk.mark(ST_SOLVE);
   cudaError_t e = launch_solve(pl, *lay, adjoint, pl.s_in, B, 0, pl.P, true, st);
   if (e != cudaSuccess) return cuda_fail("solve", e);
@@ -157,6 +165,10 @@ rexi_status step_impl(rexi_plan *plan, const void *in, void *out, int32_t B, voi
   const bool grid = pl.prm.layout == REXI_GRID;
   rexi_status r = check_io(pl, in, out, B, grid);
   if (r != REXI_OK) return r;
+  if (adjoint && pl.prm.solver == REXI_SOLVER_PHI) {
+    set_error("rexi_step_adjoint: not available for REXI_SOLVER_PHI plans");
+    return REXI_EINVAL;
+  }
   if (adjoint && (r = ensure_adjoint_factors(pl)) != REXI_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Marks mk(pl, st);
@@ -261,6 +273,10 @@ rexi_status rexi_plan_create(const rexi_params *prm, rexi_plan **out) {
     set_error("rexi_plan_create: REXI_MIXED applies to the grid layout (the spectral step is all FP64)");
     return REXI_EINVAL;
   }
+  if ((p.solver != REXI_SOLVER_DELTA && p.solver != REXI_SOLVER_PHI) || (p.solver == REXI_SOLVER_PHI && p.fsphere)) {
+    set_error("rexi_plan_create: solver must be REXI_SOLVER_DELTA or REXI_SOLVER_PHI (the latter on the rotating sphere)");
+    return REXI_EINVAL;
+  }
   Plan *pl = new Plan();
   rexi_status r = build_plan(p, pl);
   if (r != REXI_OK) {
@@ -311,6 +327,7 @@ rexi_status rexi_solve_pole(rexi_plan *plan, int32_t k, const void *in_dev, void
   if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
   Plan &pl = *plan->pl;
   if (k < 0 || k >= pl.P) { set_error("pole index out of range"); return REXI_EINVAL; }
+  if (pl.prm.solver == REXI_SOLVER_PHI) { set_error("rexi_solve_pole: not available for REXI_SOLVER_PHI plans"); return REXI_EINVAL; }
   rexi_status r = check_io(pl, in_dev, out_dev, B, false);
   if (r != REXI_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -330,8 +347,8 @@ rexi_status rexi_solve_pole(rexi_plan *plan, int32_t k, const void *in_dev, void
 rexi_status rexi_step_static(rexi_plan *plan, const void *in_dev, void *out_dev, int32_t batch, void *stream) {
   if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
   Plan &pl = *plan->pl;
-  if (pl.prm.layout != REXI_SPECTRAL) {
-    set_error("rexi_step_static: needs a plan in REXI_SPECTRAL layout");
+  if (pl.prm.layout != REXI_SPECTRAL || pl.prm.solver == REXI_SOLVER_PHI) {
+    set_error("rexi_step_static: needs a REXI_SPECTRAL plan with REXI_SOLVER_DELTA");
     return REXI_EINVAL;
   }
   rexi_status r = check_io(pl, in_dev, out_dev, batch, false);

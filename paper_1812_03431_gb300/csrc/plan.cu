@@ -148,13 +148,15 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   if ((e = upload(&pl->alpha_dev, al, &bytes))) return fail("alpha", e);
   if ((e = upload(&pl->beta_dev, be, &bytes))) return fail("beta", e);
 
-  // ---- systems (m, parity) and rows
+  // ---- systems (m, parity) and rows: delta rows (n >= max(m, 1)) for the delta
+  // elimination, Phi rows (n >= m, Phi_0^0 included) for the geopotential-only solver
+  const bool phi_solver = prm.solver == REXI_SOLVER_PHI;
   pl->sys.resize(2 * (N + 1));
   int64_t row = 0;
   int lmax = 0;
   for (int m = 0; m <= N; ++m)
     for (int p = 0; p < 2; ++p) {
-      const int nmin = std::max(m, 1);
+      const int nmin = phi_solver ? m : std::max(m, 1);
       int n0 = m + p;
       while (n0 < nmin) n0 += 2;
       const int len = n0 <= N ? (N - n0) / 2 + 1 : 0;
@@ -194,10 +196,18 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
       // reduce flags: Phi/delta rows have partials iff n >= nmin; zeta rows iff a
       // delta row of the other parity sits at n - 1 or n + 1
       const bool staterow = n >= nmin;
-      rflags[0 * NS + ix] = staterow ? 1 : 0;
-      rflags[2 * NS + ix] = staterow ? 1 : 2;
-      bool zp = staterow && ((n - 1 >= nmin) || (n + 1 <= N));
-      rflags[1 * NS + ix] = staterow ? (zp ? 1 : 0) : 2;
+      if (!phi_solver) {
+        rflags[0 * NS + ix] = staterow ? 1 : 0;
+        rflags[2 * NS + ix] = staterow ? 1 : 2;
+        bool zp = staterow && ((n - 1 >= nmin) || (n + 1 <= N));
+        rflags[1 * NS + ix] = staterow ? (zp ? 1 : 0) : 2;
+      } else {
+        // every Phi row is solved; zeta rows collect from Phi rows at n -+ 1 of the
+        // other parity; zeta_0^0 and delta_0^0 are not state
+        rflags[0 * NS + ix] = 1;
+        rflags[2 * NS + ix] = staterow ? 1 : 2;
+        rflags[1 * NS + ix] = staterow ? (((n - 1 >= m) || (n + 1 <= N)) ? 1 : 0) : 2;
+      }
     }
   }
   cplx sphf(0, 0), spha(0, 0);
@@ -207,6 +217,11 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   }
   pl->sphi_fwd = make_double2(sphf.real(), sphf.imag());
   pl->sphi_adj = make_double2(spha.real(), spha.imag());
+  {
+    cplx sb(0, 0);
+    for (int k = 0; k < P; ++k) sb += pl->beta[k];
+    pl->sumb = make_double2(sb.real(), sb.imag());
+  }
   if ((e = upload(&pl->coef_dev, coef, &bytes))) return fail("coef", e);
   if ((e = upload(&pl->m_of_dev, m_of, &bytes))) return fail("m_of", e);
   if ((e = upload(&pl->rflags_dev, rflags, &bytes))) return fail("rflags", e);
@@ -221,7 +236,42 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   if ((e = upload(&pl->zd_mone, zd_mone, &bytes))) return fail("zd", e);
 
   // ---- solve factors (forward now; adjoint on first use); the f-sphere needs none
-  if (!prm.fsphere) {
+  if (phi_solver) {
+    // Galerkin matrices of mu^2, mu^4 and mu (1 - mu^2) d/dmu in orthonormal Legendre
+    // functions, by the recurrences mu P_n = eps_{n+1} P_{n+1} + eps_n P_{n-1} and
+    // (1 - mu^2) P_n' = -n eps_{n+1} P_{n+1} + (n + 1) eps_n P_{n-1}; products are taken
+    // over all degrees and truncated afterwards (exact projection)
+    std::vector<double> zc(12 * NS, 0.0);
+    for (int m = 0; m <= N; ++m) {
+      auto ep = [m](int k) { return k > m ? eps_nm(k, m) : 0.0; };
+      auto mu2 = [&](int k, int d) {  // (mu^2)[k][k + 2d], d in -1..1
+        if (d == -1) return ep(k) * ep(k - 1);
+        if (d == 0) return ep(k) * ep(k) + ep(k + 1) * ep(k + 1);
+        return ep(k + 1) * ep(k + 2);
+      };
+      for (int n = m; n <= N; ++n) {
+        double *z = &zc[12 * spec_idx(N, m, n)];
+        for (int d = -1; d <= 1; ++d) z[1 + d] = mu2(n, d);
+        for (int d = -2; d <= 2; ++d) {  // (mu^4)[n][n + 2d] = sum_l mu2[n][l] mu2[l][n + 2d]
+          double acc = 0.0;
+          for (int d1 = -1; d1 <= 1; ++d1) {
+            const int l = n + 2 * d1, d2 = d - d1;
+            if (l < m || d2 < -1 || d2 > 1) continue;
+            acc += mu2(n, d1) * mu2(l, d2);
+          }
+          z[5 + d] = acc;
+        }
+        z[8] = ep(n) * (-(n - 2.0) * ep(n - 1));
+        z[9] = (n + 1.0) * ep(n) * ep(n) - n * ep(n + 1) * ep(n + 1);
+        z[10] = ep(n + 1) * (n + 3.0) * ep(n + 2);
+      }
+    }
+    if ((e = upload(&pl->phi_zc, zc, &bytes))) return fail("phi coefficients", e);
+    const size_t nfac = (size_t)7 * pl->nrows * P;
+    if ((e = dalloc(&pl->fac_fwd, nfac, &bytes))) return fail("factors", e);
+    if ((e = launch_phi_factor(*pl, 0))) return fail("factor setup", e);
+    if ((e = dalloc(&pl->phi_q, (size_t)5 * NS * prm.max_batch, &bytes))) return fail("phi rhs", e);
+  } else if (!prm.fsphere) {
     const size_t nfac = (size_t)F_NCOMP * pl->nrows * P;
     if ((e = dalloc(&pl->fac_fwd, nfac, &bytes))) return fail("factors", e);
     if ((e = launch_factor_setup(*pl, false, 0))) return fail("factor setup", e);
@@ -404,12 +454,18 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out) {
     tried.push_back(L.slots);
     // time the solve and the slot reduction together (more slots balance the solve
     // better but make the reduction read more partial sums)
-    launch_solve(pl, L, false, pl.s_in, B, 0, pl.P, true, st);  // warm-up
+    auto run = [&]() {
+      if (pl.prm.solver == REXI_SOLVER_PHI) {
+        launch_phi_solve(pl, L, pl.s_in, B, st);
+        launch_phi_reduce(pl, L, pl.s_in, pl.s_out, B, st);
+      } else {
+        launch_solve(pl, L, false, pl.s_in, B, 0, pl.P, true, st);
+        launch_reduce(pl, L, false, pl.s_in, pl.s_out, B, false, 0, st);
+      }
+    };
+    run();  // warm-up
     cudaEventRecord(e0, st);
-    for (int rep = 0; rep < 2; ++rep) {
-      launch_solve(pl, L, false, pl.s_in, B, 0, pl.P, true, st);
-      launch_reduce(pl, L, false, pl.s_in, pl.s_out, B, false, 0, st);
-    }
+    for (int rep = 0; rep < 2; ++rep) run();
     cudaEventRecord(e1, st);
     e = cudaEventSynchronize(e1);
     float ms = 0;
@@ -442,7 +498,7 @@ void free_plan(Plan *pl) {
                   pl->scale_syn_out, pl->mscale_fwd, pl->mscale_c, pl->mscale_adj, pl->mscale_one,
                   pl->zd_syn, pl->zd_ana_adj, pl->zd_one, pl->zd_mone, pl->fft.tw_dev, pl->fft.tw32_dev, pl->four,
                   pl->s_in, pl->s_out, pl->partial, pl->yscratch, pl->counter, pl->tc_tab_ana,
-                  pl->tc_tab_syn, pl->tc_work_ana, pl->tc_work_syn, pl->dev_err};
+                  pl->tc_tab_syn, pl->tc_work_ana, pl->tc_work_syn, pl->dev_err, pl->phi_zc, pl->phi_q};
   for (cudaEvent_t ev : pl->prof_ev) cudaEventDestroy(ev);
   for (void *p : ptrs)
     if (p) cudaFree(p);

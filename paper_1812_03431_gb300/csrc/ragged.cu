@@ -69,9 +69,11 @@ rexi_status rexi_ragged_create(rexi_plan *const *plans, int32_t nplans, int32_t 
   rexi_ragged *rg = new rexi_ragged();
   rg->max_states = max_states;
   for (int i = 0; i < nplans; ++i) {
-    if (!plans[i] || !plans[i]->pl || plans[i]->pl->prm.layout != REXI_SPECTRAL || plans[i]->pl->prm.fsphere) {
+    if (!plans[i] || !plans[i]->pl || plans[i]->pl->prm.layout != REXI_SPECTRAL || plans[i]->pl->prm.fsphere ||
+        plans[i]->pl->prm.solver != REXI_SOLVER_DELTA) {
       delete rg;
-      set_error("rexi_ragged_create: every plan must exist, use REXI_SPECTRAL and the rotating sphere");
+      set_error("rexi_ragged_create: every plan must exist, use REXI_SPECTRAL, the rotating sphere and "
+                "REXI_SOLVER_DELTA");
       return REXI_EINVAL;
     }
     rg->plans.push_back(plans[i]->pl);

@@ -146,6 +146,13 @@ struct Plan {
   int tc_nwork_ana = 0, tc_nwork_syn = 0;
   int *dev_err = nullptr;  // set by a kernel whose bounded wait expired
 
+  // geopotential-only solver (REXI_SOLVER_PHI): Z coefficients [nspec][12] (Z2, Z3, Z6
+  // entries by degree offset), right-hand-side coefficients Q_p [5][nspec][max_batch],
+  // sum of the beta_k; its factors [7][nrows][P] live in fac_fwd
+  double *phi_zc = nullptr;
+  double2 *phi_q = nullptr;
+  double2 sumb{};
+
   // workspaces (max_batch)
   double2 *four = nullptr;     // [nlat][N+1][3 B] complex (FP64 or FP32 pairs in mixed mode)
   double2 *s_in = nullptr;     // [3][nspec][B]
@@ -172,6 +179,12 @@ enum Stage { ST_FFT_FWD = 0, ST_LEG_ANA, ST_SOLVE, ST_REDUCE, ST_LEG_SYN, ST_FFT
 
 // ---- kernels (launchers) ------------------------------------------------------------
 cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st);
+// geopotential-only solver (REXI_SOLVER_PHI): plan-time factors; per step the right-hand
+// sides and the pentadiagonal solves into the slot partials, then the ordered reduction
+cudaError_t launch_phi_factor(Plan &pl, cudaStream_t st);
+cudaError_t launch_phi_solve(Plan &pl, const SolveLayout &lay, const double2 *sin, int B, cudaStream_t st);
+cudaError_t launch_phi_reduce(Plan &pl, const SolveLayout &lay, const double2 *sin, double2 *sout, int B,
+                              cudaStream_t st);
 // f-sphere plans: closed-form per-degree solves and the pole sum, sin -> sout ([3][nspec][B])
 cudaError_t launch_fsphere(Plan &pl, bool adjoint, const double2 *sin, double2 *sout, int B, bool single,
                            int pole, cudaStream_t st);

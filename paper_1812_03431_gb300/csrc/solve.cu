@@ -380,7 +380,29 @@ struct ReduceArgs {
   double tau;
 };
 
-// out[f][idx][b] = sum over slots (in order) + the pole-independent terms.
+// the pole-independent terms of output t = (f, idx, b), and the real part at m = 0
+__device__ __forceinline__ double2 reduce_finish(const ReduceArgs &a, int64_t t, int f, int64_t ix, double2 acc) {
+  const double2 x0 = a.sin[t];
+  if (!a.single) {
+    if (f == 0) acc = cfma(acc, a.sphi, x0);
+    else if (f == 1) acc = cfma(acc, a.w[ix], x0);
+  } else {
+    // single pole: partials carry beta_k X_k; divide beta_k out and add Phi0/alpha, zeta0/s
+    acc = cdiv(acc, a.beta_k);
+    if (f == 0) acc = cadd(acc, cdiv(x0, a.alpha_k));
+    else if (f == 1) {
+      double sg = a.coef[4 * ix + 0];
+      double2 s = a.adjoint ? make_double2(a.alpha_k.x, -a.alpha_k.y - a.tau * sg)
+                            : make_double2(a.alpha_k.x, a.alpha_k.y + a.tau * sg);
+      acc = cadd(acc, cdiv(x0, s));
+    }
+  }
+  if (a.realm0 && a.m_of[ix] == 0) acc.y = 0.0;
+  return acc;
+}
+
+// out[f][idx][b] = sum over slots (in order) + the pole-independent terms; one thread
+// per output.
 __global__ void reduce_kernel(ReduceArgs a) {
   const int64_t total = 3 * a.nspec * a.B;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -405,24 +427,38 @@ __global__ void reduce_kernel(ReduceArgs a) {
         }
         for (; s < a.slots; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
       }
-      const double2 x0 = a.sin[t];
-      if (!a.single) {
-        if (f == 0) acc = cfma(acc, a.sphi, x0);
-        else if (f == 1) acc = cfma(acc, a.w[ix], x0);
-      } else {
-        // single pole: partials carry beta_k X_k; divide beta_k out and add Phi0/alpha, zeta0/s
-        acc = cdiv(acc, a.beta_k);
-        if (f == 0) acc = cadd(acc, cdiv(x0, a.alpha_k));
-        else if (f == 1) {
-          double sg = a.coef[4 * ix + 0];
-          double2 s = a.adjoint ? make_double2(a.alpha_k.x, -a.alpha_k.y - a.tau * sg)
-                                : make_double2(a.alpha_k.x, a.alpha_k.y + a.tau * sg);
-          acc = cadd(acc, cdiv(x0, s));
-        }
-      }
-      if (a.realm0 && a.m_of[ix] == 0) acc.y = 0.0;
+      acc = reduce_finish(a, t, f, ix, acc);
     }
     a.sout[t] = acc;
+  }
+}
+
+// The same with one warp per output for many slots (small batches): lane l sums slots
+// l, l + 32, ... in order, then a fixed butterfly adds the lanes (bit-reproducible).
+__global__ void reduce_wide_kernel(ReduceArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t total = 3 * a.nspec * a.B;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total; t += nwarps) {
+    const int b = (int)(t % a.B);
+    const int64_t fi = t / a.B;
+    const int f = (int)(fi / a.nspec);
+    const int64_t ix = fi - (int64_t)f * a.nspec;
+    const uint8_t fl = a.rflags[fi];
+    double2 acc = make_double2(0, 0);
+    if (!(fl & 2)) {
+      if (fl & 1) {
+        const double2 *p = a.part + fi * a.slots * a.B + b;
+        for (int s = lane; s < a.slots; s += 32) acc = cadd(acc, __ldcs(p + (int64_t)s * a.B));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+      }
+      if (lane == 0) acc = reduce_finish(a, t, f, ix, acc);
+    }
+    if (lane == 0) a.sout[t] = acc;
   }
 }
 
@@ -618,8 +654,14 @@ cudaError_t launch_reduce(Plan &pl, const SolveLayout &lay, bool adjoint, const 
   a.alpha_k = single_pole ? make_double2(pl.alpha[pole].real(), pl.alpha[pole].imag()) : make_double2(0, 0);
   a.beta_k = single_pole ? make_double2(pl.beta[pole].real(), pl.beta[pole].imag()) : make_double2(1, 0);
   int64_t total = 3 * pl.nspec * B;
-  int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)pl.num_sms * 8);
-  reduce_kernel<<<blocks, 256, 0, st>>>(a);
+  // a warp per output when one thread per output would leave most of the GPU idle
+  if (a.slots >= 128 && total < (int64_t)pl.num_sms * 512) {
+    int blocks = (int)std::min<int64_t>((total + 7) / 8, (int64_t)pl.num_sms * 8);
+    reduce_wide_kernel<<<blocks, 256, 0, st>>>(a);
+  } else {
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)pl.num_sms * 8);
+    reduce_kernel<<<blocks, 256, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ class rexi_params(ctypes.Structure):
         ("precision", ctypes.c_int32), ("layout", ctypes.c_int32), ("max_batch", ctypes.c_int32),
         ("strict_range", ctypes.c_int32), ("pole_slots", ctypes.c_int32),
         ("alpha", ctypes.POINTER(ctypes.c_double)), ("beta", ctypes.POINTER(ctypes.c_double)),
-        ("npoles", ctypes.c_int32), ("fsphere", ctypes.c_int32),
+        ("npoles", ctypes.c_int32), ("fsphere", ctypes.c_int32), ("solver", ctypes.c_int32),
     ]
 
 
@@ -121,7 +121,7 @@ class Plan:
     def __init__(self, N, nlat=None, nlon=None, M=128, h=0.2, tau=3600.0, max_batch=1,
                  layout="grid", precision="fp64", normalize=True, alpha=None, beta=None,
                  radius=6.37122e6, omega=7.292e-5, gravity=9.80616, mean_depth=1.0e4,
-                 pole_slots=0, strict_range=False, fsphere=False):
+                 pole_slots=0, strict_range=False, fsphere=False, solver="delta"):
         lib = load()
         p = rexi_params()
         lib.rexi_params_default(ctypes.byref(p))
@@ -141,6 +141,7 @@ class Plan:
         p.strict_range = int(strict_range)
         p.pole_slots = pole_slots
         p.fsphere = 1 if fsphere else 0
+        p.solver = {"delta": 0, "phi": 1}[solver]
         self._keep = []
         if alpha is not None:
             al = np.ascontiguousarray(np.asarray(alpha, dtype=np.complex128)).view(np.float64)

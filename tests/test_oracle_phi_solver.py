@@ -32,32 +32,34 @@ def restrict(S, N, L):
     return out
 
 
+@pytest.mark.parametrize("recover", ["physical", "spectral"])
 @pytest.mark.parametrize("consts,fsphere", [(C, True), (Consts(omega=0.0), False)])
-def test_equals_delta_elimination_where_truncation_does_not_act(consts, fsphere):
+def test_equals_delta_elimination_where_truncation_does_not_act(consts, fsphere, recover):
     # constant f (f-sphere) or no rotation: D is a constant, multiplying through by it
     # commutes with truncation, and both solvers solve the same truncated system
     N, tau = 21, 3600.0
     al, be, _ = rc.rexi_coefficients(16, 0.2)
     S = inputs.random_spectral(N, 2, 3)
-    a = phi_solver.rexi_step_phi(S, N, 32, al, be, tau, consts, fsphere=fsphere)
+    a = phi_solver.rexi_step_phi(S, N, 32, al, be, tau, consts, fsphere=fsphere, recover=recover)
     b = ostep.rexi_step_spectral(S, N, al, be, tau, consts, fsphere=fsphere)
     for f in range(3):
         assert relerr(a[:, f], b[:, f]) < 1e-12
 
 
-def test_agrees_in_low_degrees_on_the_rotating_sphere():
+@pytest.mark.parametrize("recover", ["physical", "spectral"])
+def test_agrees_in_low_degrees_on_the_rotating_sphere(recover):
     # a band-limited state (n <= 10): both discretisations converge to the same solution,
     # so the degrees n <= 10 agree once N is large enough.  A sign slip in any of the
     # grad f terms would leave an O(1) difference here.
     L, N, tau = 10, 21, 3600.0
     al, be, _ = rc.rexi_coefficients(16, 0.2)
     S = embed(inputs.random_spectral(L, 1, 5), L, N)
-    a = restrict(phi_solver.rexi_step_phi(S, N, 30, al, be, tau, C), N, L)
+    a = restrict(phi_solver.rexi_step_phi(S, N, 30, al, be, tau, C, recover=recover), N, L)
     b = restrict(ostep.rexi_step_spectral(S, N, al, be, tau, C), N, L)
     assert relerr(a, b) < 1e-13
     # and with full-spectrum input they differ at the truncation edge only
     R = inputs.random_spectral(N, 1, 6)
-    a = phi_solver.rexi_step_phi(R, N, 30, al, be, tau, C)
+    a = phi_solver.rexi_step_phi(R, N, 30, al, be, tau, C, recover=recover)
     b = ostep.rexi_step_spectral(R, N, al, be, tau, C)
     d = relerr(a, b)
     assert 1e-9 < d < 1e-3
