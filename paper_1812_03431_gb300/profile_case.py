@@ -29,6 +29,7 @@ def main():
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--tune", action="store_true", help="pick the pole-slot layout by timing, as bench.py does")
     ap.add_argument("--pole-slots", type=int, default=0, help="fixed pole-slot count (0: the plan's default)")
+    ap.add_argument("--solver", default="delta", choices=["delta", "phi"])
     args = ap.parse_args()
     import torch
 
@@ -38,7 +39,7 @@ def main():
         nlon += 2
     nlat = args.nlat or nlon // 2
     plan = rexi.Plan(args.N, nlat, nlon, M=args.M, tau=args.tau, max_batch=args.batch, layout=args.layout,
-                     precision=args.precision, pole_slots=args.pole_slots)
+                     precision=args.precision, pole_slots=args.pole_slots, solver=args.solver)
     slots = plan.tune(args.batch) if args.tune else plan.info()["pole_slots"]
     S = torch.from_numpy(inputs.random_spectral(args.N, args.batch, 3)).cuda()
     x = plan.synthesize(S) if args.layout == "grid" else S
