@@ -45,6 +45,7 @@
 #ifndef REXI_H
 #define REXI_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -119,6 +120,10 @@ typedef struct {
 /* Fill *p with the defaults above (ntrunc = 63, nlat = 96, nlon = 192, M = 128,
  * tau = 3600).  Host only. */
 void rexi_params_default(rexi_params *p);
+
+/* sizeof(rexi_params) as compiled into the library, so that a binding can check that
+ * its copy of the struct matches before passing one.  Host only. */
+size_t rexi_params_size(void);
 
 /* T-REXI coefficients on the host, no GPU needed (Sec. 4.1; Sec. 6.1 for the
  * renormalisation).  alpha_n = h (mu + i n), n = -(M+11)..(M+11) ascending,

@@ -195,6 +195,8 @@ using namespace rexi;
 
 extern "C" {
 
+size_t rexi_params_size(void) { return sizeof(rexi_params); }
+
 void rexi_params_default(rexi_params *p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));

@@ -45,6 +45,7 @@ _I32 = ctypes.c_int32
 _DP = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "rexi_params_default": (None, [ctypes.POINTER(rexi_params)]),
+    "rexi_params_size": (ctypes.c_size_t, []),
     "rexi_coefficients": (_I32, [_I32, ctypes.c_double, _I32, _DP, _DP, ctypes.POINTER(_I32), _DP]),
     "rexi_plan_create": (_I32, [ctypes.POINTER(rexi_params), ctypes.POINTER(_VP)]),
     "rexi_step": (_I32, [_VP, _VP, _VP, _I32, _VP]),
@@ -79,6 +80,9 @@ def load():
             fn = getattr(lib, name)
             fn.restype = res
             fn.argtypes = args
+        if lib.rexi_params_size() != ctypes.sizeof(rexi_params):
+            raise RuntimeError("rexi_params: the binding's struct (%d bytes) does not match the library's (%d)"
+                               % (ctypes.sizeof(rexi_params), lib.rexi_params_size()))
         _lib = lib
     return _lib
 

@@ -84,3 +84,13 @@ def test_coefficients_reject_bad_args(lib):
     from paper_1812_03431_gb300 import rexi
     with pytest.raises(rexi.RexiError):
         rexi.rexi_coefficients(0, 0.2)
+
+
+def test_params_struct_matches_library():
+    import ctypes
+    from paper_1812_03431_gb300 import rexi
+    lib = rexi.load()
+    assert lib.rexi_params_size() == ctypes.sizeof(rexi.rexi_params)
+    p = rexi.rexi_params_default()
+    # the fields appended last keep their defaults: rotating sphere, delta elimination
+    assert (p.fsphere, p.solver, p.max_batch, p.M) == (0, 0, 1, 128)
