@@ -53,6 +53,9 @@ def test_bump_propagation(bumps, M, dt):
     plan = rexi.Plan(N, NLAT, NLON, M=M, tau=dt, max_batch=1, layout="spectral")
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    slots = plan.tune(1)  # the pole-slot layout for a single state, by timing
+    t_tune = time.perf_counter() - t0
     x = torch.from_numpy(bumps["x0"]).cuda()
     runs = []
     for _ in range(2):  # the second run is timed warm
@@ -81,7 +84,8 @@ def test_bump_propagation(bumps, M, dt):
         assert err_exact < 0.02 * np.abs(bumps["h_exact"]).max()
     if dt == T:
         assert err_exact < 1e-3 < rk4_err  # one REXI step beats the 2592-step RK4 reference
-    bumps["report"].append(dict(M=M, P=P, dt=dt, steps=nsteps, setup_s=t_setup, run_s=runs[1],
+    bumps["report"].append(dict(M=M, P=P, dt=dt, steps=nsteps, setup_s=t_setup, tune_s=t_tune, pole_slots=slots,
+                                run_s=runs[1],
                                 linf_h_vs_exact_m=err_exact, linf_h_vs_rk4_50s_m=err_rk4,
                                 rk4_50s_vs_exact_m=rk4_err, parity_rel_l2=par))
     path = os.environ.get("REXI_BUMPS_REPORT")
