@@ -166,14 +166,14 @@ __device__ __forceinline__ double eps_nm(int n, int m) {
   return n > m ? sqrt(((double)n * n - (double)m * m) / (4.0 * n * n - 1.0)) : 0.0;
 }
 
-// (mu x)_n = eps_n x_{n-1} + eps_{n+1} x_{n+1} on a window: in[j] holds degree lo + j,
-// out[j] degree lo + 1 + j, for j < L - 2
-template <int L>
-__device__ __forceinline__ void mu_apply(const double2 (&in)[L], double2 (&out)[L - 2], int lo, int m) {
+// (mu x)_n = eps_n x_{n-1} + eps_{n+1} x_{n+1} on a window around degree k: in[j] holds
+// degree k - O + j, out[j] degree k - O + 1 + j (j < L - 2); ew[i] = eps at degree k - 5 + i
+template <int L, int O>
+__device__ __forceinline__ void mu_apply(const double2 (&in)[L], double2 (&out)[L - 2], const double (&ew)[11]) {
 #pragma unroll
   for (int j = 0; j < L - 2; ++j) {
-    const int n = lo + 1 + j;
-    out[j] = cadd(cscale(in[j], eps_nm(n, m)), cscale(in[j + 2], eps_nm(n + 1, m)));
+    // degree n = k - O + 1 + j: eps_n = ew[6 - O + j], eps_{n+1} = ew[7 - O + j]
+    out[j] = cadd(cscale(in[j], ew[6 - O + j]), cscale(in[j + 2], ew[7 - O + j]));
   }
 }
 
@@ -195,29 +195,33 @@ __global__ void phi_rhs_kernel(PhiRhsArgs a) {
       if (n < m || n > N || n == 0) return make_double2(0, 0);
       return cscale(X(f, n), -rad * rad / ((double)n * (n + 1.0)));
     };
+    // eps at degrees k - 5 .. k + 5, once per output
+    double ew[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) ew[i] = eps_nm(k - 5 + i, m);
     // Phi0 at k-4 .. k+4 -> mu^2 Phi0, mu^4 Phi0 at k
     double2 p9[9], p7[7], p5[5], p3[3], p1[1];
 #pragma unroll
     for (int j = 0; j < 9; ++j) p9[j] = X(0, k - 4 + j);
-    mu_apply<9>(p9, p7, k - 4, m);
-    mu_apply<7>(p7, p5, k - 3, m);
-    mu_apply<5>(p5, p3, k - 2, m);
-    mu_apply<3>(p3, p1, k - 1, m);
+    mu_apply<9, 4>(p9, p7, ew);
+    mu_apply<7, 3>(p7, p5, ew);
+    mu_apply<5, 2>(p5, p3, ew);
+    mu_apply<3, 1>(p3, p1, ew);
     const double2 m2p = p5[2], m4p = p1[0];
     // zeta0 at k-3 .. k+3 -> mu zeta0, mu^3 zeta0 at k
     double2 z7[7], z5[5], z3[3], z1[1];
 #pragma unroll
     for (int j = 0; j < 7; ++j) z7[j] = X(1, k - 3 + j);
-    mu_apply<7>(z7, z5, k - 3, m);
-    mu_apply<5>(z5, z3, k - 2, m);
-    mu_apply<3>(z3, z1, k - 1, m);
+    mu_apply<7, 3>(z7, z5, ew);
+    mu_apply<5, 2>(z5, z3, ew);
+    mu_apply<3, 1>(z3, z1, ew);
     const double2 mz = z5[2], m3z = z1[0];
     // delta0 at k-2 .. k+2 -> mu^2 delta0 at k
     double2 d5[5], d3[3], d1[1];
 #pragma unroll
     for (int j = 0; j < 5; ++j) d5[j] = X(2, k - 2 + j);
-    mu_apply<5>(d5, d3, k - 2, m);
-    mu_apply<3>(d3, d1, k - 1, m);
+    mu_apply<5, 2>(d5, d3, ew);
+    mu_apply<3, 1>(d3, d1, ew);
     const double2 m2d = d1[0];
     // Robert winds: U_n = (1/a)[(n-1) eps_n psi_{n-1} - (n+2) eps_{n+1} psi_{n+1} + i m chi_n],
     //               V_n = (1/a)[i m psi_n - (n-1) eps_n chi_{n-1} + (n+2) eps_{n+1} chi_{n+1}]
@@ -232,24 +236,24 @@ __global__ void phi_rhs_kernel(PhiRhsArgs a) {
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
       const int n = k - 2 + j;
-      const double e0 = eps_nm(n, m), e1 = eps_nm(n + 1, m);
+      const double e0 = ew[3 + j], e1 = ew[4 + j];  // eps_n, eps_{n+1}
       double2 v = cadd(cscale(ps[j], (n - 1.0) * e0), cscale(ps[j + 2], -(n + 2.0) * e1));
       v = cadd(v, make_double2(-fm * ch[j + 1].y, fm * ch[j + 1].x));
       u5[j] = cscale(v, 1.0 / rad);
     }
-    mu_apply<5>(u5, u3, k - 2, m);
-    mu_apply<3>(u3, u1, k - 1, m);
+    mu_apply<5, 2>(u5, u3, ew);
+    mu_apply<3, 1>(u3, u1, ew);
     const double2 U0 = u5[2], m2U = u1[0];
     double2 v3[3], v1[1];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int n = k - 1 + j;
-      const double e0 = eps_nm(n, m), e1 = eps_nm(n + 1, m);
+      const double e0 = ew[4 + j], e1 = ew[5 + j];  // eps_n, eps_{n+1}
       double2 v = make_double2(-fm * ps[j + 2].y, fm * ps[j + 2].x);
       v = cadd(v, cadd(cscale(ch[j + 1], -(n - 1.0) * e0), cscale(ch[j + 3], (n + 2.0) * e1)));
       v3[j] = cscale(v, 1.0 / rad);
     }
-    mu_apply<3>(v3, v1, k - 1, m);
+    mu_apply<3, 1>(v3, v1, ew);
     const double2 mV = v1[0];
     const double tau = c.tau, pb = c.phibar, F = c.F, g = c.g;
     const double t2 = tau * tau, t3 = t2 * tau, t4 = t3 * tau;
