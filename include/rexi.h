@@ -201,6 +201,13 @@ rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *
  * workspaces, so no step of this plan may be in flight. */
 rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots);
 
+/* Sets the pole-slot layout for steps with this batch size without timing (for instance
+ * from a cache of earlier rexi_tune results); slots >= 1 is rounded down to a multiple
+ * of the lanes a warp gives each state (and capped by the partial-sum buffer), the
+ * count used is written to *used (may be NULL).  Results are deterministic for any
+ * count; only the order of the final pole sum changes.  Synchronous, like rexi_tune. */
+rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t *used);
+
 /* Host-side description of a plan: writes up to 8 int64 values
  * {N, nspec, P, nlat, nlon, max_batch, pole_slots, device bytes held}. */
 rexi_status rexi_plan_info(const rexi_plan *plan, int64_t *info, int32_t n);

@@ -1,5 +1,6 @@
 // C-ABI entry points of librexi (declared in include/rexi.h).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstring>
 #include <string>
@@ -20,6 +21,7 @@ rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out);
 void free_plan(Plan *pl);
 rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t st);
 rexi_status tune_layout(Plan &pl, int B, int *slots_out);
+rexi_status set_layout(Plan &pl, int B, int slots, int *used);
 
 namespace {
 
@@ -33,17 +35,31 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 // Event marks: a timed call records one event at the start of each stage it
 // runs and one at its end; each interval is attributed to the stage that
 // opened it.
+// Stage boundaries of one call: NVTX ranges (a host-side timeline for profilers; no cost
+// without one attached) and, when rexi_profile_enable is on, CUDA events on the stream.
+const char *const kStageNames[kStages] = {"fft_fwd", "leg_ana", "solve", "reduce",
+                                          "leg_syn", "fft_inv", "transpose_in", "transpose_out"};
+
 struct Marks {
   Plan &pl;
   cudaStream_t st;
   int call = -1;
+  bool open = false;
   Marks(Plan &p, cudaStream_t s) : pl(p), st(s) {
+    nvtxRangePushA("rexi");
     if (pl.prof && pl.prof_calls < pl.prof_cap) {
       call = pl.prof_calls++;
       pl.prof_n[call] = 0;
     }
   }
+  ~Marks() {
+    if (open) nvtxRangePop();
+    nvtxRangePop();
+  }
   void mark(int stage) {
+    if (open) nvtxRangePop();
+    open = stage < kStages;
+    if (open) nvtxRangePushA(kStageNames[stage]);
     if (call < 0) return;
     int &k = pl.prof_n[call];
     if (k > kStages) return;
@@ -382,6 +398,23 @@ rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots) {
   }
   rexi_status r = tune_layout(pl, batch, &s);
   if (r == REXI_OK && slots) *slots = s;
+  return r;
+}
+
+rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t *used) {
+  if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
+  Plan &pl = *plan->pl;
+  if (batch < 1 || batch > pl.prm.max_batch || slots < 1) {
+    set_error("rexi_set_pole_slots: batch must be in [1, max_batch] and slots >= 1");
+    return REXI_EINVAL;
+  }
+  if (pl.prm.fsphere) {  // no banded solves, no layout
+    if (used) *used = 0;
+    return REXI_OK;
+  }
+  int u = 0;
+  rexi_status r = set_layout(pl, batch, slots, &u);
+  if (r == REXI_OK && used) *used = u;
   return r;
 }
 

@@ -428,6 +428,25 @@ rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out) {
   return REXI_OK;
 }
 
+// A given slot count for batch B: the layout with slots / kk pole groups replaces any
+// earlier one for that batch.
+rexi_status set_layout(Plan &pl, int B, int slots, int *used) {
+  SolveLayout L;
+  int bw = 1;
+  while (bw < B && bw < 16) bw *= 2;
+  const int kk = std::max(1, std::min(32 / (2 * bw), (int)pl.partial_cap));
+  rexi_status r = build_layout(pl, B, false, std::max(1, slots / kk), L);
+  if (r != REXI_OK) return r;
+  auto it = pl.layouts.find(B);
+  if (it != pl.layouts.end()) {
+    cudaFree(it->second.items_dev);
+    pl.layouts.erase(it);
+  }
+  pl.layouts.emplace(B, L);
+  if (used) *used = L.slots;
+  return REXI_OK;
+}
+
 // Autotuner: time the solve kernel for each candidate number of pole groups at
 // batch B and keep the fastest layout for later steps with that batch.
 rexi_status tune_layout(Plan &pl, int B, int *slots_out) {

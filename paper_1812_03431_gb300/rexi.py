@@ -6,6 +6,7 @@ built in-tree (``python -m paper_1812_03431_gb300.build`` or
 ``__graft_entry__.build()``); loading fails loudly if it is missing.
 """
 import ctypes
+import json
 import os
 
 import numpy as np
@@ -46,6 +47,7 @@ _DP = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "rexi_params_default": (None, [ctypes.POINTER(rexi_params)]),
     "rexi_params_size": (ctypes.c_size_t, []),
+    "rexi_set_pole_slots": (ctypes.c_int32, [_VP, _I32, _I32, ctypes.POINTER(_I32)]),
     "rexi_coefficients": (_I32, [_I32, ctypes.c_double, _I32, _DP, _DP, ctypes.POINTER(_I32), _DP]),
     "rexi_plan_create": (_I32, [ctypes.POINTER(rexi_params), ctypes.POINTER(_VP)]),
     "rexi_step": (_I32, [_VP, _VP, _VP, _I32, _VP]),
@@ -85,6 +87,14 @@ def load():
                                % (ctypes.sizeof(rexi_params), lib.rexi_params_size()))
         _lib = lib
     return _lib
+
+
+def _read_json(path):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
 
 
 def _check(fn, status):
@@ -158,7 +168,7 @@ class Plan:
         _check("rexi_plan_create", lib.rexi_plan_create(ctypes.byref(p), ctypes.byref(h_)))
         self._h = h_
         self.N, self.nlat, self.nlon, self.max_batch = N, nlat, nlon, max_batch
-        self.layout, self.precision = layout, precision
+        self.layout, self.precision, self.solver = layout, precision, solver
         self.nspec = (N + 1) * (N + 2) // 2
 
     # -- helpers
@@ -238,12 +248,42 @@ class Plan:
             self._h, al.ctypes.data_as(_DP), be.ctypes.data_as(_DP), ctypes.byref(n)))
         return al.view(np.complex128).copy(), be.view(np.complex128).copy()
 
-    def tune(self, batch):
+    def tune(self, batch, cache=None):
         """rexi_tune: time the solve kernel for several pole-group counts at this batch size
-        and keep the fastest; returns the chosen number of pole slots."""
+        and keep the fastest; returns the chosen number of pole slots.
+
+        ``cache``: path of a JSON file of earlier choices keyed by the plan's shape (N,
+        grid, P, batch, precision, solver) and the GPU's name; a hit sets the layout
+        without timing (rexi_set_pole_slots), a miss tunes and records the result."""
+        key = None
+        if cache:
+            key = self._tune_key(batch)
+            table = _read_json(cache)
+            if key in table:
+                return self.set_pole_slots(batch, int(table[key]))
         n = _I32()
         _check("rexi_tune", load().rexi_tune(self._h, batch, ctypes.byref(n)))
+        if cache:
+            table = _read_json(cache)
+            table[key] = n.value
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as fh:
+                json.dump(table, fh, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
         return n.value
+
+    def set_pole_slots(self, batch, slots):
+        """rexi_set_pole_slots: use this pole-slot count for steps with this batch size."""
+        n = _I32()
+        _check("rexi_set_pole_slots", load().rexi_set_pole_slots(self._h, batch, slots, ctypes.byref(n)))
+        return n.value
+
+    def _tune_key(self, batch):
+        import torch
+        i = self.info()
+        gpu = torch.cuda.get_device_name(torch.cuda.current_device())
+        return "N%d_%dx%d_P%d_B%d_%s_%s_%s_%s" % (i["N"], i["nlon"], i["nlat"], i["P"], batch, self.precision,
+                                                  self.solver, self.layout, gpu)
 
     def info(self):
         v = (ctypes.c_int64 * 8)()

@@ -64,3 +64,27 @@ def test_mixed_balanced_flow_stays_steady(env):
     y = plan.step(torch.from_numpy(x).cuda()).cpu().numpy()
     assert rel(y, x) < TOL_MIXED
     plan.close()
+
+
+def test_c2_batched_mixed_vs_fp64(env):
+    """T127 on 384x192, K=256 (P=535), 64 seeded states, tau=7200 s: the batched plain vs
+    mixed-precision configuration.  The FP64 form matches the oracle (two states, 1e-10);
+    the mixed form matches the FP64 form state by state within the stated 1e-5."""
+    torch, rexi = env
+    N, nlat, nlon, M, B, tau = 127, 192, 384, 256, 64, 7200.0
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    gs = ostep.GridStep(N, nlat, nlon, al, be, tau, C)
+    x = gs.synthesise(inputs.random_spectral(N, B, 1001))
+    X = torch.from_numpy(x).cuda()
+    out = {}
+    for prec in ("fp64", "mixed"):
+        plan = rexi.Plan(N, nlat, nlon, tau=tau, max_batch=B, alpha=al, beta=be, precision=prec)
+        plan.tune(B)
+        out[prec] = plan.step(X).cpu().numpy()
+        plan.check_device()
+        plan.close()
+    ref = gs(x[:2])
+    for f in range(3):
+        assert rel(out["fp64"][:2, f], ref[:, f]) < 1e-10
+    worst = max(rel(out["mixed"][b, f], out["fp64"][b, f]) for b in range(B) for f in range(3))
+    assert worst < TOL_MIXED

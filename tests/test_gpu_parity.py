@@ -209,3 +209,23 @@ def test_full_size_grid_step_bench_launch(torch, rexi, full_size_case, precision
     got = plan.step(torch.from_numpy(c["x"]).cuda()).cpu().numpy()
     plan.close()
     assert fieldwise(got[:1], c["ref"], axis_f=-3) < tol
+
+
+def test_tune_cache_and_set_pole_slots(torch, rexi, tmp_path):
+    N, M, B = 63, 64, 4
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    S = torch.from_numpy(spectral_state(N, B, 51)).cuda()
+    cache = str(tmp_path / "tune.json")
+    plan = rexi.Plan(N, 96, 192, tau=3600.0, max_batch=B, layout="spectral", alpha=al, beta=be)
+    s1 = plan.tune(B, cache=cache)          # miss: tunes and records
+    y1 = plan.step(S).cpu().numpy()
+    plan.close()
+    plan = rexi.Plan(N, 96, 192, tau=3600.0, max_batch=B, layout="spectral", alpha=al, beta=be)
+    s2 = plan.tune(B, cache=cache)          # hit: same layout without timing
+    y2 = plan.step(S).cpu().numpy()
+    assert s2 == s1
+    np.testing.assert_array_equal(y1, y2)   # same layout, same bits
+    used = plan.set_pole_slots(B, 3)        # any count is valid; results differ only in the sum order
+    assert used >= 1
+    assert fieldwise(plan.step(S).cpu().numpy(), y1) < 1e-13
+    plan.close()
