@@ -189,6 +189,40 @@ def cpu_baseline(sample_ms=None):
             "sample_seconds": t_solve + t_tr}
 
 
+def _oracle_solves(task):
+    """Worker: the oracle's banded solves for a subset of zonal orders (one state)."""
+    S, al, be, ms = task
+    from oracle import step as ostep
+    t0 = time.perf_counter()
+    ostep.rexi_step_spectral(S, WORK["N"], al, be, WORK["tau"], ms=ms)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(sample_ms=None):
+    """The same oracle sample with its zonal orders spread over every host core (one
+    process each, started by spawn); the oracle's code is unchanged."""
+    import multiprocessing as mp
+    from oracle import rexi_coeffs
+    from paper_1812_03431_gb300 import inputs
+    N, B = WORK["N"], WORK["batch"]
+    al, be, _ = rexi_coeffs.rexi_coefficients(WORK["M"], WORK["h"])
+    S = inputs.random_spectral(N, 1, WORK["seed"])
+    ms = sample_ms if sample_ms is not None else list(range(0, N + 1, 3))
+    n = max(1, min(os.cpu_count() or 1, len(ms)))
+    # interleaved chunks balance the decreasing row counts of higher orders
+    chunks = [ms[i::n] for i in range(n)]
+    with mp.get_context("spawn").Pool(n) as pool:
+        pool.map(_oracle_solves, [(S, al, be, [N]) for _ in range(n)], chunksize=1)  # start-up and imports
+        t0 = time.perf_counter()
+        pool.map(_oracle_solves, [(S, al, be, c) for c in chunks], chunksize=1)
+        wall = time.perf_counter() - t0
+    rows_sample = sum(N - m + 1 for m in ms)
+    rows_all = rows_of(N) + 1
+    return {"value": 1.0 / (B * wall * rows_all / rows_sample), "unit": "steps/s", "cores": n,
+            "sample_seconds": wall, "sample": "the banded solves of the same sample on %d processes; "
+            "transforms not included" % n}
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -420,6 +454,10 @@ def main():
         line["phi_solver_form"] = phi
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        try:
+            line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores()
+        except Exception as exc:  # a host without process support still gets the 1-core number
+            line["cpu_baseline"]["all_cores"] = {"unavailable": repr(exc)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -29,7 +29,8 @@ def env():
     return torch, rexi
 
 
-@pytest.mark.parametrize("N,nlat,nlon,M,B", [(31, 48, 96, 32, 2), (63, 96, 192, 64, 3), (127, 192, 384, 64, 17)])
+@pytest.mark.parametrize("N,nlat,nlon,M,B", [(1, 2, 4, 2, 1), (31, 48, 96, 32, 2), (63, 96, 192, 64, 3),
+                                             (127, 192, 384, 64, 17), (20, 30, 90, 16, 18)])
 def test_mixed_transforms_step_adjoint(env, N, nlat, nlon, M, B):
     torch, rexi = env
     al, be, _ = rc.rexi_coefficients(M, 0.2)

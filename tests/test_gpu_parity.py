@@ -45,8 +45,8 @@ def spectral_state(N, B, seed):
     return S
 
 
-@pytest.mark.parametrize("N,M,B,tau", [(2, 4, 1, 600.0), (15, 16, 3, 3600.0), (31, 32, 5, 7200.0),
-                                       (63, 128, 1, 3600.0), (63, 64, 17, 1800.0)])
+@pytest.mark.parametrize("N,M,B,tau", [(1, 2, 1, 600.0), (2, 4, 1, 600.0), (15, 16, 3, 3600.0), (31, 32, 5, 7200.0),
+                                       (63, 128, 1, 3600.0), (63, 64, 17, 1800.0), (23, 16, 33, 900.0)])
 def test_spectral_step_matches_oracle(torch, rexi, N, M, B, tau):
     al, be, _ = rc.rexi_coefficients(M, 0.2)
     S = spectral_state(N, B, 100 + N)
@@ -86,7 +86,8 @@ def test_single_pole_solve(torch, rexi, k):
     assert fieldwise(got, ref) < TOL
 
 
-@pytest.mark.parametrize("N,nlat,nlon,M,B", [(31, 48, 96, 32, 2), (63, 96, 192, 128, 3), (42, 64, 160, 48, 1)])
+@pytest.mark.parametrize("N,nlat,nlon,M,B", [(1, 2, 4, 2, 1), (31, 48, 96, 32, 2), (63, 96, 192, 128, 3),
+                                             (42, 64, 160, 48, 1), (20, 30, 90, 16, 18)])
 def test_grid_step_matches_oracle(torch, rexi, N, nlat, nlon, M, B):
     tau = 3600.0
     al, be, _ = rc.rexi_coefficients(M, 0.2)
