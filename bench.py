@@ -433,6 +433,7 @@ def main():
                      "traffic": SOLVE_TRAFFIC_T170[tslots] * rows_of(W["N"]) / rows_of(170),
                      "traffic_source": "ncu dram bytes at T170/K256/B16 with %d pole slots (the captured "
                                        "layout nearest the bench's %d), scaled by rows to T341" % (tslots, r["slots"]),
+                     "dram_gbs": SOLVE_TRAFFIC_T170[tslots] * rows_of(W["N"]) / rows_of(170) / (solve_ms * 1e-3) / 1e9,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz",
                      "flops_per_launch": flops, "launch_ms": solve_ms},
         "stage_ms": r["stages"],
