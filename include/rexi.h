@@ -39,6 +39,10 @@
  *   is allocated inside rexi_step / rexi_step_adjoint once a batch size has
  *   been seen by the plan (its work list is cached), so those calls can be
  *   captured in a CUDA graph after a first eager call with the same batch.
+ *   A plan's workspaces (transposed states, Fourier data, slot partials) serve
+ *   one call at a time: calls on one plan must be ordered on the GPU (one
+ *   stream, or events between streams); independent plans may run
+ *   concurrently.
  * Errors: negative rexi_status; rexi_last_error() gives a thread-local
  *   message.  A CUDA launch error is reported by the call that launched.
  */
