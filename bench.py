@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 
 WORK = dict(N=341, nlat=512, nlon=1024, M=256, h=0.2, tau=1200.0, batch=16, seed=1005)
 METRIC = "REXI steps/s at T341, K=256 poles: chosen vs plain FP64 form at stated error"
-FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve: 36 FMAs (see DESIGN.md)
+FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve: 36 FMAs
 # DRAM bytes (read + write) of one solve_kernel launch from ncu captures at T170, K=256,
 # batch 16, by pole-slot count (profiles/solve_kernel_t170_b16.md); traffic per row is
 # constant, so a launch of the bench workload moves this times rows(T341) / rows(T170).

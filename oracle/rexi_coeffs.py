@@ -9,7 +9,7 @@ Construction, in the paper's order and notation:
    The paper takes mu and a_l from Haut et al., Table 1, which is not available
    here; they are refitted: for fixed mu the fit is linear least squares in
    (Re a_l, Im a_l) on dense samples of y = x/h, and mu < 0 is chosen by a
-   golden-section search on the sup error.  (Reading: the design doc.)
+   golden-section search on the sup error (a reading: the table is missing).
 2. Gaussian-basis expansion of the exponential (Sec. 4.1, second block):
    exp(i x) ~ sum_{m=-M}^{M} b_m psi_h(x + m h).  The paper prints no b_m;
    Poisson summation of the Gaussian gives b_m = exp(h^2) exp(-i m h)
@@ -18,7 +18,7 @@ Construction, in the paper's order and notation:
    ~ sum_n Re( beta^Re_n / (i x + alpha_n) ) with
    alpha_n = h (mu + i n),  beta^Re_n = h sum_{l+m=n} Re(b_m) a_l,
    n = -(M+K) .. (M+K); the imaginary-part set beta^Im uses Im(b_m).
-4. Merge (reading): the linear SWE operator and state are real, and
+4. Merge (a reading of "merged"): the linear SWE operator and state are real, and
    for a real operator the conjugate-symmetric imaginary-part terms contribute
    exactly zero to Re(sum beta X); the coefficient set applied in Algorithm 1
    is beta_n = beta^Re_n.  With it the x = 0 residual
@@ -30,7 +30,7 @@ Construction, in the paper's order and notation:
 Pins: symmetry a_{-l} = conj(a_l) and the fit's sup error; the real part of
 the response equals cos(x) to the fit level on |x| <= h(M-10); the x = 0
 residual is of the printed order; the imaginary part obeys the closed-form
-truncation bound derived from the Hilbert-transform tail; and
+truncation bound derived from the Hilbert-transform tail of the b_m sum; and
 conjugate symmetry alpha_{-n} = conj(alpha_n), beta_{-n} = conj(beta_n).
 """
 

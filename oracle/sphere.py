@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-Conventions (the paper defers to SHTns defaults and fixes none of them; these
-readings are listed in the design doc):
+Conventions (the paper defers to SHTns defaults and fixes none of them, so these
+are readings):
 
 * Triangular truncation at degree N: coefficients xi_n^m for 0 <= m <= n <= N,
   stored m-major, ``idx(m, n) = m(2N+3-m)/2 + (n-m)``, ``nspec=(N+1)(N+2)/2``.

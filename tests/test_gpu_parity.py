@@ -1,8 +1,8 @@
 """CUDA path (librexi through its C-ABI) vs the CPU oracle, element by element.
 
-FP64 tolerance: relative L2 error <= 1e-10 per field (the plain-FP64 bound of
-the benchmark spec; rounding differences come from the pole-sum order,
-the delta-eliminated vs full banded solves and the FFT algorithm).
+FP64 tolerance: relative L2 error <= 1e-10 per field (the stated bound for the
+plain FP64 form; rounding differences come from the pole-sum order, the
+delta-eliminated vs full banded solves and the FFT algorithm).
 """
 import numpy as np
 import pytest
@@ -152,7 +152,7 @@ def test_deterministic_and_slot_invariant(torch, rexi):
 
 
 def test_geostrophic_balance_grid(torch, rexi):
-    # the C1 state without noise: the normalised REXI step keeps it steady (Sec. 6.1)
+    # the balanced zonal flow without noise: the normalised REXI step keeps it steady (Sec. 6.1)
     N, nlat, nlon = 63, 96, 192
     plan = rexi.Plan(N, nlat, nlon, M=128, tau=3600.0)
     from oracle.sphere import gauss_legendre

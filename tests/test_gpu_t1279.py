@@ -37,7 +37,7 @@ def test_t1279_spectral_step_sampled_orders():
 
 
 def test_t1279_mixed_vs_fp64_grid_step():
-    """The C5 comparison: 3xTF32 Legendre + FP32 FFTs vs all-FP64, same poles, one state."""
+    """T1279 on 3840x1920, K=512: 3xTF32 Legendre + FP32 FFTs vs all-FP64, same poles, one state."""
     import torch
     from paper_1812_03431_gb300 import rexi
     S = torch.from_numpy(inputs.random_spectral(N, 1, 1004)).cuda()

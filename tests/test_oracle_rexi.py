@@ -44,7 +44,7 @@ def test_x0_residual_has_printed_order(golden):
     assert abs(eps.imag) < 1e-15
     assert 1e-3 * abs(printed) < abs(eps.real) < 10 * abs(printed)
     # the other merges of the real and imaginary sets are far off at x = 0, which is what
-    # selects beta = beta^Re as the reading of "merged" (DESIGN.md)
+    # selects beta = beta^Re as the reading of "merged"
     al, bre, bim = rc.rexi_parts(128, golden["h_paper"])
     for beta in (0.5 * (bre + 1j * bim), bre + 1j * bim):
         assert abs(1 - np.sum(beta / al)) > 1e-4
