@@ -198,19 +198,22 @@ rexi_status rexi_solve_pole(rexi_plan *plan, int32_t k, const void *in_dev, void
 rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *beta, int32_t *P);
 
 /* Autotuner (no paper counterpart; a tuning knob of this implementation): times
- * the banded-solve kernel at this batch size for 1, 2, 4, ... pole groups (the
- * number of partial sums per coefficient, which trades load balance against
- * reduction traffic), keeps the fastest for later steps with this batch and
- * writes the chosen slot count to *slots.  Synchronous; uses the plan's
+ * the banded solve and the slot reduction at this batch size for 1, 2, 4, ... pole
+ * groups (the number of partial sums per coefficient, which trades load balance
+ * against reduction work) in two shapes -- 0: the same number of groups for every
+ * zonal order; 1: groups in proportion to the order's system length -- keeps the
+ * fastest for later steps with this batch and writes its slot count to *slots and
+ * its shape to *shape (either may be NULL).  Synchronous; uses the plan's
  * workspaces, so no step of this plan may be in flight. */
-rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots);
+rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots, int32_t *shape);
 
 /* Sets the pole-slot layout for steps with this batch size without timing (for instance
- * from a cache of earlier rexi_tune results); slots >= 1 is rounded down to a multiple
- * of the lanes a warp gives each state (and capped by the partial-sum buffer), the
- * count used is written to *used (may be NULL).  Results are deterministic for any
- * count; only the order of the final pole sum changes.  Synchronous, like rexi_tune. */
-rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t *used);
+ * from a cache of earlier rexi_tune results): slots >= 1 (rounded down to a multiple of
+ * the lanes a warp gives each state and capped by the partial-sum buffer) and shape 0
+ * or 1 as for rexi_tune; the slot count used is written to *used (may be NULL).
+ * Results are deterministic for any layout; only the order of the final pole sum
+ * changes.  Synchronous, like rexi_tune. */
+rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t shape, int32_t *used);
 
 /* Host-side description of a plan: writes up to 8 int64 values
  * {N, nspec, P, nlat, nlon, max_batch, pole_slots, device bytes held}. */

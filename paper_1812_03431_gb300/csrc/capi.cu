@@ -20,8 +20,8 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl);
 rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out);
 void free_plan(Plan *pl);
 rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t st);
-rexi_status tune_layout(Plan &pl, int B, int *slots_out);
-rexi_status set_layout(Plan &pl, int B, int slots, int *used);
+rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out);
+rexi_status set_layout(Plan &pl, int B, int slots, int shape, int *used);
 
 namespace {
 
@@ -387,21 +387,23 @@ rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *
   return REXI_OK;
 }
 
-rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots) {
+rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots, int32_t *shape) {
   if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
   Plan &pl = *plan->pl;
   if (batch < 1 || batch > pl.prm.max_batch) { set_error("rexi_tune: batch must be in [1, max_batch]"); return REXI_EINVAL; }
-  int s = 0;
+  int s = 0, sh = 0;
   if (pl.prm.fsphere) {  // no banded solves, nothing to tune
     if (slots) *slots = 0;
+    if (shape) *shape = 0;
     return REXI_OK;
   }
-  rexi_status r = tune_layout(pl, batch, &s);
+  rexi_status r = tune_layout(pl, batch, &s, &sh);
   if (r == REXI_OK && slots) *slots = s;
+  if (r == REXI_OK && shape) *shape = sh;
   return r;
 }
 
-rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t *used) {
+rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t shape, int32_t *used) {
   if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
   Plan &pl = *plan->pl;
   if (batch < 1 || batch > pl.prm.max_batch || slots < 1) {
@@ -413,7 +415,7 @@ rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, i
     return REXI_OK;
   }
   int u = 0;
-  rexi_status r = set_layout(pl, batch, slots, &u);
+  rexi_status r = set_layout(pl, batch, slots, shape, &u);
   if (r == REXI_OK && used) *used = u;
   return r;
 }

@@ -276,6 +276,7 @@ struct PhiSolveArgs {
   const int4 *sys;
   double2 *ybuf;
   const WorkItem *items;
+  const int32_t *slots_m;  // per zonal order slot count (<= slots, the partial stride)
   unsigned *counter;
   int nitems, lmax, P, N, B, bw, kk, slots;
   int64_t nspec, nrows;
@@ -394,7 +395,8 @@ __global__ void __launch_bounds__(128) phi_solve_kernel(PhiSolveArgs a) {
     const int4 sy = a.sys[2 * w.m + p];
     const int m = sy.x, n0 = sy.y, len = sy.z;
     const int slot = w.g * a.kk + kk;
-    if (kk >= a.kk || b >= a.B || len <= 0 || slot >= a.slots) continue;
+    const int Sm = a.slots_m[m];
+    if (kk >= a.kk || b >= a.B || len <= 0 || slot >= Sm) continue;
     const int64_t NS = a.nspec, S = a.slots, B = a.B;
     const int64_t base = base_of(a.N, m);
     double2 *pP = a.part + (int64_t)slot * B + b;
@@ -404,8 +406,8 @@ __global__ void __launch_bounds__(128) phi_solve_kernel(PhiSolveArgs a) {
     const double2 *qb = a.q + b;
     bool first = true;
     int k0 = slot;
-    for (; k0 + a.slots < a.P; k0 += 2 * a.slots) {
-      const int kp[2] = {k0, k0 + a.slots};
+    for (; k0 + Sm < a.P; k0 += 2 * Sm) {
+      const int kp[2] = {k0, k0 + Sm};
       phi_sweep<2>(a, kp, m, n0, len, sy.w, base, qb, pP, pZ, pD, rstride, first, ybuf);
       first = false;
     }
@@ -424,6 +426,7 @@ struct PhiReduceArgs {
   const double2 *w;       // [nspec] sum_k beta_k / (alpha_k + i tau sigma_n)
   const double *coef;     // [nspec][4]
   const int32_t *m_of;
+  const int32_t *slots_m; // per zonal order slot count (<= slots, the partial stride)
   double2 sumb;           // sum_k beta_k
   int slots, B, N;
   int64_t nspec;
@@ -443,15 +446,16 @@ __global__ void phi_reduce_kernel(PhiReduceArgs a) {
     if (!(fl & 2)) {
       if (fl & 1) {
         const double2 *p = a.part + fi * a.slots * a.B + b;
+        const int Sm = a.slots_m[a.m_of[ix]];
         int s = 0;
-        for (; s + 8 <= a.slots; s += 8) {
+        for (; s + 8 <= Sm; s += 8) {
           double2 v[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + (int64_t)(s + u) * a.B);
 #pragma unroll
           for (int u = 0; u < 8; ++u) acc = cadd(acc, v[u]);
         }
-        for (; s < a.slots; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
+        for (; s < Sm; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
       }
       const int64_t NB = a.nspec * a.B;
       const int64_t sb = ix * a.B + b;
@@ -520,6 +524,7 @@ cudaError_t launch_phi_solve(Plan &pl, const SolveLayout &lay, const double2 *si
     s.sys = pl.sys_dev;
     s.ybuf = pl.yscratch;
     s.items = lay.items_dev;
+    s.slots_m = lay.slots_m_dev;
     s.counter = pl.counter;
     s.nitems = lay.nitems;
     s.lmax = pl.lmax;
@@ -551,6 +556,7 @@ cudaError_t launch_phi_reduce(Plan &pl, const SolveLayout &lay, const double2 *s
   r.w = pl.w_fwd;
   r.coef = pl.coef_dev;
   r.m_of = pl.m_of_dev;
+  r.slots_m = lay.slots_m_dev;
   r.sumb = pl.sumb;
   r.slots = lay.slots;
   r.B = B;

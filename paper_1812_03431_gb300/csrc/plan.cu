@@ -363,9 +363,14 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
 
 // Work list for batch B with a given number of pole groups (0: heuristic):
 // items (m, slot group, first state), longest first.
-rexi_status build_layout(Plan &pl, int B, bool single, int groups_req, SolveLayout &L) {
+// shape 0: every zonal order gets the same number of pole groups (items of different
+// sizes, packed longest first); shape 1: groups in proportion to the system length
+// (items of similar size, fewer partial sums for the short high orders).  Which is
+// faster depends on the batch: the autotuner times both.
+rexi_status build_layout(Plan &pl, int B, bool single, int groups_req, SolveLayout &L, int shape) {
   L = SolveLayout{};
   L.batch = B;
+  L.shape = single ? 0 : shape;
   int bw = 1;
   while (bw < B && bw < 16) bw *= 2;
   L.bw = bw;
@@ -393,23 +398,43 @@ rexi_status build_layout(Plan &pl, int B, bool single, int groups_req, SolveLayo
     L.groups = std::max(1, std::min(g, slots_cap / L.kk));
   }
   L.slots = L.groups * L.kk;
-  std::vector<WorkItem> items;
+  // pole groups per zonal order (shape 1: in proportion to its system length, the
+  // longest orders getting L.groups, so that every item carries about the same work)
+  int lmax = 1;
+  for (int m = 0; m <= pl.N; ++m) lmax = std::max(lmax, std::max(pl.sys[2 * m].len, pl.sys[2 * m + 1].len));
+  L.groups_m.assign(pl.N + 1, 1);
+  std::vector<int32_t> slots_m(pl.N + 1, L.kk);
+  for (int m = 0; m <= pl.N; ++m) {
+    const int l = std::max(pl.sys[2 * m].len, pl.sys[2 * m + 1].len);
+    L.groups_m[m] = L.shape == 0 ? L.groups
+                                 : std::max(1, std::min(L.groups, (int)(((int64_t)L.groups * l + lmax - 1) / lmax)));
+    slots_m[m] = L.groups_m[m] * L.kk;
+  }
+  struct Keyed { WorkItem w; double work; };
+  std::vector<Keyed> keyed;
   const int nb = (B + bw - 1) / bw;
   for (int m = 0; m <= pl.N; ++m) {
     const int l = std::max(pl.sys[2 * m].len, pl.sys[2 * m + 1].len);
     if (l == 0) continue;
-    for (int g = 0; g < L.groups; ++g)
-      for (int bb = 0; bb < nb; ++bb) items.push_back(WorkItem{m, g, bb * bw, l});
+    const double work = (double)l * ((pl.P + slots_m[m] - 1) / slots_m[m]);
+    for (int g = 0; g < L.groups_m[m]; ++g)
+      for (int bb = 0; bb < nb; ++bb) keyed.push_back(Keyed{WorkItem{m, g, bb * bw, l}, work});
   }
-  std::stable_sort(items.begin(), items.end(),
-                   [](const WorkItem &x, const WorkItem &y) { return x.len > y.len; });
+  std::stable_sort(keyed.begin(), keyed.end(), [](const Keyed &x, const Keyed &y) { return x.work > y.work; });
+  std::vector<WorkItem> items;
+  for (const Keyed &k : keyed) items.push_back(k.w);
   L.nitems = (int)items.size();
-  cudaError_t e = cudaMalloc(&L.items_dev, std::max<size_t>(1, items.size()) * sizeof(WorkItem));
+  const size_t item_bytes = std::max<size_t>(1, items.size()) * sizeof(WorkItem);
+  void *mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, item_bytes + slots_m.size() * sizeof(int32_t));
   if (e != cudaSuccess) {
     set_error(std::string("work list: ") + cudaGetErrorString(e));
     return REXI_ENOMEM;
   }
+  L.items_dev = static_cast<WorkItem *>(mem);
+  L.slots_m_dev = reinterpret_cast<int32_t *>(static_cast<char *>(mem) + item_bytes);
   cudaMemcpy(L.items_dev, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+  cudaMemcpy(L.slots_m_dev, slots_m.data(), slots_m.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   return REXI_OK;
 }
 
@@ -421,7 +446,11 @@ rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out) {
     return REXI_OK;
   }
   SolveLayout L;
-  rexi_status r = build_layout(pl, B, single, single ? 1 : pl.slots_override, L);
+  // default shape: proportional groups for one or two states per warp, where the
+  // uniform layout leaves most pole groups short of work
+  int bw = 1;
+  while (bw < B && bw < 16) bw *= 2;
+  rexi_status r = build_layout(pl, B, single, single ? 1 : pl.slots_override, L, bw <= 2 ? 1 : 0);
   if (r != REXI_OK) return r;
   auto res = pl.layouts.emplace(key, L);
   *out = &res.first->second;
@@ -430,12 +459,12 @@ rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out) {
 
 // A given slot count for batch B: the layout with slots / kk pole groups replaces any
 // earlier one for that batch.
-rexi_status set_layout(Plan &pl, int B, int slots, int *used) {
+rexi_status set_layout(Plan &pl, int B, int slots, int shape, int *used) {
   SolveLayout L;
   int bw = 1;
   while (bw < B && bw < 16) bw *= 2;
   const int kk = std::max(1, std::min(32 / (2 * bw), (int)pl.partial_cap));
-  rexi_status r = build_layout(pl, B, false, std::max(1, slots / kk), L);
+  rexi_status r = build_layout(pl, B, false, std::max(1, slots / kk), L, shape != 0 ? 1 : 0);
   if (r != REXI_OK) return r;
   auto it = pl.layouts.find(B);
   if (it != pl.layouts.end()) {
@@ -449,7 +478,7 @@ rexi_status set_layout(Plan &pl, int B, int slots, int *used) {
 
 // Autotuner: time the solve kernel for each candidate number of pole groups at
 // batch B and keep the fastest layout for later steps with that batch.
-rexi_status tune_layout(Plan &pl, int B, int *slots_out) {
+rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
   cudaStream_t st = 0;
   cudaError_t e = cudaMemsetAsync(pl.s_in, 0, (size_t)3 * pl.nspec * B * sizeof(double2), st);
   if (e != cudaSuccess) {
@@ -462,15 +491,16 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out) {
   float best = 1e30f;
   SolveLayout bestL{};
   std::vector<int> tried;
-  for (int g = 1; g <= 256; g *= 2) {
+  for (int cand = 0; cand < 2 * 9; ++cand) {
+    const int g = 1 << (cand >> 1), shape = cand & 1;
     SolveLayout L;
-    rexi_status r = build_layout(pl, B, false, g, L);
+    rexi_status r = build_layout(pl, B, false, g, L, shape);
     if (r != REXI_OK) return r;
-    if (std::find(tried.begin(), tried.end(), L.slots) != tried.end()) {
+    if (std::find(tried.begin(), tried.end(), 2 * L.slots + shape) != tried.end()) {
       cudaFree(L.items_dev);
       continue;
     }
-    tried.push_back(L.slots);
+    tried.push_back(2 * L.slots + shape);
     // time the solve and the slot reduction together (more slots balance the solve
     // better but make the reduction read more partial sums)
     auto run = [&]() {
@@ -506,6 +536,7 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out) {
   }
   pl.layouts.emplace(B, bestL);
   if (slots_out) *slots_out = bestL.slots;
+  if (shape_out) *shape_out = bestL.shape;
   return REXI_OK;
 }
 

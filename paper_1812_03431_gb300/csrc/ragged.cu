@@ -130,12 +130,13 @@ rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *c
       const SolveLayout &L = *lays[p];
       views[p] = make_view(pl, L, false, pl.s_in, pl.partial, counts[p], 0, pl.P);
       const int nb = (counts[p] + L.bw - 1) / L.bw;
-      const double per_slot = (double)((pl.P + L.slots - 1) / L.slots);
       for (int m = 0; m <= pl.N; ++m) {
         const int l = std::max(pl.sys[2 * m].len, pl.sys[2 * m + 1].len);
         if (l == 0) continue;
-        for (int g = 0; g < L.groups; ++g)
-          for (int bb = 0; bb < nb; ++bb) all.push_back(Tagged{WorkItem{m, g, bb * L.bw, p}, l * per_slot});
+        const int sm = L.groups_m[m] * L.kk;
+        const double work = (double)l * ((pl.P + sm - 1) / sm);
+        for (int g = 0; g < L.groups_m[m]; ++g)
+          for (int bb = 0; bb < nb; ++bb) all.push_back(Tagged{WorkItem{m, g, bb * L.bw, p}, work});
       }
     }
     std::stable_sort(all.begin(), all.end(), [](const Tagged &x, const Tagged &y) { return x.work > y.work; });

@@ -82,9 +82,14 @@ struct WorkItem {
 // Lane layout of the solve kernel for a given batch: lane = (b_local, p, kk)
 // with bw * 2 * kk_per_warp = 32.
 struct SolveLayout {
-  int batch, bw, kk, groups, slots;  // slots = groups * kk
+  int batch, bw, kk, groups, slots;  // slots = groups * kk: the partial buffer's slot stride
+  int shape = 0;                     // 0: same groups for every order; 1: in proportion to length
   int nitems;
-  WorkItem *items_dev = nullptr;
+  WorkItem *items_dev = nullptr;     // nitems items, followed by slots_m (one allocation)
+  // per zonal order: pole groups proportional to the system length, so that items carry
+  // similar work; order m uses slots_m[m] = groups_m[m] * kk <= slots partial sums
+  std::vector<int> groups_m;
+  int32_t *slots_m_dev = nullptr;
 };
 
 struct FftPlan {
@@ -199,6 +204,7 @@ struct SolveView {
   const int4 *sys;      // per (m, p): {m, n0, len, row0}
   int P, N, B, bw, kk, slots, pole_begin, pole_end;
   int64_t nspec, nrows;
+  const int32_t *slots_m;  // per zonal order slot count (<= slots), or null for slots everywhere
 };
 SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, double2 *part, int B,
                     int pole_begin, int pole_end);

@@ -298,7 +298,8 @@ __device__ __forceinline__ void solve_item(const SolveView &a, int wm, int wg, i
   const int m = sy.x, n0 = sy.y, len = sy.z;
   const int64_t row0 = sy.w;
   const int slot = wg * a.kk + kk;
-  if (kk >= a.kk || b >= B || len <= 0 || slot >= S) return;
+  const int Sm = a.slots_m ? a.slots_m[m] : S;  // this order's slot count; S is the buffer stride
+  if (kk >= a.kk || b >= B || len <= 0 || slot >= Sm) return;
   const int nmin = m > 1 ? m : 1;
   const int64_t base_idx = (int64_t)m * (2 * N + 3 - m) / 2 - m;  // idx(m, n) = base_idx + n
   const double2 *sPhi = a.sin + b;
@@ -310,8 +311,8 @@ __device__ __forceinline__ void solve_item(const SolveView &a, int wm, int wg, i
   const int64_t rstride = (int64_t)S * B;  // partial stride per idx
   bool first = true;
   int k0 = a.pole_begin + slot;
-  for (; k0 + S < a.pole_end; k0 += 2 * S) {
-    const int kp[2] = {k0, k0 + S};
+  for (; k0 + Sm < a.pole_end; k0 += 2 * Sm) {
+    const int kp[2] = {k0, k0 + Sm};
     sweep_poles<2>(a, kp, n0, len, nmin, row0, base_idx, sPhi, sZeta, sDel, pPhi, pZeta, pDel, rstride, first,
                    ybuf);
     first = false;
@@ -372,6 +373,7 @@ struct ReduceArgs {
   const double2 *w;        // [nspec] zeta weights sum beta/s
   const double *coef;      // [nspec][4] (for single-pole s_n)
   const int32_t *m_of;     // [nspec] zonal order of idx
+  const int32_t *slots_m;  // per zonal order slot count (<= slots, the partial stride), or null
   double2 sphi;
   int slots, B, N;
   int64_t nspec;
@@ -417,15 +419,16 @@ __global__ void reduce_kernel(ReduceArgs a) {
       if (fl & 1) {
         // loads issued eight at a time, added strictly in slot order (bit-reproducible)
         const double2 *p = a.part + fi * a.slots * a.B + b;
+        const int Sm = a.slots_m ? a.slots_m[a.m_of[ix]] : a.slots;
         int s = 0;
-        for (; s + 8 <= a.slots; s += 8) {
+        for (; s + 8 <= Sm; s += 8) {
           double2 v[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + (int64_t)(s + u) * a.B);
 #pragma unroll
           for (int u = 0; u < 8; ++u) acc = cadd(acc, v[u]);
         }
-        for (; s < a.slots; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
+        for (; s < Sm; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
       }
       acc = reduce_finish(a, t, f, ix, acc);
     }
@@ -449,7 +452,8 @@ __global__ void reduce_wide_kernel(ReduceArgs a) {
     if (!(fl & 2)) {
       if (fl & 1) {
         const double2 *p = a.part + fi * a.slots * a.B + b;
-        for (int s = lane; s < a.slots; s += 32) acc = cadd(acc, __ldcs(p + (int64_t)s * a.B));
+        const int Sm = a.slots_m ? a.slots_m[a.m_of[ix]] : a.slots;
+        for (int s = lane; s < Sm; s += 32) acc = cadd(acc, __ldcs(p + (int64_t)s * a.B));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
@@ -601,6 +605,7 @@ SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double
   v.bw = lay.bw;
   v.kk = lay.kk;
   v.slots = lay.slots;
+  v.slots_m = lay.slots_m_dev;
   v.pole_begin = pole_begin;
   v.pole_end = pole_end;
   v.nspec = pl.nspec;
@@ -644,6 +649,7 @@ cudaError_t launch_reduce(Plan &pl, const SolveLayout &lay, bool adjoint, const 
   a.m_of = pl.m_of_dev;
   a.sphi = adjoint ? pl.sphi_adj : pl.sphi_fwd;
   a.slots = single_pole ? 1 : lay.slots;
+  a.slots_m = single_pole ? nullptr : lay.slots_m_dev;
   a.B = B;
   a.N = pl.N;
   a.nspec = pl.nspec;
@@ -783,6 +789,7 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
     a.v.bw = bw;
     a.v.kk = slots;
     a.v.slots = slots;
+    a.v.slots_m = nullptr;
     a.v.pole_begin = 0;
     a.v.pole_end = pl.P;
     a.v.nspec = pl.nspec;
@@ -806,6 +813,7 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
     r.m_of = pl.m_of_dev;
     r.sphi = pl.sphi_fwd;
     r.slots = slots;
+    r.slots_m = nullptr;
     r.B = B;
     r.N = pl.N;
     r.nspec = pl.nspec;

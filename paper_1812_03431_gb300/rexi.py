@@ -47,7 +47,7 @@ _DP = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "rexi_params_default": (None, [ctypes.POINTER(rexi_params)]),
     "rexi_params_size": (ctypes.c_size_t, []),
-    "rexi_set_pole_slots": (ctypes.c_int32, [_VP, _I32, _I32, ctypes.POINTER(_I32)]),
+    "rexi_set_pole_slots": (ctypes.c_int32, [_VP, _I32, _I32, _I32, ctypes.POINTER(_I32)]),
     "rexi_coefficients": (_I32, [_I32, ctypes.c_double, _I32, _DP, _DP, ctypes.POINTER(_I32), _DP]),
     "rexi_plan_create": (_I32, [ctypes.POINTER(rexi_params), ctypes.POINTER(_VP)]),
     "rexi_step": (_I32, [_VP, _VP, _VP, _I32, _VP]),
@@ -58,7 +58,7 @@ SIGNATURES = {
     "rexi_solve_pole": (_I32, [_VP, _I32, _VP, _VP, _I32, _VP]),
     "rexi_get_coefficients": (_I32, [_VP, _DP, _DP, ctypes.POINTER(_I32)]),
     "rexi_plan_info": (_I32, [_VP, ctypes.POINTER(ctypes.c_int64), _I32]),
-    "rexi_tune": (_I32, [_VP, _I32, ctypes.POINTER(_I32)]),
+    "rexi_tune": (_I32, [_VP, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "rexi_ragged_create": (_I32, [ctypes.POINTER(_VP), _I32, _I32, ctypes.POINTER(_VP)]),
     "rexi_ragged_step": (_I32, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_I32), _I32, _VP]),
     "rexi_ragged_destroy": (None, [_VP]),
@@ -169,6 +169,7 @@ class Plan:
         self._h = h_
         self.N, self.nlat, self.nlon, self.max_batch = N, nlat, nlon, max_batch
         self.layout, self.precision, self.solver = layout, precision, solver
+        self.layout_shape = {}
         self.nspec = (N + 1) * (N + 2) // 2
 
     # -- helpers
@@ -249,8 +250,9 @@ class Plan:
         return al.view(np.complex128).copy(), be.view(np.complex128).copy()
 
     def tune(self, batch, cache=None):
-        """rexi_tune: time the solve kernel for several pole-group counts at this batch size
-        and keep the fastest; returns the chosen number of pole slots.
+        """rexi_tune: time the solve and reduction for several pole-group counts and both
+        layout shapes at this batch size and keep the fastest; returns the chosen number
+        of pole slots (the shape is kept in ``self.layout_shape[batch]``).
 
         ``cache``: path of a JSON file of earlier choices keyed by the plan's shape (N,
         grid, P, batch, precision, solver) and the GPU's name; a hit sets the layout
@@ -260,22 +262,26 @@ class Plan:
             key = self._tune_key(batch)
             table = _read_json(cache)
             if key in table:
-                return self.set_pole_slots(batch, int(table[key]))
-        n = _I32()
-        _check("rexi_tune", load().rexi_tune(self._h, batch, ctypes.byref(n)))
+                slots, shape = table[key]
+                return self.set_pole_slots(batch, int(slots), int(shape))
+        n, sh = _I32(), _I32()
+        _check("rexi_tune", load().rexi_tune(self._h, batch, ctypes.byref(n), ctypes.byref(sh)))
+        self.layout_shape[batch] = sh.value
         if cache:
             table = _read_json(cache)
-            table[key] = n.value
+            table[key] = [n.value, sh.value]
             tmp = cache + ".tmp"
             with open(tmp, "w") as fh:
                 json.dump(table, fh, indent=1, sort_keys=True)
             os.replace(tmp, cache)
         return n.value
 
-    def set_pole_slots(self, batch, slots):
-        """rexi_set_pole_slots: use this pole-slot count for steps with this batch size."""
+    def set_pole_slots(self, batch, slots, shape=0):
+        """rexi_set_pole_slots: use this pole-slot count and layout shape (0: the same groups
+        for every zonal order, 1: in proportion to the system length) for this batch size."""
         n = _I32()
-        _check("rexi_set_pole_slots", load().rexi_set_pole_slots(self._h, batch, slots, ctypes.byref(n)))
+        _check("rexi_set_pole_slots", load().rexi_set_pole_slots(self._h, batch, slots, shape, ctypes.byref(n)))
+        self.layout_shape[batch] = shape
         return n.value
 
     def _tune_key(self, batch):
