@@ -336,7 +336,9 @@ def main():
         yh = torch.empty(y.shape, dtype=y.dtype).pin_memory()
         xd = [torch.empty_like(x) for _ in range(2)]
         yd = [torch.empty_like(y) for _ in range(2)]
-        h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+        # a compute stream of its own and two copy streams, none of them the legacy
+        # default stream (which would serialise with the others)
+        cs, h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
 
         def e2e_steps(n, start_event):
             computed, copied_back = [None, None], [None, None]
@@ -350,30 +352,31 @@ def main():
                     xd[k].copy_(xh, non_blocking=True)
                     loaded = torch.cuda.Event()
                     loaded.record(h2d)
-                stream.wait_event(loaded)
+                cs.wait_event(loaded)
                 if copied_back[k] is not None:
-                    stream.wait_event(copied_back[k])  # yd[k] of step i-2 is on the host
-                plan.step(xd[k], out=yd[k])
+                    cs.wait_event(copied_back[k])  # yd[k] of step i-2 is on the host
+                plan.step(xd[k], out=yd[k], stream=cs)
                 computed[k] = torch.cuda.Event()
-                computed[k].record(stream)
+                computed[k].record(cs)
                 with torch.cuda.stream(d2h):
                     d2h.wait_event(computed[k])
                     yh.copy_(yd[k], non_blocking=True)
                     copied_back[k] = torch.cuda.Event()
                     copied_back[k].record(d2h)
                 last = copied_back[k]
-            stream.wait_event(last)
+            cs.wait_event(last)
 
+        torch.cuda.synchronize()
         w0 = torch.cuda.Event()
-        w0.record(stream)
+        w0.record(cs)
         e2e_steps(2, w0)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
+        f0.record(cs)
         e2e_steps(args.steps, f0)
-        f1.record(stream)
+        f1.record(cs)
         torch.cuda.synchronize()
         ms_e2e = f0.elapsed_time(f1) / args.steps
         ms_e2e = replica_max_ms(ms_e2e, dist)
