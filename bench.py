@@ -31,10 +31,10 @@ WORK = dict(N=341, nlat=512, nlon=1024, M=256, h=0.2, tau=1200.0, batch=16, seed
 METRIC = "REXI steps/s at T341, K=256 poles: chosen vs plain FP64 form at stated error"
 FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve: 36 FMAs
 # DRAM bytes (read + write) of one solve_kernel launch from ncu captures at T170, K=256,
-# batch 16, by pole-slot count (profiles/solve_kernel_t170_b16.md); traffic per row is
-# constant, so a launch of the bench workload moves this times rows(T341) / rows(T170).
-# Re-captured after each change of the solve kernel.
-SOLVE_TRAFFIC_T170 = {47: 10.47e9, 64: 10.23e9}
+# batch 16, by (pole slots, layout shape) (profiles/solve_kernel_t170_b16.md); traffic per
+# row is constant, so a launch of the bench workload moves this times rows(T341) /
+# rows(T170).  Re-captured after each change of the solve kernel.
+SOLVE_TRAFFIC_T170 = {(32, 0): 12.64e9, (32, 1): 12.58e9}
 
 
 def rows_of(N):
@@ -383,7 +383,7 @@ def main():
         e2e_same = bool(torch.equal(yh, y.cpu()))  # the copied-back result is the device step's, bit for bit
         results[prec] = dict(ms=ms, ms_e2e=ms_e2e, stages={k: v / max(ncalls, 1) for k, v in stages.items()},
                              clocks=ck, y=y, bytes=x.numel() * 8, info=plan.info(), slots=slots,
-                             e2e_same=e2e_same)
+                             shape=plan.layout_shape.get(B, 0), e2e_same=e2e_same)
         plan.close()
 
     # the paper's geopotential-only solver on the same workload (FP64 form), for comparison
@@ -424,19 +424,20 @@ def main():
     sm_mhz = (r["clocks"] or {}).get("sm_max_mhz") or 2070.0
     peak = fp64_peak_tflops(sm_mhz)
     achieved = flops / (solve_ms * 1e-3) / 1e12
-    tslots = min(SOLVE_TRAFFIC_T170, key=lambda k: abs(k - r["slots"]))
+    tkey = min(SOLVE_TRAFFIC_T170, key=lambda k: (k[1] != r["shape"], abs(k[0] - r["slots"])))
     line = {
         "metric": METRIC, "value": world * 1e3 / r["ms"], "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if chosen == "fp64" else "f64 solves + 3xtf32 legendre",
-        "data": "synthetic", "config": {**workload_config(), "form": chosen, "pole_slots": r["slots"]},
+        "data": "synthetic", "config": {**workload_config(), "form": chosen, "pole_slots": r["slots"], "layout_shape": r["shape"]},
         "roofline": {"bound": "alu", "kernel": "solve_kernel (FP64 banded solves + pole sum)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": SOLVE_TRAFFIC_T170[tslots] * rows_of(W["N"]) / rows_of(170),
-                     "traffic_source": "ncu dram bytes at T170/K256/B16 with %d pole slots (the captured "
-                                       "layout nearest the bench's %d), scaled by rows to T341" % (tslots, r["slots"]),
-                     "dram_gbs": SOLVE_TRAFFIC_T170[tslots] * rows_of(W["N"]) / rows_of(170) / (solve_ms * 1e-3) / 1e9,
+                     "traffic": SOLVE_TRAFFIC_T170[tkey] * rows_of(W["N"]) / rows_of(170),
+                     "traffic_source": "ncu dram bytes at T170/K256/B16 with %d pole slots, layout shape %d "
+                                       "(the captured layout nearest the bench's %d, shape %d), scaled by rows "
+                                       "to T341" % (tkey[0], tkey[1], r["slots"], r["shape"]),
+                     "dram_gbs": SOLVE_TRAFFIC_T170[tkey] * rows_of(W["N"]) / rows_of(170) / (solve_ms * 1e-3) / 1e9,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz",
                      "flops_per_launch": flops, "launch_ms": solve_ms},
         "stage_ms": r["stages"],
@@ -451,7 +452,7 @@ def main():
         f = results["fp64"]
         d = (results[chosen]["y"] - f["y"]).norm() / f["y"].norm()
         line["fp64_form"] = {"value": world * 1e3 / f["ms"], "ms_per_step": f["ms"], "stage_ms": f["stages"],
-                             "pole_slots": f["slots"],
+                             "pole_slots": f["slots"], "layout_shape": f["shape"],
                              "kernels": kernel_rooflines("fp64", f["stages"], f["slots"], sm_mhz)}
         line["error_vs_fp64_form"] = float(d)
     if phi is not None:

@@ -104,3 +104,23 @@ def test_phi_unsupported_calls():
     plan.close()
     with pytest.raises(rexi.RexiError):
         rexi.Plan(15, 16, 32, M=8, layout="spectral", solver="phi", fsphere=True)
+
+
+def test_phi_long_step_matches_oracle():
+    """A 1.5-day step at T128 (tau omega up to ~820, the Gaussian-bump setting) with a
+    spread of the M = 4116 poles, from the smallest |alpha| to the largest: the
+    pentadiagonal LU without pivoting against the oracle's pivoted dense solves."""
+    import torch
+    from paper_1812_03431_gb300 import rexi
+    N, tau = 128, 129600.0
+    al, be, _ = rc.rexi_coefficients(4116, 0.2)
+    pick = np.unique(np.concatenate([np.arange(0, al.size, 400), np.argsort(np.abs(al))[:8]]))
+    al, be = al[pick], be[pick]
+    S = inputs.random_spectral(N, 2, 77)
+    plan = rexi.Plan(N, 192, 384, tau=tau, max_batch=2, layout="spectral", alpha=al, beta=be, solver="phi")
+    got = plan.step(torch.from_numpy(S).cuda()).cpu().numpy()
+    plan.close()
+    ms = [0, 1, 64, 127, 128]
+    ref = phi_solver.rexi_step_phi(S, N, 134, al, be, tau, C, ms=ms, recover="spectral")
+    sel = np.concatenate([np.arange(idx(m, m, N), idx(m, N, N) + 1) for m in ms])
+    assert fieldwise(got[..., sel], ref[..., sel]) < TOL
