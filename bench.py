@@ -440,6 +440,7 @@ def main():
                      "dram_gbs": SOLVE_TRAFFIC_T170[tkey] * rows_of(W["N"]) / rows_of(170) / (solve_ms * 1e-3) / 1e9,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz",
                      "flops_per_launch": flops, "launch_ms": solve_ms},
+        "state_steps_per_s": world * B * 1e3 / r["ms"],
         "stage_ms": r["stages"],
         "kernels": kernel_rooflines(chosen, r["stages"], r["slots"], sm_mhz),
         "e2e": {"value": world * 1e3 / r["ms_e2e"], "unit": "steps/s", "h2d_bytes_per_step": r["bytes"],
