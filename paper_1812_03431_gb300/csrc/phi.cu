@@ -72,7 +72,7 @@ struct PhiSetupArgs {
   const double *coef;  // [nspec][4] sigma, ct, dt, G
   const double *zc;    // [nspec][12] Z2(-2, 0, +2), Z3(-4 .. +4), Z6(-2, 0, +2)
   const double2 *alpha, *beta;
-  double2 *fac;        // [G_NCOMP][nrows][P]
+  double2 *fac;        // [7][nrows][P]: l1, l2, u1, u2, 1/u0, zeta weights zp, zm
   const int4 *sys;     // per (m, p): {m, n0, len, row0}
   int nsys, P, N;
   int64_t nrows;

@@ -40,3 +40,21 @@ def test_two_replicas_take_the_max_time():
         assert out[0] == out[1] == 40.0
         # whole-job value: units of all ranks over the slowest rank's time
         assert 2 * 1e3 / out[0] == pytest.approx(50.0)
+
+
+def test_kernel_rooflines_arithmetic():
+    import bench
+    st = {"fft_fwd": 0.2, "leg_ana": 0.15, "solve": 30.0, "reduce": 0.4, "leg_syn": 0.3, "fft_inv": 0.2}
+    for form in ("mixed", "fp64"):
+        k = bench.kernel_rooflines(form, st, 32, 2070.0)
+        assert set(k) == set(st)
+        for name, v in k.items():
+            scale = 1e9 if v["unit"] == "GB/s" else 1e12
+            assert abs(v["achieved"] - v["algorithmic"] / (v["ms"] * 1e-3) / scale) < 1e-9 * v["achieved"]
+            assert abs(v["frac"] - v["achieved"] / v["peak"]) < 1e-12
+        # the solve: 72 flops per (state, pole, row) at the derived FP64 rate
+        W = bench.WORK
+        P = 2 * (W["M"] + 11) + 1
+        assert k["solve"]["algorithmic"] == 72 * W["batch"] * P * bench.rows_of(W["N"])
+        assert abs(k["solve"]["peak"] - 152 * 4 * 2070e6 / 1e12) < 1e-12
+    assert bench.rows_of(341) == 58652
