@@ -495,7 +495,12 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
     const int g = 1 << (cand >> 1), shape = cand & 1;
     SolveLayout L;
     rexi_status r = build_layout(pl, B, false, g, L, shape);
-    if (r != REXI_OK) return r;
+    if (r != REXI_OK) {
+      if (bestL.items_dev) cudaFree(bestL.items_dev);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return r;
+    }
     if (std::find(tried.begin(), tried.end(), 2 * L.slots + shape) != tried.end()) {
       cudaFree(L.items_dev);
       continue;
