@@ -173,6 +173,9 @@ def test_invalid_calls(torch, rexi):
     assert st == rexi.REXI_EINVAL  # in == out
     with pytest.raises(rexi.RexiError):
         plan.solve_pole(plan.info()["P"], S)
+    out = torch.empty_like(S)
+    assert rexi.load().rexi_step(plan._h, S.data_ptr(), out.data_ptr(), 0, None) == rexi.REXI_EINVAL  # empty batch
+    assert rexi.load().rexi_step(plan._h, S.data_ptr() + 8, out.data_ptr(), 1, None) == rexi.REXI_EINVAL  # misaligned
 
 
 def test_full_size_sampled_orders(torch, rexi):
@@ -207,6 +210,7 @@ def test_full_size_grid_step_bench_launch(torch, rexi, full_size_case, precision
     c = full_size_case
     plan = rexi.Plan(c["N"], c["nlat"], c["nlon"], tau=c["tau"], max_batch=c["B"], alpha=c["al"], beta=c["be"],
                      precision=precision)
+    plan.tune(c["B"])  # the layout the bench times
     got = plan.step(torch.from_numpy(c["x"]).cuda()).cpu().numpy()
     plan.close()
     assert fieldwise(got[:1], c["ref"], axis_f=-3) < tol

@@ -55,6 +55,22 @@ def test_phi_grid_step_matches_oracle():
     assert fieldwise(got, ref, axis_f=-3) < TOL
 
 
+def test_phi_grid_step_mixed_precision():
+    # the Phi-only solve behind the mixed form's tcgen05 Legendre transforms
+    import torch
+    from paper_1812_03431_gb300 import rexi
+    N, nlat, nlon, M, B, tau = 63, 96, 192, 64, 3, 3600.0
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    gs = ostep.GridStep(N, nlat, nlon, al, be, tau, C)
+    x = gs.synthesise(inputs.random_spectral(N, B, 19))
+    plan = rexi.Plan(N, nlat, nlon, tau=tau, max_batch=B, alpha=al, beta=be, solver="phi", precision="mixed")
+    got = plan.step(torch.from_numpy(x).cuda()).cpu().numpy()
+    plan.check_device()
+    plan.close()
+    ref = gs.synthesise(phi_solver.rexi_step_phi(gs.analyse(x), N, nlat, al, be, tau, C, recover="spectral"))
+    assert fieldwise(got, ref, axis_f=-3) < 1e-5
+
+
 def test_phi_and_delta_solvers_agree_in_low_degrees():
     # a state band-limited to n <= 12 at T63: both discretisations have converged in the
     # low degrees, where they agree to rounding; at the truncation edge they do not
