@@ -141,8 +141,10 @@ rexi_status rexi_coefficients(int32_t M, double h, int32_t normalize,
 
 /* Create a plan on the current CUDA device: Gaussian grid, Legendre tables,
  * REXI poles, the per-(pole, m, n) factors of the banded solves for the step
- * and its adjoint, and workspaces for max_batch states.  Allocates device
- * memory; synchronises the device once.  *out is NULL on failure. */
+ * (those of the adjoint are built on the first rexi_step_adjoint call), and
+ * workspaces for max_batch states.  Allocates device memory; synchronises the
+ * device once.  *out is NULL on failure (REXI_ENOMEM when the device memory does
+ * not suffice). */
 rexi_status rexi_plan_create(const rexi_params *params, rexi_plan **out);
 
 /* One T-REXI step (Algorithm 1): out = Re sum_k beta_k (alpha_k + tau L)^{-1} in,
@@ -223,7 +225,8 @@ rexi_status rexi_plan_info(const rexi_plan *plan, int64_t *info, int32_t n);
  * every state of several plans run as ONE persistent launch over the merged
  * work list of (m, pole group, state group, plan) items sorted longest first
  * (Sec. 5: every (pole, m) system is independent).  Plans must use
- * REXI_SPECTRAL; the ragged object keeps pointers to them (destroy it first).
+ * REXI_SPECTRAL, the rotating sphere and REXI_SOLVER_DELTA; the ragged object
+ * keeps pointers to them (destroy it first).
  * rexi_ragged_step: in_dev[s], out_dev[s] are state s's [3][nspec_p] complex128
  * device arrays (p = state_plan[s]); at most max_batch of plan p's states per
  * call, nstates <= max_states.  A call with a new per-plan state count
