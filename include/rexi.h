@@ -161,6 +161,17 @@ rexi_status rexi_step(rexi_plan *plan, const void *in_dev, void *out_dev,
 rexi_status rexi_step_adjoint(rexi_plan *plan, const void *gout_dev, void *gin_dev,
                               int32_t batch, void *stream);
 
+/* nsteps >= 1 consecutive T-REXI steps from in_dev, the result in out_dev (same layouts
+ * as rexi_step): the state stays in spectral space between steps (the grid layout
+ * analyses once at the start and synthesises once at the end), ping-ponging between
+ * the plan's two internal buffers, so a long time integration (Sec. 6.2) costs one
+ * launch sequence per step and no transforms in between.  For spectral plans the
+ * result equals nsteps rexi_step calls bit for bit; for grid plans it differs from
+ * them only by the rounding of the skipped intermediate transforms.  No device memory
+ * is allocated once the batch size has been seen. */
+rexi_status rexi_integrate(rexi_plan *plan, const void *in_dev, void *out_dev, int32_t batch, int32_t nsteps,
+                           void *stream);
+
 /* Allocation-free spectral step (no counterpart in the paper).  Some callers
  * cannot allocate device memory while they step -- for example a time loop
  * inside an application that hands all device memory out at start-up, or code

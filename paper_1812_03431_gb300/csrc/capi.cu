@@ -3,6 +3,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <cstring>
+#include <utility>
 #include <string>
 
 #include "rexi_internal.h"
@@ -45,9 +46,9 @@ struct Marks {
   cudaStream_t st;
   int call = -1;
   bool open = false;
-  Marks(Plan &p, cudaStream_t s) : pl(p), st(s) {
+  Marks(Plan &p, cudaStream_t s, bool timed = true) : pl(p), st(s) {
     nvtxRangePushA("rexi");
-    if (pl.prof && pl.prof_calls < pl.prof_cap) {
+    if (timed && pl.prof && pl.prof_calls < pl.prof_cap) {
       call = pl.prof_calls++;
       pl.prof_n[call] = 0;
     }
@@ -360,6 +361,40 @@ rexi_status rexi_solve_pole(rexi_plan *plan, int32_t k, const void *in_dev, void
   }
   if (e == cudaSuccess) e = launch_transpose_out(pl.s_out, static_cast<double2 *>(out_dev), pl.nspec, B, pl.N, st);
   return e == cudaSuccess ? REXI_OK : cuda_fail("solve_pole", e);
+}
+
+rexi_status rexi_integrate(rexi_plan *plan, const void *in_dev, void *out_dev, int32_t batch, int32_t nsteps,
+                           void *stream) {
+  if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
+  Plan &pl = *plan->pl;
+  if (nsteps < 1) { set_error("rexi_integrate: nsteps must be >= 1"); return REXI_EINVAL; }
+  const bool grid = pl.prm.layout == REXI_GRID;
+  rexi_status r = check_io(pl, in_dev, out_dev, batch, grid);
+  if (r != REXI_OK) return r;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Marks mk(pl, st, false);
+  if (grid) {
+    if ((r = analyze(pl, static_cast<const double *>(in_dev), batch, false, st, mk)) != REXI_OK) return r;
+  } else {
+    mk.mark(ST_TRANS_IN);
+    cudaError_t e = launch_transpose_in(static_cast<const double2 *>(in_dev), pl.s_in, pl.nspec, batch, st);
+    if (e != cudaSuccess) return cuda_fail("transpose", e);
+  }
+  // the spectral state ping-pongs between the plan's two internal buffers: each step
+  // reads s_in and writes s_out, and the pointers swap (kernels take them at launch)
+  double2 *const s_in0 = pl.s_in, *const s_out0 = pl.s_out;
+  for (int k = 0; k < nsteps && r == REXI_OK; ++k) {
+    r = core(pl, batch, false, st, mk);
+    std::swap(pl.s_in, pl.s_out);
+  }
+  double2 *const result = pl.s_in;
+  pl.s_in = s_in0;
+  pl.s_out = s_out0;
+  if (r != REXI_OK) return r;
+  if (grid) return synthesize(pl, result, static_cast<double *>(out_dev), batch, false, st, mk);
+  mk.mark(ST_TRANS_OUT);
+  cudaError_t e = launch_transpose_out(result, static_cast<double2 *>(out_dev), pl.nspec, batch, pl.N, st);
+  return e == cudaSuccess ? REXI_OK : cuda_fail("transpose", e);
 }
 
 rexi_status rexi_step_static(rexi_plan *plan, const void *in_dev, void *out_dev, int32_t batch, void *stream) {

@@ -47,6 +47,7 @@ _DP = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "rexi_params_default": (None, [ctypes.POINTER(rexi_params)]),
     "rexi_params_size": (ctypes.c_size_t, []),
+    "rexi_integrate": (_I32, [_VP, _VP, _VP, _I32, _I32, _VP]),
     "rexi_set_pole_slots": (ctypes.c_int32, [_VP, _I32, _I32, _I32, ctypes.POINTER(_I32)]),
     "rexi_coefficients": (_I32, [_I32, ctypes.c_double, _I32, _DP, _DP, ctypes.POINTER(_I32), _DP]),
     "rexi_plan_create": (_I32, [ctypes.POINTER(rexi_params), ctypes.POINTER(_VP)]),
@@ -195,14 +196,13 @@ class Plan:
                                               _stream_handle(stream)))
         return out
 
-    def integrate(self, x, nsteps, stream=None):
-        """nsteps consecutive steps from x, ping-ponging between two device buffers."""
-        import torch
-        a, b = x.clone(), torch.empty_like(x)
-        for _ in range(nsteps):
-            self.step(a, out=b, stream=stream)
-            a, b = b, a
-        return a
+    def integrate(self, x, nsteps, out=None, stream=None):
+        """rexi_integrate: nsteps consecutive steps from x in one call (the state stays in
+        spectral space in between)."""
+        out = self._io(x, out, self.layout == "grid")
+        _check("rexi_integrate", load().rexi_integrate(self._h, x.data_ptr(), out.data_ptr(), x.shape[0],
+                                                        int(nsteps), _stream_handle(stream)))
+        return out
 
     def step_adjoint(self, g, out=None, stream=None):
         out = self._io(g, out, self.layout == "grid")

@@ -236,3 +236,48 @@ def test_tune_cache_and_set_pole_slots(torch, rexi, tmp_path):
         np.testing.assert_array_equal(ya, plan.step(S).cpu().numpy())
         assert fieldwise(ya, y1) < 1e-13
     plan.close()
+
+
+@pytest.mark.parametrize("M,h", [(128, 0.2), (128, 0.15)])
+def test_stationary_mode_drift_without_renormalisation(torch, rexi, M, h):
+    """Sec. 6.1: the balanced zonal flow is a zero-frequency mode, on which one step
+    multiplies by the REXI response at x = 0, 1 - eps.  Without the renormalisation of
+    the beta, K steps change it by (1 - eps)^K - 1 (the paper's error-growth estimate);
+    with it the state stays put to rounding."""
+    N, K, tau = 63, 4000, 3600.0
+    al, be, eps = rc.rexi_coefficients(M, h, normalize=False)
+    U = inputs.balanced_zonal_flow(N)[None]
+    x = torch.from_numpy(U).cuda()
+    plan = rexi.Plan(N, 96, 192, tau=tau, layout="spectral", alpha=al, beta=be)
+    y = plan.integrate(x, K).cpu().numpy()
+    plan.close()
+    growth = (1.0 - eps) ** K - 1.0
+    assert abs(growth) > 1e-9  # far above the rounding of the steps
+    sel = np.abs(U[0, 0]) > 1e-3 * np.abs(U[0, 0]).max()  # Phi coefficients of the flow
+    ratio = (y[0, 0][sel] - U[0, 0][sel]) / U[0, 0][sel]
+    np.testing.assert_allclose(ratio.real, growth.real, rtol=0.02)
+    al2, be2, _ = rc.rexi_coefficients(M, h)
+    plan = rexi.Plan(N, 96, 192, tau=tau, layout="spectral", alpha=al2, beta=be2)
+    y2 = plan.integrate(x, K).cpu().numpy()
+    plan.close()
+    assert relerr(y2, U) < 1e-3 * abs(growth)
+
+
+def test_integrate_equals_repeated_steps(torch, rexi):
+    N, M, B, K = 31, 32, 3, 7
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    S = torch.from_numpy(spectral_state(N, B, 61)).cuda()
+    plan = rexi.Plan(N, 48, 96, tau=3600.0, max_batch=B, layout="spectral", alpha=al, beta=be)
+    y = S
+    for _ in range(K):
+        y = plan.step(y)
+    np.testing.assert_array_equal(plan.integrate(S, K).cpu().numpy(), y.cpu().numpy())  # bit for bit
+    plan.close()
+    plan = rexi.Plan(N, 48, 96, tau=3600.0, max_batch=B, alpha=al, beta=be)  # grid layout
+    x = plan.synthesize(S)
+    y = x
+    for _ in range(K):
+        y = plan.step(y)
+    got = plan.integrate(x, K).cpu().numpy()
+    assert fieldwise(got, y.cpu().numpy(), axis_f=-3) < 1e-12  # only the skipped transforms' rounding
+    plan.close()

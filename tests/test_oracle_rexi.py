@@ -62,3 +62,12 @@ def test_conjugate_symmetric_poles():
     np.testing.assert_array_equal(al[::-1], np.conj(al))
     np.testing.assert_allclose(be[::-1], np.conj(be), rtol=0, atol=1e-15 * np.abs(be).max())
     assert np.all(al.real < 0)
+
+
+def test_printed_drift_estimate(golden):
+    # Sec. 6.1: with the printed x = 0 residual the stationary modes drift by
+    # (1 - eps)^N - 1; the number of steps to a drift of 1e-6 is "about 60000"
+    eps = golden["eps_x0_M128"]
+    n = np.log(1.0 + 1e-6) / abs(np.log(1.0 - eps))
+    assert abs(n - golden["drift_steps_to_1e-6"]) < 0.1 * golden["drift_steps_to_1e-6"]
+    assert abs(((1.0 - eps) ** n - 1.0) - 1e-6) < 1e-12
