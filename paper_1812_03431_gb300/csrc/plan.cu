@@ -433,8 +433,16 @@ rexi_status build_layout(Plan &pl, int B, bool single, int groups_req, SolveLayo
   }
   L.items_dev = static_cast<WorkItem *>(mem);
   L.slots_m_dev = reinterpret_cast<int32_t *>(static_cast<char *>(mem) + item_bytes);
-  cudaMemcpy(L.items_dev, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
-  cudaMemcpy(L.slots_m_dev, slots_m.data(), slots_m.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(L.items_dev, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(L.slots_m_dev, slots_m.data(), slots_m.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(mem);
+    L.items_dev = nullptr;
+    L.slots_m_dev = nullptr;
+    set_error(std::string("work list: ") + cudaGetErrorString(e));
+    return REXI_ECUDA;
+  }
   return REXI_OK;
 }
 
