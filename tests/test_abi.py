@@ -94,3 +94,14 @@ def test_params_struct_matches_library():
     p = rexi.rexi_params_default()
     # the fields appended last keep their defaults: rotating sphere, delta elimination
     assert (p.fsphere, p.solver, p.max_batch, p.M) == (0, 0, 1, 128)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    # no CPU fallback: without the built library every entry point raises
+    from paper_1812_03431_gb300 import rexi
+    monkeypatch.setattr(rexi, "_lib", None)
+    monkeypatch.setattr(rexi, "LIB_PATH", "/nonexistent/librexi.so")
+    with pytest.raises(RuntimeError, match="librexi.so not found"):
+        rexi.load()
+    with pytest.raises(RuntimeError):
+        rexi.Plan(15, 16, 32, M=4)
