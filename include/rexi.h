@@ -83,6 +83,18 @@ enum { REXI_SOLVER_DELTA = 0, /* per (pole, m, parity): Phi and zeta eliminated,
                                  the result differs from REXI_SOLVER_DELTA at the highest
                                  degrees (it agrees in the interior of a band-limited state). */
 
+enum { REXI_SOLVE_FP64 = 0,    /* banded solves and pole sum in binary64 (default) */
+       REXI_SOLVE_FP32X2 = 1 }; /* the same solves and pole sum in float-float arithmetic: every
+                                  value is an unevaluated pair hi + lo of binary32 numbers
+                                  (48-bit significand, unit roundoff ~3.6e-15; Dekker's
+                                  double-length arithmetic with error-free sums and FMA
+                                  products), run on the FP32 pipes.  The factors are built in
+                                  binary64 and stored as pairs; inputs and outputs stay
+                                  binary64.  Values must lie in binary32's range: magnitudes
+                                  above ~3e38 overflow and below ~1e-31 lose relative precision
+                                  (the SWE states and factors of Sec. 6 are within 1e-20 .. 1e6).
+                                  REXI_SOLVER_DELTA on the rotating sphere only. */
+
 typedef struct rexi_plan rexi_plan;
 typedef struct rexi_ragged rexi_ragged;
 
@@ -119,6 +131,9 @@ typedef struct {
                            rexi_analyze / rexi_synthesize and rexi_tune only:
                            rexi_step_adjoint, rexi_step_static, rexi_solve_pole and
                            rexi_ragged_create return REXI_EINVAL for such plans. */
+  int32_t solve_arith;  /* REXI_SOLVE_FP64 | REXI_SOLVE_FP32X2: arithmetic of the banded solves
+                           and the beta-weighted pole sum (the transforms follow `precision`).
+                           rexi_ragged_create needs the same value on every plan. */
 } rexi_params;
 
 /* Fill *p with the defaults above (ntrunc = 63, nlat = 96, nlon = 192, M = 128,

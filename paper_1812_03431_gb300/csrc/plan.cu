@@ -102,6 +102,7 @@ void free_plan(Plan *pl);
 
 rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   pl->prm = prm;
+  pl->ff = prm.solve_arith == REXI_SOLVE_FP32X2;
   const int N = prm.ntrunc;
   pl->N = N;
   pl->nlat = prm.nlat;
@@ -345,6 +346,7 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   if ((e = dalloc(&pl->four, (size_t)pl->nlat * (N + 1) * 3 * B, &bytes))) return fail("fourier", e);
   if ((e = dalloc(&pl->s_in, (size_t)3 * NS * B, &bytes))) return fail("spectral", e);
   if ((e = dalloc(&pl->s_out, (size_t)3 * NS * B, &bytes))) return fail("spectral", e);
+  if (pl->ff && (e = dalloc(&pl->s_ff, (size_t)3 * NS * B, &bytes))) return fail("spectral", e);
   // partial sums: at most 1024 slots and ~4 GiB (small batches need many slots to spread
   // the poles over enough warps; the reduction reads every slot once per step)
   size_t per_slot = (size_t)3 * NS * B * sizeof(double2);
@@ -560,7 +562,7 @@ void free_plan(Plan *pl) {
                   pl->tabP_hi, pl->tabP_lo, pl->tabH_hi, pl->tabH_lo, pl->scale_ana_in,
                   pl->scale_syn_out, pl->mscale_fwd, pl->mscale_c, pl->mscale_adj, pl->mscale_one,
                   pl->zd_syn, pl->zd_ana_adj, pl->zd_one, pl->zd_mone, pl->fft.tw_dev, pl->fft.tw32_dev, pl->four,
-                  pl->s_in, pl->s_out, pl->partial, pl->yscratch, pl->counter, pl->tc_tab_ana,
+                  pl->s_in, pl->s_out, pl->s_ff, pl->partial, pl->yscratch, pl->counter, pl->tc_tab_ana,
                   pl->tc_tab_syn, pl->tc_work_ana, pl->tc_work_syn, pl->dev_err, pl->phi_zc, pl->phi_q};
   for (cudaEvent_t ev : pl->prof_ev) cudaEventDestroy(ev);
   for (void *p : ptrs)

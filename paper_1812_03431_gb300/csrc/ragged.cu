@@ -76,6 +76,11 @@ rexi_status rexi_ragged_create(rexi_plan *const *plans, int32_t nplans, int32_t 
                 "REXI_SOLVER_DELTA");
       return REXI_EINVAL;
     }
+    if (plans[i]->pl->ff != plans[0]->pl->ff) {
+      delete rg;
+      set_error("rexi_ragged_create: every plan must use the same solve_arith");
+      return REXI_EINVAL;
+    }
     rg->plans.push_back(plans[i]->pl);
     rg->lmax = std::max(rg->lmax, plans[i]->pl->lmax);
     rg->resident_warps = std::max(rg->resident_warps, plans[i]->pl->resident_warps);
@@ -128,7 +133,7 @@ rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *c
       if (counts[p] == 0) continue;
       Plan &pl = *rg->plans[p];
       const SolveLayout &L = *lays[p];
-      views[p] = make_view(pl, L, false, pl.s_in, pl.partial, counts[p], 0, pl.P);
+      views[p] = make_view(pl, L, false, pl.ff ? pl.s_ff : pl.s_in, pl.partial, counts[p], 0, pl.P);
       const int nb = (counts[p] + L.bw - 1) / L.bw;
       for (int m = 0; m <= pl.N; ++m) {
         const int l = std::max(pl.sys[2 * m].len, pl.sys[2 * m + 1].len);
@@ -160,9 +165,15 @@ rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *c
         static_cast<const double2 *>(in_dev[s]), pl.s_in, n3, counts[state_plan[s]], rank[s]);
     e = cudaGetLastError();
   }
+  const bool ff = rg->plans[0]->ff;
+  for (int p = 0; p < np && e == cudaSuccess; ++p)  // float-float solves read split states
+    if (ff && counts[p] > 0) {
+      Plan &pl = *rg->plans[p];
+      e = launch_split_state(pl, pl.s_in, pl.s_ff, 3 * pl.nspec * counts[p], st);
+    }
   if (e == cudaSuccess)
     e = launch_solve_ragged(cfg.views_dev, cfg.items_dev, cfg.nitems, rg->ybuf, rg->lmax, rg->counter,
-                            rg->resident_warps, st);
+                            rg->resident_warps, ff, st);
   for (int p = 0; p < np && e == cudaSuccess; ++p)
     if (counts[p] > 0)
       e = launch_reduce(*rg->plans[p], *lays[p], false, rg->plans[p]->s_in, rg->plans[p]->s_out, counts[p], false, 0, st);

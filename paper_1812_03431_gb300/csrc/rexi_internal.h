@@ -158,6 +158,11 @@ struct Plan {
   double2 *phi_q = nullptr;
   double2 sumb{};
 
+  // float-float solves (REXI_SOLVE_FP32X2): the factors hold float-float values in place
+  // of binary64 ones, and s_ff [3][nspec][B] the step's input states split the same way
+  bool ff = false;
+  double2 *s_ff = nullptr;
+
   // workspaces (max_batch)
   double2 *four = nullptr;     // [nlat][N+1][3 B] complex (FP64 or FP32 pairs in mixed mode)
   double2 *s_in = nullptr;     // [3][nspec][B]
@@ -209,7 +214,11 @@ struct SolveView {
 SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, double2 *part, int B,
                     int pole_begin, int pole_end);
 cudaError_t launch_solve_ragged(const SolveView *views_dev, const WorkItem *items, int nitems, double2 *ybuf,
-                                int lmax, unsigned *counter, int resident_warps, cudaStream_t st);
+                                int lmax, unsigned *counter, int resident_warps, bool ff, cudaStream_t st);
+// float-float solves: convert n complex values in place (factors), or split n binary64
+// states into out (float-float values in double2 slots)
+cudaError_t launch_to_ff(Plan &pl, double2 *v, int64_t n, cudaStream_t st);
+cudaError_t launch_split_state(Plan &pl, const double2 *in, double2 *out, int64_t n, cudaStream_t st);
 cudaError_t launch_reduce(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin,
                           double2 *sout, int B, bool single_pole, int pole, cudaStream_t st);
 cudaError_t launch_transpose_in(const double2 *user, double2 *sint, int64_t nspec, int B,

@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <string>
 
+#include "ff.h"
 #include "rexi_internal.h"
 
 namespace rexi {
@@ -283,9 +284,110 @@ __device__ __forceinline__ void sweep_poles(const SolveView &a, const int (&k)[K
   }
 }
 
+// The same sweeps in float-float arithmetic (ff.h): factors, states, the sweep
+// intermediates and the slot partials are complex float-float values (float4) in the
+// buffers' double2 slots, and every FP64 FMA of the sweep above becomes an
+// error-compensated FP32 product and sum.  On GB300 the FP64 unit issues 1/64 of the
+// FP32 rate, so the solve runs on the FP32 pipes at 48-bit significand precision.
+__device__ __forceinline__ float4 ldf(const float4 *p) { return __ldg(p); }
+
+template <int KC>
+__device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k)[KC], int n0, int len, int nmin,
+                                               int64_t row0, int64_t base_idx, const float4 *sPhi,
+                                               const float4 *sZeta, const float4 *sDel, float4 *pPhi,
+                                               float4 *pZeta, float4 *pDel, int64_t rstride, bool first,
+                                               float4 *ybuf) {
+  const int64_t NR = a.nrows, P = a.P;
+  const int N = a.N, B = a.B;
+  const float4 *fac = reinterpret_cast<const float4 *>(a.fac);
+  const float4 *fL[KC], *fG[KC], *fE[KC], *fF[KC];
+  for (int c = 0; c < KC; ++c) {
+    fL[c] = fac + ((int64_t)F_L * NR + row0) * P + k[c];
+    fG[c] = fac + ((int64_t)F_G * NR + row0) * P + k[c];
+    fE[c] = fac + ((int64_t)F_E * NR + row0) * P + k[c];
+    fF[c] = fac + ((int64_t)F_F * NR + row0) * P + k[c];
+  }
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  // ---- forward sweep: y_i = delta0 - g Phi0 - e zeta0_{n-1} - f zeta0_{n+1} - l y_{i-1}
+  float4 yprev[KC];
+  for (int c = 0; c < KC; ++c) yprev[c] = zero;
+  float4 zprev = (n0 - 1 >= nmin) ? ldf(sZeta + (base_idx + n0 - 1) * B) : zero;
+  for (int i = 0; i < len; ++i) {
+    const int n = n0 + 2 * i;
+    const int64_t ix = base_idx + n;
+    const float4 zn = (n + 1 <= N) ? ldf(sZeta + (ix + 1) * B) : zero;
+    const float4 d0 = ldf(sDel + ix * B), p0 = ldf(sPhi + ix * B);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      ff::CAcc y = ff::cacc(d0);
+      ff::cmsub(y, ldf(fG[c] + (int64_t)i * P), p0);
+      ff::cmsub(y, ldf(fE[c] + (int64_t)i * P), zprev);
+      ff::cmsub(y, ldf(fF[c] + (int64_t)i * P), zn);
+      ff::cmsub(y, ldf(fL[c] + (int64_t)i * P), yprev[c]);
+      const float4 yv = ff::norm(y);
+      ybuf[((int64_t)i * KC + c) * 32] = yv;
+      yprev[c] = yv;
+    }
+    zprev = zn;
+  }
+  // ---- backward sweep with the beta-weighted accumulation (as in sweep_poles)
+  const float4 *fC[KC], *fBD[KC], *fBAD[KC], *fZP[KC], *fZM[KC];
+  for (int c = 0; c < KC; ++c) {
+    fC[c] = fac + ((int64_t)F_C * NR + row0) * P + k[c];
+    fBD[c] = fac + ((int64_t)F_BD * NR + row0) * P + k[c];
+    fBAD[c] = fac + ((int64_t)F_BAD * NR + row0) * P + k[c];
+    fZP[c] = fac + ((int64_t)F_ZP * NR + row0) * P + k[c];
+    fZM[c] = fac + ((int64_t)F_ZM * NR + row0) * P + k[c];
+  }
+  float4 wnext[KC], zmnext[KC];
+  for (int c = 0; c < KC; ++c) wnext[c] = zmnext[c] = zero;
+  for (int i = len - 1; i >= 0; --i) {
+    const int n = n0 + 2 * i;
+    const int64_t ix = base_idx + n;
+    float4 wv[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      ff::CAcc w = ff::cacc(ybuf[((int64_t)i * KC + c) * 32]);
+      ff::cmsub(w, ldf(fC[c] + (int64_t)i * P), wnext[c]);
+      wv[c] = ff::norm(w);
+    }
+    ff::CAcc accD = first ? ff::czero() : ff::cacc(pDel[ix * rstride]);
+    ff::CAcc accP = first ? ff::czero() : ff::cacc(pPhi[ix * rstride]);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      ff::cmac(accD, ldf(fBD[c] + (int64_t)i * P), wv[c]);
+      ff::cmac(accP, ldf(fBAD[c] + (int64_t)i * P), wv[c]);
+    }
+    pDel[ix * rstride] = ff::norm(accD);
+    pPhi[ix * rstride] = ff::norm(accP);
+    if (n + 1 <= N) {
+      ff::CAcc accZ = first ? ff::czero() : ff::cacc(pZeta[(ix + 1) * rstride]);
+#pragma unroll
+      for (int c = 0; c < KC; ++c) {
+        ff::cmac(accZ, ldf(fZP[c] + (int64_t)i * P), wv[c]);
+        ff::cmac(accZ, zmnext[c], wnext[c]);
+      }
+      pZeta[(ix + 1) * rstride] = ff::norm(accZ);
+    }
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      zmnext[c] = ldf(fZM[c] + (int64_t)i * P);
+      wnext[c] = wv[c];
+    }
+  }
+  if (n0 - 1 >= nmin) {
+    const int64_t ix = base_idx + n0 - 1;
+    ff::CAcc accZ = first ? ff::czero() : ff::cacc(pZeta[ix * rstride]);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) ff::cmac(accZ, zmnext[c], wnext[c]);
+    pZeta[ix * rstride] = ff::norm(accZ);
+  }
+}
+
 // Forward/backward sweeps of one work item (m, pole group g, states from b0) for this
 // lane = (state b, parity p, slot kk): its poles k = slot, slot + S, ... two at a time,
 // accumulated into its slot's partials in ascending k.
+template <bool FF>
 __device__ __forceinline__ void solve_item(const SolveView &a, int wm, int wg, int wb0, int lane,
                                            double2 *ybuf) {
   const int bl = lane % a.bw;
@@ -311,22 +413,41 @@ __device__ __forceinline__ void solve_item(const SolveView &a, int wm, int wg, i
   const int64_t rstride = (int64_t)S * B;  // partial stride per idx
   bool first = true;
   int k0 = a.pole_begin + slot;
-  for (; k0 + Sm < a.pole_end; k0 += 2 * Sm) {
-    const int kp[2] = {k0, k0 + Sm};
-    sweep_poles<2>(a, kp, n0, len, nmin, row0, base_idx, sPhi, sZeta, sDel, pPhi, pZeta, pDel, rstride, first,
-                   ybuf);
-    first = false;
-  }
-  if (k0 < a.pole_end) {
-    const int kp[1] = {k0};
-    sweep_poles<1>(a, kp, n0, len, nmin, row0, base_idx, sPhi, sZeta, sDel, pPhi, pZeta, pDel, rstride, first,
-                   ybuf);
+  if constexpr (FF) {
+    const float4 *fPhi = reinterpret_cast<const float4 *>(sPhi), *fZeta = reinterpret_cast<const float4 *>(sZeta),
+                 *fDel = reinterpret_cast<const float4 *>(sDel);
+    float4 *qPhi = reinterpret_cast<float4 *>(pPhi), *qZeta = reinterpret_cast<float4 *>(pZeta),
+           *qDel = reinterpret_cast<float4 *>(pDel), *fy = reinterpret_cast<float4 *>(ybuf);
+    for (; k0 + Sm < a.pole_end; k0 += 2 * Sm) {
+      const int kp[2] = {k0, k0 + Sm};
+      sweep_poles_ff<2>(a, kp, n0, len, nmin, row0, base_idx, fPhi, fZeta, fDel, qPhi, qZeta, qDel, rstride, first,
+                        fy);
+      first = false;
+    }
+    if (k0 < a.pole_end) {
+      const int kp[1] = {k0};
+      sweep_poles_ff<1>(a, kp, n0, len, nmin, row0, base_idx, fPhi, fZeta, fDel, qPhi, qZeta, qDel, rstride, first,
+                        fy);
+    }
+  } else {
+    for (; k0 + Sm < a.pole_end; k0 += 2 * Sm) {
+      const int kp[2] = {k0, k0 + Sm};
+      sweep_poles<2>(a, kp, n0, len, nmin, row0, base_idx, sPhi, sZeta, sDel, pPhi, pZeta, pDel, rstride, first,
+                     ybuf);
+      first = false;
+    }
+    if (k0 < a.pole_end) {
+      const int kp[1] = {k0};
+      sweep_poles<1>(a, kp, n0, len, nmin, row0, base_idx, sPhi, sZeta, sDel, pPhi, pZeta, pDel, rstride, first,
+                     ybuf);
+    }
   }
 }
 
 // Persistent kernel: each warp takes (m, pole group, first state) items from an
 // atomic counter (items are sorted longest first) and runs one tridiagonal
 // forward/backward sweep per (lane, pole).
+template <bool FF>
 __global__ void __launch_bounds__(128) solve_kernel(SolveArgs a) {
   const int lane = threadIdx.x & 31;
   const int wslot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -337,7 +458,7 @@ __global__ void __launch_bounds__(128) solve_kernel(SolveArgs a) {
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= (unsigned)a.nitems) break;
     const WorkItem w = a.items[it];
-    solve_item(a.v, w.m, w.g, w.b0, lane, ybuf);
+    solve_item<FF>(a.v, w.m, w.g, w.b0, lane, ybuf);
   }
 }
 
@@ -351,6 +472,7 @@ struct RaggedArgs {
   int nitems, lmax;
 };
 
+template <bool FF>
 __global__ void __launch_bounds__(128) solve_ragged_kernel(RaggedArgs a) {
   const int lane = threadIdx.x & 31;
   const int wslot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -362,7 +484,7 @@ __global__ void __launch_bounds__(128) solve_ragged_kernel(RaggedArgs a) {
     if (it >= (unsigned)a.nitems) break;
     const WorkItem w = a.items[it];
     const SolveView v = a.views[w.len];
-    solve_item(v, w.m, w.g, w.b0, lane, ybuf);
+    solve_item<FF>(v, w.m, w.g, w.b0, lane, ybuf);
   }
 }
 
@@ -403,8 +525,15 @@ __device__ __forceinline__ double2 reduce_finish(const ReduceArgs &a, int64_t t,
   return acc;
 }
 
+// Slot sums of float-float partials (solve_kernel<true>): added in slot order as
+// float-float values, rounded once to binary64 (hi and lo converted on the integer pipe).
+__device__ __forceinline__ double2 ff_result(const ff::CAcc &fa) {
+  return make_double2(f32_to_f64(fa.re.s) + f32_to_f64(fa.re.e), f32_to_f64(fa.im.s) + f32_to_f64(fa.im.e));
+}
+
 // out[f][idx][b] = sum over slots (in order) + the pole-independent terms; one thread
 // per output.
+template <bool FF>
 __global__ void reduce_kernel(ReduceArgs a) {
   const int64_t total = 3 * a.nspec * a.B;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -418,17 +547,32 @@ __global__ void reduce_kernel(ReduceArgs a) {
     if (!(fl & 2)) {
       if (fl & 1) {
         // loads issued eight at a time, added strictly in slot order (bit-reproducible)
-        const double2 *p = a.part + fi * a.slots * a.B + b;
         const int Sm = a.slots_m ? a.slots_m[a.m_of[ix]] : a.slots;
-        int s = 0;
-        for (; s + 8 <= Sm; s += 8) {
-          double2 v[8];
+        if constexpr (FF) {
+          const float4 *p = reinterpret_cast<const float4 *>(a.part) + fi * a.slots * a.B + b;
+          ff::CAcc fa = ff::czero();
+          int s = 0;
+          for (; s + 8 <= Sm; s += 8) {
+            float4 v[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + (int64_t)(s + u) * a.B);
+            for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + (int64_t)(s + u) * a.B);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) acc = cadd(acc, v[u]);
+            for (int u = 0; u < 8; ++u) ff::cadd(fa, v[u]);
+          }
+          for (; s < Sm; ++s) ff::cadd(fa, p[(int64_t)s * a.B]);
+          acc = ff_result(fa);
+        } else {
+          const double2 *p = a.part + fi * a.slots * a.B + b;
+          int s = 0;
+          for (; s + 8 <= Sm; s += 8) {
+            double2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + (int64_t)(s + u) * a.B);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc = cadd(acc, v[u]);
+          }
+          for (; s < Sm; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
         }
-        for (; s < Sm; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
       }
       acc = reduce_finish(a, t, f, ix, acc);
     }
@@ -438,6 +582,7 @@ __global__ void reduce_kernel(ReduceArgs a) {
 
 // The same with one warp per output for many slots (small batches): lane l sums slots
 // l, l + 32, ... in order, then a fixed butterfly adds the lanes (bit-reproducible).
+template <bool FF>
 __global__ void reduce_wide_kernel(ReduceArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t total = 3 * a.nspec * a.B;
@@ -451,13 +596,27 @@ __global__ void reduce_wide_kernel(ReduceArgs a) {
     double2 acc = make_double2(0, 0);
     if (!(fl & 2)) {
       if (fl & 1) {
-        const double2 *p = a.part + fi * a.slots * a.B + b;
         const int Sm = a.slots_m ? a.slots_m[a.m_of[ix]] : a.slots;
-        for (int s = lane; s < Sm; s += 32) acc = cadd(acc, __ldcs(p + (int64_t)s * a.B));
+        if constexpr (FF) {
+          const float4 *p = reinterpret_cast<const float4 *>(a.part) + fi * a.slots * a.B + b;
+          ff::CAcc fa = ff::czero();
+          for (int s = lane; s < Sm; s += 32) ff::cadd(fa, __ldcs(p + (int64_t)s * a.B));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+          for (int o = 16; o > 0; o >>= 1) {
+            const float rs = __shfl_xor_sync(0xffffffffu, fa.re.s, o), re = __shfl_xor_sync(0xffffffffu, fa.re.e, o);
+            const float is = __shfl_xor_sync(0xffffffffu, fa.im.s, o), ie = __shfl_xor_sync(0xffffffffu, fa.im.e, o);
+            ff::add(fa.re, rs, re);
+            ff::add(fa.im, is, ie);
+          }
+          acc = ff_result(fa);
+        } else {
+          const double2 *p = a.part + fi * a.slots * a.B + b;
+          for (int s = lane; s < Sm; s += 32) acc = cadd(acc, __ldcs(p + (int64_t)s * a.B));
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+          }
         }
       }
       if (lane == 0) acc = reduce_finish(a, t, f, ix, acc);
@@ -527,6 +686,18 @@ __global__ void fsphere_kernel(FsphereArgs a) {
   }
 }
 
+// In-place binary64 -> float-float conversion of complex values (factors, once per plan).
+__global__ void to_ff_kernel(double2 *v, int64_t n) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    reinterpret_cast<float4 *>(v)[t] = ff::csplit(v[t]);
+}
+
+// States for a float-float solve: in (binary64) -> out (float-float), once per step.
+__global__ void split_state_kernel(const double2 *in, float4 *out, int64_t n) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = ff::csplit(in[t]);
+}
+
 // [rows][cols] -> [cols][rows] of double2 via 32x32 shared tiles (tiles indexed
 // linearly in blockIdx.x, so neither dimension is limited by gridDim.y).
 __global__ void transpose_kernel(const double2 *in, double2 *out, int64_t rows, int64_t cols) {
@@ -589,6 +760,20 @@ cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st) {
   a.adjoint = adjoint ? 1 : 0;
   int64_t total = (int64_t)a.P * a.nsys;
   factor_setup_kernel<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && pl.ff) e = launch_to_ff(pl, a.fac, (int64_t)F_NCOMP * pl.nrows * pl.P, st);
+  return e;
+}
+
+cudaError_t launch_to_ff(Plan &pl, double2 *v, int64_t n, cudaStream_t st) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)pl.num_sms * 16));
+  to_ff_kernel<<<blocks, 256, 0, st>>>(v, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_state(Plan &pl, const double2 *in, double2 *out, int64_t n, cudaStream_t st) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)pl.num_sms * 16));
+  split_state_kernel<<<blocks, 256, 0, st>>>(in, reinterpret_cast<float4 *>(out), n);
   return cudaGetLastError();
 }
 
@@ -615,6 +800,12 @@ SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double
 
 cudaError_t launch_solve(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, int B,
                          int pole_begin, int pole_end, bool, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (pl.ff) {  // the solve reads the states as float-float values
+    e = launch_split_state(pl, sin, pl.s_ff, 3 * pl.nspec * B, st);
+    if (e != cudaSuccess) return e;
+    sin = pl.s_ff;
+  }
   SolveArgs a;
   a.v = make_view(pl, lay, adjoint, sin, pl.partial, B, pole_begin, pole_end);
   a.ybuf = pl.yscratch;
@@ -622,18 +813,20 @@ cudaError_t launch_solve(Plan &pl, const SolveLayout &lay, bool adjoint, const d
   a.counter = pl.counter;
   a.nitems = lay.nitems;
   a.lmax = pl.lmax;
-  cudaError_t e = cudaMemsetAsync(pl.counter, 0, sizeof(unsigned), st);
+  e = cudaMemsetAsync(pl.counter, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  solve_kernel<<<pl.resident_warps / 4, 128, 0, st>>>(a);
+  if (pl.ff) solve_kernel<true><<<pl.resident_warps / 4, 128, 0, st>>>(a);
+  else solve_kernel<false><<<pl.resident_warps / 4, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_solve_ragged(const SolveView *views_dev, const WorkItem *items, int nitems, double2 *ybuf,
-                                int lmax, unsigned *counter, int resident_warps, cudaStream_t st) {
+                                int lmax, unsigned *counter, int resident_warps, bool ff, cudaStream_t st) {
   RaggedArgs a{views_dev, items, ybuf, counter, nitems, lmax};
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  solve_ragged_kernel<<<resident_warps / 4, 128, 0, st>>>(a);
+  if (ff) solve_ragged_kernel<true><<<resident_warps / 4, 128, 0, st>>>(a);
+  else solve_ragged_kernel<false><<<resident_warps / 4, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -663,10 +856,12 @@ cudaError_t launch_reduce(Plan &pl, const SolveLayout &lay, bool adjoint, const 
   // a warp per output when one thread per output would leave most of the GPU idle
   if (a.slots >= 128 && total < (int64_t)pl.num_sms * 512) {
     int blocks = (int)std::min<int64_t>((total + 7) / 8, (int64_t)pl.num_sms * 8);
-    reduce_wide_kernel<<<blocks, 256, 0, st>>>(a);
+    if (pl.ff) reduce_wide_kernel<true><<<blocks, 256, 0, st>>>(a);
+    else reduce_wide_kernel<false><<<blocks, 256, 0, st>>>(a);
   } else {
     int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)pl.num_sms * 8);
-    reduce_kernel<<<blocks, 256, 0, st>>>(a);
+    if (pl.ff) reduce_kernel<true><<<blocks, 256, 0, st>>>(a);
+    else reduce_kernel<false><<<blocks, 256, 0, st>>>(a);
   }
   return cudaGetLastError();
 }
@@ -737,7 +932,8 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
   const size_t part_b = align256((size_t)3 * pl.nspec * slots * B * sizeof(double2));
   const size_t y_b = align256((size_t)warps * pl.lmax * 2 * 32 * sizeof(double2));
   const size_t item_b = align256((size_t)nitems * sizeof(WorkItem));
-  const size_t need = 2 * state_b + part_b + y_b + item_b + 256;
+  const size_t ffstate_b = pl.ff ? state_b : 0;  // float-float copy of the input states
+  const size_t need = 2 * state_b + part_b + y_b + item_b + 256 + ffstate_b;
   if (need > kStaticScratchBytes) {
     set_error("rexi_step_static: this truncation and batch need " + std::to_string(need) +
               " bytes of scratch, above the fixed limit of " + std::to_string(kStaticScratchBytes) +
@@ -760,6 +956,7 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
   double2 *ybuf = reinterpret_cast<double2 *>(base + 2 * state_b + part_b);
   WorkItem *items = reinterpret_cast<WorkItem *>(base + 2 * state_b + part_b + y_b);
   unsigned *counter = reinterpret_cast<unsigned *>(base + 2 * state_b + part_b + y_b + item_b);
+  double2 *s_ff = reinterpret_cast<double2 *>(base + 2 * state_b + part_b + y_b + item_b + 256);
 
   if (pl.prm.fsphere) {  // closed-form per-degree solves: only the two state buffers are used
     e = launch_transpose_in(static_cast<const double2 *>(in), s_in, pl.nspec, B, st);
@@ -777,10 +974,11 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);  // the work counter starts at zero
+  if (e == cudaSuccess && pl.ff) e = launch_split_state(pl, s_in, s_ff, 3 * pl.nspec * B, st);
   if (e == cudaSuccess) {
     SolveArgs a;
     a.v.fac = pl.fac_fwd;
-    a.v.sin = s_in;
+    a.v.sin = pl.ff ? s_ff : s_in;
     a.v.part = part;
     a.v.sys = pl.sys_dev;
     a.v.P = pl.P;
@@ -799,7 +997,8 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
     a.counter = counter;
     a.nitems = nitems;
     a.lmax = pl.lmax;
-    solve_kernel<<<warps / 4, 128, 0, st>>>(a);
+    if (pl.ff) solve_kernel<true><<<warps / 4, 128, 0, st>>>(a);
+    else solve_kernel<false><<<warps / 4, 128, 0, st>>>(a);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
@@ -825,7 +1024,8 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
     r.tau = pl.prm.tau;
     const int64_t total = 3 * pl.nspec * B;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)pl.num_sms * 8);
-    reduce_kernel<<<blocks, 256, 0, st>>>(r);
+    if (pl.ff) reduce_kernel<true><<<blocks, 256, 0, st>>>(r);
+    else reduce_kernel<false><<<blocks, 256, 0, st>>>(r);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = launch_transpose_out(s_out, static_cast<double2 *>(out), pl.nspec, B, pl.N, st);

@@ -30,6 +30,7 @@ def main():
     ap.add_argument("--tune", action="store_true", help="pick the pole-slot layout by timing, as bench.py does")
     ap.add_argument("--pole-slots", type=int, default=0, help="fixed pole-slot count (0: the plan's default)")
     ap.add_argument("--solver", default="delta", choices=["delta", "phi"])
+    ap.add_argument("--solve-arith", default="fp64", choices=["fp64", "fp32x2"])
     ap.add_argument("--layout-shape", type=int, default=-1,
                     help="with --pole-slots: 0 same pole groups for every order, 1 proportional to length")
     args = ap.parse_args()
@@ -41,7 +42,8 @@ def main():
         nlon += 2
     nlat = args.nlat or nlon // 2
     plan = rexi.Plan(args.N, nlat, nlon, M=args.M, tau=args.tau, max_batch=args.batch, layout=args.layout,
-                     precision=args.precision, pole_slots=args.pole_slots, solver=args.solver)
+                     precision=args.precision, pole_slots=args.pole_slots, solver=args.solver,
+                     solve_arith=args.solve_arith)
     if args.layout_shape >= 0 and args.pole_slots > 0:
         plan.set_pole_slots(args.batch, args.pole_slots, args.layout_shape)
     slots = plan.tune(args.batch) if args.tune else plan.info()["pole_slots"]

@@ -31,6 +31,7 @@ class rexi_params(ctypes.Structure):
         ("strict_range", ctypes.c_int32), ("pole_slots", ctypes.c_int32),
         ("alpha", ctypes.POINTER(ctypes.c_double)), ("beta", ctypes.POINTER(ctypes.c_double)),
         ("npoles", ctypes.c_int32), ("fsphere", ctypes.c_int32), ("solver", ctypes.c_int32),
+        ("solve_arith", ctypes.c_int32),
     ]
 
 
@@ -131,12 +132,16 @@ def _stream_handle(stream):
 
 
 class Plan:
-    """A librexi plan: one T-REXI step of the linear SWE for a fixed truncation, grid and poles."""
+    """A librexi plan: one T-REXI step of the linear SWE for a fixed truncation, grid and poles.
+
+    ``precision`` selects the transforms ("fp64", or "mixed": 3xTF32 Legendre and FP32
+    FFTs); ``solve_arith`` the arithmetic of the banded solves and the pole sum ("fp64",
+    or "fp32x2": float-float pairs of FP32 on the FP32 pipes, 48-bit significands)."""
 
     def __init__(self, N, nlat=None, nlon=None, M=128, h=0.2, tau=3600.0, max_batch=1,
                  layout="grid", precision="fp64", normalize=True, alpha=None, beta=None,
                  radius=6.37122e6, omega=7.292e-5, gravity=9.80616, mean_depth=1.0e4,
-                 pole_slots=0, strict_range=False, fsphere=False, solver="delta"):
+                 pole_slots=0, strict_range=False, fsphere=False, solver="delta", solve_arith="fp64"):
         lib = load()
         p = rexi_params()
         lib.rexi_params_default(ctypes.byref(p))
@@ -157,6 +162,7 @@ class Plan:
         p.pole_slots = pole_slots
         p.fsphere = 1 if fsphere else 0
         p.solver = {"delta": 0, "phi": 1}[solver]
+        p.solve_arith = {"fp64": 0, "fp32x2": 1}[solve_arith]
         self._keep = []
         if alpha is not None:
             al = np.ascontiguousarray(np.asarray(alpha, dtype=np.complex128)).view(np.float64)
@@ -170,6 +176,7 @@ class Plan:
         self._h = h_
         self.N, self.nlat, self.nlon, self.max_batch = N, nlat, nlon, max_batch
         self.layout, self.precision, self.solver = layout, precision, solver
+        self.solve_arith = solve_arith
         self.layout_shape = {}
         self.nspec = (N + 1) * (N + 2) // 2
 
@@ -255,7 +262,7 @@ class Plan:
         of pole slots (the shape is kept in ``self.layout_shape[batch]``).
 
         ``cache``: path of a JSON file of earlier choices keyed by the plan's shape (N,
-        grid, P, batch, precision, solver) and the GPU's name; a hit sets the layout
+        grid, P, batch, precision, solver, solve arithmetic) and the GPU's name; a hit sets the layout
         without timing (rexi_set_pole_slots), a miss tunes and records the result."""
         key = None
         if cache:
@@ -288,8 +295,8 @@ class Plan:
         import torch
         i = self.info()
         gpu = torch.cuda.get_device_name(torch.cuda.current_device())
-        return "N%d_%dx%d_P%d_B%d_%s_%s_%s_%s" % (i["N"], i["nlon"], i["nlat"], i["P"], batch, self.precision,
-                                                  self.solver, self.layout, gpu)
+        return "N%d_%dx%d_P%d_B%d_%s_%s_%s_%s_%s" % (i["N"], i["nlon"], i["nlat"], i["P"], batch, self.precision,
+                                                     self.solver, self.solve_arith, self.layout, gpu)
 
     def info(self):
         v = (ctypes.c_int64 * 8)()
