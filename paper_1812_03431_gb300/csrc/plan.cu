@@ -355,8 +355,9 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   pl->partial_cap = (size_t)cap;
   if ((e = dalloc(&pl->partial, (size_t)cap * 3 * NS * B, &bytes))) return fail("partials", e);
   pl->resident_warps = pl->num_sms * 16;
-  // forward-sweep intermediates: two poles per lane per row
-  if ((e = dalloc(&pl->yscratch, (size_t)pl->resident_warps * pl->lmax * 2 * 32, &bytes))) return fail("scratch", e);
+  // forward-sweep intermediates: sweep_width poles per lane per row
+  if ((e = dalloc(&pl->yscratch, (size_t)pl->resident_warps * pl->lmax * sweep_width(pl->ff) * 32, &bytes)))
+    return fail("scratch", e);
   if ((e = dalloc(&pl->counter, 1, &bytes))) return fail("counter", e);
   pl->slots_override = prm.pole_slots;
   if ((e = cudaDeviceSynchronize())) return fail("setup", e);

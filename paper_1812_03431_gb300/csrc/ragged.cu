@@ -85,7 +85,8 @@ rexi_status rexi_ragged_create(rexi_plan *const *plans, int32_t nplans, int32_t 
     rg->lmax = std::max(rg->lmax, plans[i]->pl->lmax);
     rg->resident_warps = std::max(rg->resident_warps, plans[i]->pl->resident_warps);
   }
-  cudaError_t e = cudaMalloc(&rg->ybuf, (size_t)rg->resident_warps * rg->lmax * 2 * 32 * sizeof(double2));
+  cudaError_t e = cudaMalloc(&rg->ybuf, (size_t)rg->resident_warps * rg->lmax * sweep_width(rg->plans[0]->ff) * 32 *
+                                            sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&rg->counter, sizeof(unsigned));
   if (e != cudaSuccess) {
     rexi_ragged_destroy(rg);

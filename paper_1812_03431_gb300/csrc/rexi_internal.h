@@ -103,6 +103,10 @@ struct FftPlan {
 
 enum FacComp { F_L = 0, F_G, F_E, F_F, F_C, F_BD, F_BAD, F_ZP, F_ZM, F_NCOMP };
 
+// Poles a lane sweeps at once in the solve kernel; the forward-sweep buffer holds lmax
+// rows of that many values per lane.
+inline int sweep_width(bool) { return 2; }
+
 struct Plan {
   rexi_params prm{};
   int N = 0, nlat = 0, nlon = 0, J = 0, P = 0;
@@ -120,7 +124,8 @@ struct Plan {
   int4 *sys_dev = nullptr;
   int32_t *m_of_dev = nullptr;
 
-  // solve factors (forward and adjoint): [F_NCOMP][nrows][P] double2
+  // solve factors (forward and adjoint): [F_NCOMP][nrows][P] double2; float-float plans
+  // hold [nrows][P][F_NCOMP] float-float values (float4 in the double2 slots)
   double2 *fac_fwd = nullptr, *fac_adj = nullptr;
   double2 *alpha_dev = nullptr, *beta_dev = nullptr;
   // pole-independent parts: W[idx] = sum_k beta_k/s_{k,n} (zeta), scalar S_Phi
@@ -203,7 +208,7 @@ cudaError_t launch_solve(Plan &pl, const SolveLayout &lay, bool adjoint, const d
 // One plan's view for the solve kernels: factors, internal states, partial sums,
 // systems and the lane layout of its batch.
 struct SolveView {
-  const double2 *fac;   // [F_NCOMP][nrows][P]
+  const double2 *fac;   // [F_NCOMP][nrows][P] (float-float plans: [nrows][P][F_NCOMP])
   const double2 *sin;   // [3][nspec][B]
   double2 *part;        // [3][nspec][slots][B]
   const int4 *sys;      // per (m, p): {m, n0, len, row0}

@@ -65,12 +65,13 @@ __device__ __forceinline__ double2 cfma(double2 acc, double2 a, double2 b) {
 struct SetupArgs {
   const double *coef;   // [nspec][4] = sigma, ct, dt, G
   const double2 *alpha, *beta;
-  double2 *fac;         // [F_NCOMP][nrows][P]
+  double2 *fac;         // [F_NCOMP][nrows][P], or [nrows][P][F_NCOMP] when interleaved
   const int4 *sys;      // per system (m, p): {m, n0, len, row0}
   int nsys, P, N;
   int64_t nrows;
   double tau, phibar, q;  // q = 2 Omega tau
   int adjoint;
+  int interleaved;      // float-float plans: the nine factors of a (row, pole) are adjacent
 };
 
 __device__ __forceinline__ int64_t sidx(int N, int m, int n) { return (int64_t)m * (2 * N + 3 - m) / 2 + (n - m); }
@@ -101,7 +102,10 @@ __global__ void factor_setup_kernel(SetupArgs a) {
   };
   const int64_t NR = a.nrows, P = a.P;
   double2 *F = a.fac;
-  auto put = [&](int comp, int64_t row, double2 v) { F[((int64_t)comp * NR + row) * P + k] = v; };
+  auto at = [&](int comp, int64_t row) -> int64_t {
+    return a.interleaved ? (row * P + k) * F_NCOMP + comp : ((int64_t)comp * NR + row) * P + k;
+  };
+  auto put = [&](int comp, int64_t row, double2 v) { F[at(comp, row)] = v; };
   const double2 one = make_double2(1.0, 0.0);
 
   // first pass: d' and l, store d' temporarily in the F_C slot
@@ -162,8 +166,8 @@ __global__ void factor_setup_kernel(SetupArgs a) {
   for (int i = len - 1; i >= 0; --i) {
     const int n = n0 + 2 * i;
     const int64_t row = row0 + i;
-    const double2 C = F[((int64_t)F_C * NR + row) * P + k];
-    const double2 dp = F[((int64_t)F_BD * NR + row) * P + k];
+    const double2 C = F[at(F_C, row)];
+    const double2 dp = F[at(F_BD, row)];
     put(F_C, row, i == len - 1 ? make_double2(0, 0) : cdiv(C, dnext));
     const double2 bd = cdiv(be, dp);  // beta / d'
     const double G = C4(n, 3);
@@ -187,7 +191,7 @@ __global__ void factor_setup_kernel(SetupArgs a) {
 
 struct SolveArgs {
   SolveView v;
-  double2 *ybuf;        // [resident warps][lmax][32]
+  double2 *ybuf;        // [resident warps][lmax][sweep_width][32]
   const WorkItem *items;
   unsigned *counter;
   int nitems, lmax;
@@ -291,89 +295,127 @@ __device__ __forceinline__ void sweep_poles(const SolveView &a, const int (&k)[K
 // FP32 rate, so the solve runs on the FP32 pipes at 48-bit significand precision.
 __device__ __forceinline__ float4 ldf(const float4 *p) { return __ldg(p); }
 
+// Loads of one forward row: the three states and the four factors of each pole.
+template <int KC>
+struct FwdRow {
+  float4 zn, d0, p0, g[KC], e[KC], f[KC], l[KC];
+};
+// Loads of one backward row: the sweep intermediates, the five factors of each pole
+// and the three slot partials.
+template <int KC>
+struct BwdRow {
+  float4 y[KC], c[KC], bd[KC], bad[KC], zp[KC], zm[KC], accD, accP, accZ;
+};
+
 template <int KC>
 __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k)[KC], int n0, int len, int nmin,
                                                int64_t row0, int64_t base_idx, const float4 *sPhi,
                                                const float4 *sZeta, const float4 *sDel, float4 *pPhi,
                                                float4 *pZeta, float4 *pDel, int64_t rstride, bool first,
                                                float4 *ybuf) {
-  const int64_t NR = a.nrows, P = a.P;
+  const int64_t RS = (int64_t)a.P * F_NCOMP;  // row stride of the interleaved factors
   const int N = a.N, B = a.B;
-  const float4 *fac = reinterpret_cast<const float4 *>(a.fac);
-  const float4 *fL[KC], *fG[KC], *fE[KC], *fF[KC];
-  for (int c = 0; c < KC; ++c) {
-    fL[c] = fac + ((int64_t)F_L * NR + row0) * P + k[c];
-    fG[c] = fac + ((int64_t)F_G * NR + row0) * P + k[c];
-    fE[c] = fac + ((int64_t)F_E * NR + row0) * P + k[c];
-    fF[c] = fac + ((int64_t)F_F * NR + row0) * P + k[c];
-  }
+  // factor (comp, row i, pole c) at fk[c] + i RS + comp
+  const float4 *fk[KC];
+  for (int c = 0; c < KC; ++c) fk[c] = reinterpret_cast<const float4 *>(a.fac) + (row0 * a.P + k[c]) * F_NCOMP;
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  // Every row's loads are issued one row ahead (into registers), so that their latency
+  // overlaps the previous row's arithmetic.
+  auto load_fwd = [&](int i, FwdRow<KC> &r) {
+    const int n = n0 + 2 * i;
+    const int64_t ix = base_idx + n;
+    r.zn = (n + 1 <= N) ? ldf(sZeta + (ix + 1) * B) : zero;
+    r.d0 = ldf(sDel + ix * B);
+    r.p0 = ldf(sPhi + ix * B);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      const float4 *f = fk[c] + (int64_t)i * RS;
+      r.g[c] = ldf(f + F_G);
+      r.e[c] = ldf(f + F_E);
+      r.f[c] = ldf(f + F_F);
+      r.l[c] = ldf(f + F_L);
+    }
+  };
   // ---- forward sweep: y_i = delta0 - g Phi0 - e zeta0_{n-1} - f zeta0_{n+1} - l y_{i-1}
   float4 yprev[KC];
   for (int c = 0; c < KC; ++c) yprev[c] = zero;
   float4 zprev = (n0 - 1 >= nmin) ? ldf(sZeta + (base_idx + n0 - 1) * B) : zero;
+  FwdRow<KC> cur;
+  load_fwd(0, cur);
   for (int i = 0; i < len; ++i) {
-    const int n = n0 + 2 * i;
-    const int64_t ix = base_idx + n;
-    const float4 zn = (n + 1 <= N) ? ldf(sZeta + (ix + 1) * B) : zero;
-    const float4 d0 = ldf(sDel + ix * B), p0 = ldf(sPhi + ix * B);
+    FwdRow<KC> nxt;
+    load_fwd(i + 1 < len ? i + 1 : i, nxt);
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      ff::CAcc y = ff::cacc(d0);
-      ff::cmsub(y, ldf(fG[c] + (int64_t)i * P), p0);
-      ff::cmsub(y, ldf(fE[c] + (int64_t)i * P), zprev);
-      ff::cmsub(y, ldf(fF[c] + (int64_t)i * P), zn);
-      ff::cmsub(y, ldf(fL[c] + (int64_t)i * P), yprev[c]);
+      ff::CAcc y = ff::cacc(cur.d0);
+      ff::cmsub(y, cur.g[c], cur.p0);
+      ff::cmsub(y, cur.e[c], zprev);
+      ff::cmsub(y, cur.f[c], cur.zn);
+      ff::cmsub(y, cur.l[c], yprev[c]);
       const float4 yv = ff::norm(y);
       ybuf[((int64_t)i * KC + c) * 32] = yv;
       yprev[c] = yv;
     }
-    zprev = zn;
+    zprev = cur.zn;
+    cur = nxt;
   }
   // ---- backward sweep with the beta-weighted accumulation (as in sweep_poles)
-  const float4 *fC[KC], *fBD[KC], *fBAD[KC], *fZP[KC], *fZM[KC];
-  for (int c = 0; c < KC; ++c) {
-    fC[c] = fac + ((int64_t)F_C * NR + row0) * P + k[c];
-    fBD[c] = fac + ((int64_t)F_BD * NR + row0) * P + k[c];
-    fBAD[c] = fac + ((int64_t)F_BAD * NR + row0) * P + k[c];
-    fZP[c] = fac + ((int64_t)F_ZP * NR + row0) * P + k[c];
-    fZM[c] = fac + ((int64_t)F_ZM * NR + row0) * P + k[c];
-  }
+  auto load_bwd = [&](int i, BwdRow<KC> &r) {
+    const int n = n0 + 2 * i;
+    const int64_t ix = base_idx + n;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      const float4 *f = fk[c] + (int64_t)i * RS;
+      r.y[c] = ybuf[((int64_t)i * KC + c) * 32];
+      r.c[c] = ldf(f + F_C);
+      r.bd[c] = ldf(f + F_BD);
+      r.bad[c] = ldf(f + F_BAD);
+      r.zp[c] = ldf(f + F_ZP);
+      r.zm[c] = ldf(f + F_ZM);
+    }
+    r.accD = first ? zero : pDel[ix * rstride];
+    r.accP = first ? zero : pPhi[ix * rstride];
+    r.accZ = (first || n + 1 > N) ? zero : pZeta[(ix + 1) * rstride];
+  };
   float4 wnext[KC], zmnext[KC];
   for (int c = 0; c < KC; ++c) wnext[c] = zmnext[c] = zero;
+  BwdRow<KC> bc;
+  load_bwd(len - 1, bc);
   for (int i = len - 1; i >= 0; --i) {
     const int n = n0 + 2 * i;
     const int64_t ix = base_idx + n;
+    BwdRow<KC> bn;
+    load_bwd(i > 0 ? i - 1 : i, bn);
     float4 wv[KC];
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      ff::CAcc w = ff::cacc(ybuf[((int64_t)i * KC + c) * 32]);
-      ff::cmsub(w, ldf(fC[c] + (int64_t)i * P), wnext[c]);
+      ff::CAcc w = ff::cacc(bc.y[c]);
+      ff::cmsub(w, bc.c[c], wnext[c]);
       wv[c] = ff::norm(w);
     }
-    ff::CAcc accD = first ? ff::czero() : ff::cacc(pDel[ix * rstride]);
-    ff::CAcc accP = first ? ff::czero() : ff::cacc(pPhi[ix * rstride]);
+    ff::CAcc accD = ff::cacc(bc.accD), accP = ff::cacc(bc.accP);
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      ff::cmac(accD, ldf(fBD[c] + (int64_t)i * P), wv[c]);
-      ff::cmac(accP, ldf(fBAD[c] + (int64_t)i * P), wv[c]);
+      ff::cmac(accD, bc.bd[c], wv[c]);
+      ff::cmac(accP, bc.bad[c], wv[c]);
     }
     pDel[ix * rstride] = ff::norm(accD);
     pPhi[ix * rstride] = ff::norm(accP);
     if (n + 1 <= N) {
-      ff::CAcc accZ = first ? ff::czero() : ff::cacc(pZeta[(ix + 1) * rstride]);
+      ff::CAcc accZ = ff::cacc(bc.accZ);
 #pragma unroll
       for (int c = 0; c < KC; ++c) {
-        ff::cmac(accZ, ldf(fZP[c] + (int64_t)i * P), wv[c]);
+        ff::cmac(accZ, bc.zp[c], wv[c]);
         ff::cmac(accZ, zmnext[c], wnext[c]);
       }
       pZeta[(ix + 1) * rstride] = ff::norm(accZ);
     }
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      zmnext[c] = ldf(fZM[c] + (int64_t)i * P);
+      zmnext[c] = bc.zm[c];
       wnext[c] = wv[c];
     }
+    bc = bn;
   }
   if (n0 - 1 >= nmin) {
     const int64_t ix = base_idx + n0 - 1;
@@ -758,6 +800,7 @@ cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st) {
   a.phibar = pl.prm.gravity * pl.prm.mean_depth;
   a.q = 2.0 * pl.prm.omega * pl.prm.tau;
   a.adjoint = adjoint ? 1 : 0;
+  a.interleaved = pl.ff ? 1 : 0;
   int64_t total = (int64_t)a.P * a.nsys;
   factor_setup_kernel<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
@@ -930,7 +973,7 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
   const int warps = pl.num_sms * 4;
   const size_t state_b = align256((size_t)3 * pl.nspec * B * sizeof(double2));
   const size_t part_b = align256((size_t)3 * pl.nspec * slots * B * sizeof(double2));
-  const size_t y_b = align256((size_t)warps * pl.lmax * 2 * 32 * sizeof(double2));
+  const size_t y_b = align256((size_t)warps * pl.lmax * sweep_width(pl.ff) * 32 * sizeof(double2));
   const size_t item_b = align256((size_t)nitems * sizeof(WorkItem));
   const size_t ffstate_b = pl.ff ? state_b : 0;  // float-float copy of the input states
   const size_t need = 2 * state_b + part_b + y_b + item_b + 256 + ffstate_b;
