@@ -29,12 +29,21 @@ sys.path.insert(0, ROOT)
 
 WORK = dict(N=341, nlat=512, nlon=1024, M=256, h=0.2, tau=1200.0, batch=16, seed=1005)
 METRIC = "REXI steps/s at T341, K=256 poles: chosen vs plain FP64 form at stated error"
+# (name, transforms, solve arithmetic); the first is the chosen form.  mixed_fp32x2: 3xTF32
+# Legendre and FP32 FFTs, float-float banded solves and pole sum; mixed: the same transforms
+# with binary64 solves; fp64: every stage in binary64 (the plain form).
+FORMS = [("mixed_fp32x2", "mixed", "fp32x2"), ("mixed", "mixed", "fp64"), ("fp64", "fp64", "fp64")]
 FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve: 36 FMAs
+# FP32 operations per (state, pole, row) of the float-float solve: the same 36 real
+# multiply-adds, each an error-free product and sum of 12 FP32 operations (1 mul, 3 FMA,
+# 8 add); stored values stay unnormalised pairs, so there is no renormalisation
+FF_OPS_PER_ROW = 36 * 12
 # DRAM bytes (read + write) of one solve_kernel launch from ncu captures at T170, K=256,
 # batch 16, by (pole slots, layout shape) (profiles/solve_kernel_t170_b16.md); traffic per
 # row is constant, so a launch of the bench workload moves this times rows(T341) /
 # rows(T170).  Re-captured after each change of the solve kernel.
 SOLVE_TRAFFIC_T170 = {(32, 0): 12.64e9, (32, 1): 12.58e9}
+SOLVE_FF_TRAFFIC_T170 = {(32, 0): 10.86e9}  # the float-float kernel (solve_kernel<true>)
 
 
 def rows_of(N):
@@ -46,6 +55,11 @@ def fp64_peak_tflops(sm_mhz):
     return 152 * 4 * sm_mhz * 1e6 / 1e12
 
 
+def fp32_peak_tops(sm_mhz):
+    # GB300: 152 SMs x 128 FP32 lanes, one add, multiply or FMA per lane and clock
+    return 152 * 128 * sm_mhz * 1e6 / 1e12
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -55,7 +69,7 @@ def measured_peaks():
         return 6800.0, 1900.0, "fallback"
 
 
-def kernel_rooflines(form, stages, slots, sm_mhz):
+def kernel_rooflines(form, stages, slots, sm_mhz, solve_arith="fp64"):
     """Every stage of the grid step against its own bound: algorithmic bytes (HBM-bound
     stages) or flops (ALU-bound stages) per launch / its live CUDA-event time."""
     W = WORK
@@ -97,10 +111,16 @@ def kernel_rooflines(form, stages, slots, sm_mhz):
         fl = 20.0 * ns * (nlat // 2) * B
         put("leg_ana", "alu", fl, "TFLOP/s", fp64, "derived FP64")
         put("leg_syn", "alu", fl, "TFLOP/s", fp64, "derived FP64")
-    put("solve", "alu", FLOPS_PER_ROW * B * P * rows_of(N), "TFLOP/s", fp64, "derived FP64")
-    # reduction: one FP64 complex add per slot and output coefficient; the kernel is bound
-    # by the FP64 issue rate (ncu: FP64 pipe 82 %, DRAM 47 %), where an add costs an FMA's slot
-    put("reduce", "alu", 2.0 * slots * 3 * ns * B, "TFLOP/s", fp64 / 2, "derived FP64 add rate")
+    if solve_arith == "fp32x2":
+        put("solve", "alu", FF_OPS_PER_ROW * B * P * rows_of(N), "Tops/s", fp32_peak_tops(sm_mhz),
+            "derived FP32 (ops = adds, multiplies and FMAs)")
+        # float-float reduction: reads every slot's partials once, writes the result
+        put("reduce", "hbm", (slots + 2) * 3 * ns * B * 16, "GB/s", hbm, src + " HBM copy")
+    else:
+        put("solve", "alu", FLOPS_PER_ROW * B * P * rows_of(N), "TFLOP/s", fp64, "derived FP64")
+        # reduction: one FP64 complex add per slot and output coefficient; the kernel is bound
+        # by the FP64 issue rate (ncu: FP64 pipe 82 %, DRAM 47 %), where an add costs an FMA's slot
+        put("reduce", "alu", 2.0 * slots * 3 * ns * B, "TFLOP/s", fp64 / 2, "derived FP64 add rate")
     return out
 
 
@@ -267,7 +287,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--form", default="auto", choices=["auto"] + [f[0] for f in FORMS],
+                    help="auto: time every form, the first (chosen) one gives value")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-phi-solver", action="store_true",
                     help="skip timing the paper's geopotential-only solver next to the default one")
@@ -289,20 +310,13 @@ def main():
 
     W = WORK
     B = W["batch"]
-    precisions = ["fp64"]
-    if args.precision in ("auto", "mixed"):
-        try:
-            rexi.Plan(15, 16, 48, M=4, precision="mixed").close()
-            precisions = ["mixed", "fp64"] if args.precision == "auto" else ["mixed"]
-        except rexi.RexiError:
-            if args.precision == "mixed":
-                raise
+    forms = [f for f in FORMS if args.form in ("auto", f[0])]
     S = torch.from_numpy(inputs.random_spectral(W["N"], B, W["seed"])).cuda()
     results = {}
     stream = torch.cuda.current_stream()
-    for prec in precisions:
+    for name, prec, arith in forms:
         plan = rexi.Plan(W["N"], W["nlat"], W["nlon"], M=W["M"], h=W["h"], tau=W["tau"], max_batch=B,
-                         precision=prec)
+                         precision=prec, solve_arith=arith)
         slots = plan.tune(B)  # the library's autotuner picks the pole-slot count for this batch
         x = plan.synthesize(S)
         y = torch.empty_like(x)
@@ -381,9 +395,10 @@ def main():
         ms_e2e = f0.elapsed_time(f1) / args.steps
         ms_e2e = replica_max_ms(ms_e2e, dist)
         e2e_same = bool(torch.equal(yh, y.cpu()))  # the copied-back result is the device step's, bit for bit
-        results[prec] = dict(ms=ms, ms_e2e=ms_e2e, stages={k: v / max(ncalls, 1) for k, v in stages.items()},
+        results[name] = dict(ms=ms, ms_e2e=ms_e2e, stages={k: v / max(ncalls, 1) for k, v in stages.items()},
                              clocks=ck, y=y, bytes=x.numel() * 8, info=plan.info(), slots=slots,
-                             shape=plan.layout_shape.get(B, 0), e2e_same=e2e_same)
+                             shape=plan.layout_shape.get(B, 0), e2e_same=e2e_same, precision=prec,
+                             solve_arith=arith)
         plan.close()
 
     # the paper's geopotential-only solver on the same workload (FP64 form), for comparison
@@ -416,46 +431,60 @@ def main():
                        "(pole, m, parity); a different truncation, so it differs at the highest degrees"}
         plan.close()
 
-    chosen = precisions[0]
+    chosen = forms[0][0]
     r = results[chosen]
     P = 2 * (W["M"] + 11) + 1
     solve_ms = r["stages"]["solve"]
-    flops = FLOPS_PER_ROW * B * P * rows_of(W["N"])
     sm_mhz = (r["clocks"] or {}).get("sm_max_mhz") or 2070.0
-    peak = fp64_peak_tflops(sm_mhz)
-    achieved = flops / (solve_ms * 1e-3) / 1e12
-    tkey = min(SOLVE_TRAFFIC_T170, key=lambda k: (k[1] != r["shape"], abs(k[0] - r["slots"])))
+    if r["solve_arith"] == "fp32x2":
+        amount, peak = FF_OPS_PER_ROW * B * P * rows_of(W["N"]), fp32_peak_tops(sm_mhz)
+        traffic_t170, kname = SOLVE_FF_TRAFFIC_T170, "solve_kernel<true> (float-float banded solves + pole sum)"
+        roof_unit, peak_source = "Tops/s", "derived: 152 SMs x 128 FP32 lanes x sm_max_mhz (ops = adds, mults, FMAs)"
+    else:
+        amount, peak = FLOPS_PER_ROW * B * P * rows_of(W["N"]), fp64_peak_tflops(sm_mhz)
+        traffic_t170, kname = SOLVE_TRAFFIC_T170, "solve_kernel<false> (FP64 banded solves + pole sum)"
+        roof_unit, peak_source = "TFLOP/s", "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz"
+    achieved = amount / (solve_ms * 1e-3) / 1e12
+    tkey = min(traffic_t170, key=lambda k: (k[1] != r["shape"], abs(k[0] - r["slots"])))
+    traffic = traffic_t170[tkey] * rows_of(W["N"]) / rows_of(170)
+    dtypes = {"mixed_fp32x2": "f64 i/o; float-float (2 x f32) solves + pole sum; 3xtf32 legendre; f32 fft",
+              "mixed": "f64 solves + pole sum; 3xtf32 legendre; f32 fft", "fp64": "f64"}
     line = {
         "metric": METRIC, "value": world * 1e3 / r["ms"], "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if chosen == "fp64" else "f64 solves + 3xtf32 legendre",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtypes[chosen],
         "data": "synthetic", "config": {**workload_config(), "form": chosen, "pole_slots": r["slots"], "layout_shape": r["shape"]},
-        "roofline": {"bound": "alu", "kernel": "solve_kernel (FP64 banded solves + pole sum)",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": SOLVE_TRAFFIC_T170[tkey] * rows_of(W["N"]) / rows_of(170),
+        "roofline": {"bound": "alu", "kernel": kname,
+                     "achieved": achieved, "peak": peak, "unit": roof_unit, "frac": achieved / peak,
+                     "traffic": traffic,
                      "traffic_source": "ncu dram bytes at T170/K256/B16 with %d pole slots, layout shape %d "
                                        "(the captured layout nearest the bench's %d, shape %d), scaled by rows "
                                        "to T341" % (tkey[0], tkey[1], r["slots"], r["shape"]),
-                     "dram_gbs": SOLVE_TRAFFIC_T170[tkey] * rows_of(W["N"]) / rows_of(170) / (solve_ms * 1e-3) / 1e9,
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz",
-                     "flops_per_launch": flops, "launch_ms": solve_ms},
+                     "dram_gbs": traffic / (solve_ms * 1e-3) / 1e9,
+                     "peak_source": peak_source, "algorithmic_per_launch": amount, "launch_ms": solve_ms},
         "state_steps_per_s": world * B * 1e3 / r["ms"],
         "stage_ms": r["stages"],
-        "kernels": kernel_rooflines(chosen, r["stages"], r["slots"], sm_mhz),
+        "kernels": kernel_rooflines(r["precision"], r["stages"], r["slots"], sm_mhz, r["solve_arith"]),
         "e2e": {"value": world * 1e3 / r["ms_e2e"], "unit": "steps/s", "h2d_bytes_per_step": r["bytes"],
                 "d2h_bytes_per_step": r["bytes"], "copies": "pinned host, own streams, overlapping compute",
                 "result_matches_device_step": r["e2e_same"]},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": (7 if r["solve_arith"] == "fp32x2" else 6) * args.steps,
         "clocks": r["clocks"],
     }
+    for name, _, _ in forms[1:]:
+        f = results[name]
+        line[name + "_form"] = {"value": world * 1e3 / f["ms"], "ms_per_step": f["ms"], "stage_ms": f["stages"],
+                                "pole_slots": f["slots"], "layout_shape": f["shape"],
+                                "kernels": kernel_rooflines(f["precision"], f["stages"], f["slots"], sm_mhz,
+                                                            f["solve_arith"])}
     if "fp64" in results and chosen != "fp64":
         f = results["fp64"]
-        d = (results[chosen]["y"] - f["y"]).norm() / f["y"].norm()
-        line["fp64_form"] = {"value": world * 1e3 / f["ms"], "ms_per_step": f["ms"], "stage_ms": f["stages"],
-                             "pole_slots": f["slots"], "layout_shape": f["shape"],
-                             "kernels": kernel_rooflines("fp64", f["stages"], f["slots"], sm_mhz)}
-        line["error_vs_fp64_form"] = float(d)
+        line["error_vs_fp64_form"] = float((results[chosen]["y"] - f["y"]).norm() / f["y"].norm())
+    if "mixed" in results and chosen == "mixed_fp32x2":
+        f = results["mixed"]["y"]
+        y = results[chosen]["y"]
+        line["vs_mixed_fp64_solves"] = {"rel_l2": float((y - f).norm() / f.norm()),
+                                        "bitwise_equal": bool(torch.equal(y, f))}
     if phi is not None:
         line["phi_solver_form"] = phi
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

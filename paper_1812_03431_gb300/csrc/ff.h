@@ -89,6 +89,14 @@ __device__ __forceinline__ void cadd(CAcc &acc, float4 v) {
   add(acc.im, v.z, v.w);
 }
 
+// An accumulator as a value without renormalising: the pair (s, e) still represents s + e
+// exactly, and |e| stays within a few 2^-24 of the summed magnitudes |p| that formed it.
+// As a factor of mac, e enters through FP32 cross products (relative error 2^-24), so the
+// error stays at the float-float level of those magnitudes; as the start of another
+// accumulator or a summand of add it is exact.  Values that are stored and read back
+// within a sweep skip the six-operation TwoSum this way.
+__device__ __forceinline__ float4 raw(const CAcc &a) { return make_float4(a.re.s, a.re.e, a.im.s, a.im.e); }
+
 // normalised value of an accumulator (TwoSum: no condition on |s| against |e|)
 __device__ __forceinline__ float4 norm(const CAcc &a) {
   float4 r;

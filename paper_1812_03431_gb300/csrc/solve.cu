@@ -352,7 +352,7 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
       ff::cmsub(y, cur.e[c], zprev);
       ff::cmsub(y, cur.f[c], cur.zn);
       ff::cmsub(y, cur.l[c], yprev[c]);
-      const float4 yv = ff::norm(y);
+      const float4 yv = ff::raw(y);
       ybuf[((int64_t)i * KC + c) * 32] = yv;
       yprev[c] = yv;
     }
@@ -391,7 +391,7 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
     for (int c = 0; c < KC; ++c) {
       ff::CAcc w = ff::cacc(bc.y[c]);
       ff::cmsub(w, bc.c[c], wnext[c]);
-      wv[c] = ff::norm(w);
+      wv[c] = ff::raw(w);
     }
     ff::CAcc accD = ff::cacc(bc.accD), accP = ff::cacc(bc.accP);
 #pragma unroll
@@ -399,8 +399,8 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
       ff::cmac(accD, bc.bd[c], wv[c]);
       ff::cmac(accP, bc.bad[c], wv[c]);
     }
-    pDel[ix * rstride] = ff::norm(accD);
-    pPhi[ix * rstride] = ff::norm(accP);
+    pDel[ix * rstride] = ff::raw(accD);
+    pPhi[ix * rstride] = ff::raw(accP);
     if (n + 1 <= N) {
       ff::CAcc accZ = ff::cacc(bc.accZ);
 #pragma unroll
@@ -408,7 +408,7 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
         ff::cmac(accZ, bc.zp[c], wv[c]);
         ff::cmac(accZ, zmnext[c], wnext[c]);
       }
-      pZeta[(ix + 1) * rstride] = ff::norm(accZ);
+      pZeta[(ix + 1) * rstride] = ff::raw(accZ);
     }
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
@@ -422,7 +422,7 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
     ff::CAcc accZ = first ? ff::czero() : ff::cacc(pZeta[ix * rstride]);
 #pragma unroll
     for (int c = 0; c < KC; ++c) ff::cmac(accZ, zmnext[c], wnext[c]);
-    pZeta[ix * rstride] = ff::norm(accZ);
+    pZeta[ix * rstride] = ff::raw(accZ);
   }
 }
 

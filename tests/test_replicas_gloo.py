@@ -57,4 +57,13 @@ def test_kernel_rooflines_arithmetic():
         P = 2 * (W["M"] + 11) + 1
         assert k["solve"]["algorithmic"] == 72 * W["batch"] * P * bench.rows_of(W["N"])
         assert abs(k["solve"]["peak"] - 152 * 4 * 2070e6 / 1e12) < 1e-12
+    # the float-float solve: 36 multiply-adds of 12 FP32 operations at the derived FP32 rate;
+    # its reduction is HBM-bound (every slot's partials read once, the result written)
+    k = bench.kernel_rooflines("mixed", st, 32, 2070.0, "fp32x2")
+    assert k["solve"]["algorithmic"] == 432 * W["batch"] * P * bench.rows_of(W["N"])
+    assert abs(k["solve"]["peak"] - 152 * 128 * 2070e6 / 1e12) < 1e-12
+    assert k["solve"]["unit"] == "Tops/s" and k["reduce"]["unit"] == "GB/s"
+    ns = (W["N"] + 1) * (W["N"] + 2) // 2
+    assert k["reduce"]["algorithmic"] == 34 * 3 * ns * W["batch"] * 16
+    assert [f[0] for f in bench.FORMS] == ["mixed_fp32x2", "mixed", "fp64"]
     assert bench.rows_of(341) == 58652
