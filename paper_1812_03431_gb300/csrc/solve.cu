@@ -295,17 +295,8 @@ __device__ __forceinline__ void sweep_poles(const SolveView &a, const int (&k)[K
 // FP32 rate, so the solve runs on the FP32 pipes at 48-bit significand precision.
 __device__ __forceinline__ float4 ldf(const float4 *p) { return __ldg(p); }
 
-// Loads of one forward row: the three states and the four factors of each pole.
-template <int KC>
-struct FwdRow {
-  float4 zn, d0, p0, g[KC], e[KC], f[KC], l[KC];
-};
-// Loads of one backward row: the sweep intermediates, the five factors of each pole
-// and the three slot partials.
-template <int KC>
-struct BwdRow {
-  float4 y[KC], c[KC], bd[KC], bad[KC], zp[KC], zm[KC], accD, accP, accZ;
-};
+// bring the line holding p into L2 (no register result, no wait)
+__device__ __forceinline__ void l2_prefetch(const void *p) { asm volatile("prefetch.global.L2 [%0];" : : "l"(p)); }
 
 template <int KC>
 __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k)[KC], int n0, int len, int nmin,
@@ -313,109 +304,110 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
                                                const float4 *sZeta, const float4 *sDel, float4 *pPhi,
                                                float4 *pZeta, float4 *pDel, int64_t rstride, bool first,
                                                float4 *ybuf) {
+  constexpr int D = 3;  // rows prefetched ahead into L2
   const int64_t RS = (int64_t)a.P * F_NCOMP;  // row stride of the interleaved factors
   const int N = a.N, B = a.B;
   // factor (comp, row i, pole c) at fk[c] + i RS + comp
   const float4 *fk[KC];
   for (int c = 0; c < KC; ++c) fk[c] = reinterpret_cast<const float4 *>(a.fac) + (row0 * a.P + k[c]) * F_NCOMP;
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  // Every row's loads are issued one row ahead (into registers), so that their latency
-  // overlaps the previous row's arithmetic.
-  auto load_fwd = [&](int i, FwdRow<KC> &r) {
+  // Every row's data (states, factors, sweep intermediates, slot partials) is prefetched
+  // into L2 D rows ahead, so that the row's own loads find it there; the prefetches hold
+  // no registers (a register prefetch of the next row needed 168 registers per thread,
+  // this kernel 128, i.e. four CTAs per SM instead of three).
+  auto pf_fwd = [&](int i) {
     const int n = n0 + 2 * i;
     const int64_t ix = base_idx + n;
-    r.zn = (n + 1 <= N) ? ldf(sZeta + (ix + 1) * B) : zero;
-    r.d0 = ldf(sDel + ix * B);
-    r.p0 = ldf(sPhi + ix * B);
+    if (n + 1 <= N) l2_prefetch(sZeta + (ix + 1) * B);
+    l2_prefetch(sDel + ix * B);
+    l2_prefetch(sPhi + ix * B);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {  // factors 0..3 of the 144-byte record: at most two lines
+      const float4 *f = fk[c] + (int64_t)i * RS;
+      l2_prefetch(f);
+      l2_prefetch(f + 3);
+    }
+  };
+  auto pf_bwd = [&](int i) {
+    const int n = n0 + 2 * i;
+    const int64_t ix = base_idx + n;
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      const float4 *f = fk[c] + (int64_t)i * RS;
-      r.g[c] = ldf(f + F_G);
-      r.e[c] = ldf(f + F_E);
-      r.f[c] = ldf(f + F_F);
-      r.l[c] = ldf(f + F_L);
+      const float4 *f = fk[c] + (int64_t)i * RS;  // factors 4..8
+      l2_prefetch(f + 4);
+      l2_prefetch(f + 8);
+      l2_prefetch(ybuf + ((int64_t)i * KC + c) * 32);
+    }
+    if (!first) {
+      l2_prefetch(pDel + ix * rstride);
+      l2_prefetch(pPhi + ix * rstride);
+      if (n + 1 <= N) l2_prefetch(pZeta + (ix + 1) * rstride);
     }
   };
   // ---- forward sweep: y_i = delta0 - g Phi0 - e zeta0_{n-1} - f zeta0_{n+1} - l y_{i-1}
   float4 yprev[KC];
   for (int c = 0; c < KC; ++c) yprev[c] = zero;
   float4 zprev = (n0 - 1 >= nmin) ? ldf(sZeta + (base_idx + n0 - 1) * B) : zero;
-  FwdRow<KC> cur;
-  load_fwd(0, cur);
+  for (int j = 1; j <= D && j < len; ++j) pf_fwd(j);
   for (int i = 0; i < len; ++i) {
-    FwdRow<KC> nxt;
-    load_fwd(i + 1 < len ? i + 1 : i, nxt);
+    if (i + D < len) pf_fwd(i + D);
+    const int n = n0 + 2 * i;
+    const int64_t ix = base_idx + n;
+    const float4 zn = (n + 1 <= N) ? ldf(sZeta + (ix + 1) * B) : zero;
+    const float4 d0 = ldf(sDel + ix * B), p0 = ldf(sPhi + ix * B);
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      ff::CAcc y = ff::cacc(cur.d0);
-      ff::cmsub(y, cur.g[c], cur.p0);
-      ff::cmsub(y, cur.e[c], zprev);
-      ff::cmsub(y, cur.f[c], cur.zn);
-      ff::cmsub(y, cur.l[c], yprev[c]);
+      const float4 *f = fk[c] + (int64_t)i * RS;
+      ff::CAcc y = ff::cacc(d0);
+      ff::cmsub(y, ldf(f + F_G), p0);
+      ff::cmsub(y, ldf(f + F_E), zprev);
+      ff::cmsub(y, ldf(f + F_F), zn);
+      ff::cmsub(y, ldf(f + F_L), yprev[c]);
       const float4 yv = ff::raw(y);
       ybuf[((int64_t)i * KC + c) * 32] = yv;
       yprev[c] = yv;
     }
-    zprev = cur.zn;
-    cur = nxt;
+    zprev = zn;
   }
   // ---- backward sweep with the beta-weighted accumulation (as in sweep_poles)
-  auto load_bwd = [&](int i, BwdRow<KC> &r) {
-    const int n = n0 + 2 * i;
-    const int64_t ix = base_idx + n;
-#pragma unroll
-    for (int c = 0; c < KC; ++c) {
-      const float4 *f = fk[c] + (int64_t)i * RS;
-      r.y[c] = ybuf[((int64_t)i * KC + c) * 32];
-      r.c[c] = ldf(f + F_C);
-      r.bd[c] = ldf(f + F_BD);
-      r.bad[c] = ldf(f + F_BAD);
-      r.zp[c] = ldf(f + F_ZP);
-      r.zm[c] = ldf(f + F_ZM);
-    }
-    r.accD = first ? zero : pDel[ix * rstride];
-    r.accP = first ? zero : pPhi[ix * rstride];
-    r.accZ = (first || n + 1 > N) ? zero : pZeta[(ix + 1) * rstride];
-  };
   float4 wnext[KC], zmnext[KC];
   for (int c = 0; c < KC; ++c) wnext[c] = zmnext[c] = zero;
-  BwdRow<KC> bc;
-  load_bwd(len - 1, bc);
+  for (int j = len - 2; j >= 0 && j >= len - 1 - D; --j) pf_bwd(j);
   for (int i = len - 1; i >= 0; --i) {
+    if (i - D >= 0) pf_bwd(i - D);
     const int n = n0 + 2 * i;
     const int64_t ix = base_idx + n;
-    BwdRow<KC> bn;
-    load_bwd(i > 0 ? i - 1 : i, bn);
     float4 wv[KC];
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      ff::CAcc w = ff::cacc(bc.y[c]);
-      ff::cmsub(w, bc.c[c], wnext[c]);
+      ff::CAcc w = ff::cacc(ybuf[((int64_t)i * KC + c) * 32]);
+      ff::cmsub(w, ldf(fk[c] + (int64_t)i * RS + F_C), wnext[c]);
       wv[c] = ff::raw(w);
     }
-    ff::CAcc accD = ff::cacc(bc.accD), accP = ff::cacc(bc.accP);
+    ff::CAcc accD = first ? ff::czero() : ff::cacc(pDel[ix * rstride]);
+    ff::CAcc accP = first ? ff::czero() : ff::cacc(pPhi[ix * rstride]);
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      ff::cmac(accD, bc.bd[c], wv[c]);
-      ff::cmac(accP, bc.bad[c], wv[c]);
+      const float4 *f = fk[c] + (int64_t)i * RS;
+      ff::cmac(accD, ldf(f + F_BD), wv[c]);
+      ff::cmac(accP, ldf(f + F_BAD), wv[c]);
     }
     pDel[ix * rstride] = ff::raw(accD);
     pPhi[ix * rstride] = ff::raw(accP);
     if (n + 1 <= N) {
-      ff::CAcc accZ = ff::cacc(bc.accZ);
+      ff::CAcc accZ = first ? ff::czero() : ff::cacc(pZeta[(ix + 1) * rstride]);
 #pragma unroll
       for (int c = 0; c < KC; ++c) {
-        ff::cmac(accZ, bc.zp[c], wv[c]);
+        ff::cmac(accZ, ldf(fk[c] + (int64_t)i * RS + F_ZP), wv[c]);
         ff::cmac(accZ, zmnext[c], wnext[c]);
       }
       pZeta[(ix + 1) * rstride] = ff::raw(accZ);
     }
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      zmnext[c] = bc.zm[c];
+      zmnext[c] = ldf(fk[c] + (int64_t)i * RS + F_ZM);
       wnext[c] = wv[c];
     }
-    bc = bn;
   }
   if (n0 - 1 >= nmin) {
     const int64_t ix = base_idx + n0 - 1;
