@@ -21,11 +21,12 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def test_t1279_spectral_step_sampled_orders():
+@pytest.mark.parametrize("arith", ["fp64", "fp32x2"])
+def test_t1279_spectral_step_sampled_orders(arith):
     import torch
     from paper_1812_03431_gb300 import rexi
     al, be, _ = rc.rexi_coefficients(M, 0.2)
-    plan = rexi.Plan(N, NLAT, NLON, tau=TAU, layout="spectral", alpha=al, beta=be)
+    plan = rexi.Plan(N, NLAT, NLON, tau=TAU, layout="spectral", alpha=al, beta=be, solve_arith=arith)
     S = inputs.random_spectral(N, 1, 1004)
     got = plan.step(torch.from_numpy(S).cuda()).cpu().numpy()
     plan.close()
@@ -37,18 +38,22 @@ def test_t1279_spectral_step_sampled_orders():
 
 
 def test_t1279_mixed_vs_fp64_grid_step():
-    """T1279 on 3840x1920, K=512: 3xTF32 Legendre + FP32 FFTs vs all-FP64, same poles, one state."""
+    """T1279 on 3840x1920, K=512: 3xTF32 Legendre + FP32 FFTs (with binary64 and with
+    float-float solves) vs all-FP64, same poles, one state."""
     import torch
     from paper_1812_03431_gb300 import rexi
     S = torch.from_numpy(inputs.random_spectral(N, 1, 1004)).cuda()
     out = {}
-    for prec in ("fp64", "mixed"):
-        plan = rexi.Plan(N, NLAT, NLON, M=M, tau=TAU, precision=prec)
+    for prec, arith in (("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "fp32x2")):
+        plan = rexi.Plan(N, NLAT, NLON, M=M, tau=TAU, precision=prec, solve_arith=arith)
         x = plan.synthesize(S) if prec == "fp64" else x
-        out[prec] = plan.step(x).cpu().numpy()
+        out[prec, arith] = plan.step(x).cpu().numpy()
         plan.check_device()
         plan.close()
         torch.cuda.empty_cache()
-    err = rel(out["mixed"], out["fp64"])
-    print("T1279 mixed vs FP64 relative L2:", err)
-    assert err < 1e-5
+    err = rel(out["mixed", "fp64"], out["fp64", "fp64"])
+    err2 = rel(out["mixed", "fp32x2"], out["fp64", "fp64"])
+    d = rel(out["mixed", "fp32x2"], out["mixed", "fp64"])
+    print("T1279 vs FP64, relative L2: mixed %.3e, mixed with float-float solves %.3e (%.1e from binary64 solves)"
+          % (err, err2, d))
+    assert err < 1e-5 and err2 < 1e-5 and d < 1e-10
