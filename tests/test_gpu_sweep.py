@@ -1,5 +1,6 @@
 """Seeded sweep over plan configurations (truncation, grid, poles, batch, layout, precision,
-solver, f-sphere) against the oracle, to catch indexing slips that fixed cases miss."""
+solver, f-sphere, solve arithmetic) against the oracle, to catch indexing slips that fixed
+cases miss."""
 import numpy as np
 import pytest
 
@@ -22,6 +23,7 @@ def smooth(n):
 
 def configs(count=48, seed=4242):
     rng = np.random.default_rng(seed)
+    rng_arith = np.random.default_rng(seed + 1)  # a separate stream: the other draws stay as they were
     out = []
     while len(out) < count:
         N = int(rng.integers(1, 48))
@@ -37,7 +39,10 @@ def configs(count=48, seed=4242):
         precision = str(rng.choice(["fp64", "mixed"])) if layout == "grid" else "fp64"
         kind = str(rng.choice(["delta", "delta", "phi", "fsphere"]))
         tau = float(rng.choice([600.0, 1800.0, 3600.0, 7200.0]))
-        out.append((N, nlat, nlon, M, B, layout, precision, kind, tau))
+        arith = str(rng_arith.choice(["fp64", "fp32x2"]))
+        if kind != "delta":
+            arith = "fp64"  # float-float solves serve the delta elimination on the rotating sphere
+        out.append((N, nlat, nlon, M, B, layout, precision, kind, tau, arith))
     return out
 
 
@@ -45,16 +50,16 @@ def relerr(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("cfg", configs(), ids=lambda c: "N%d_%dx%d_M%d_B%d_%s_%s_%s" % (c[0], c[2], c[1], c[3], c[4],
-                                                                                        c[5], c[6], c[7]))
+@pytest.mark.parametrize("cfg", configs(), ids=lambda c: "N%d_%dx%d_M%d_B%d_%s_%s_%s_%s" % (
+    c[0], c[2], c[1], c[3], c[4], c[5], c[6], c[7], c[9]))
 def test_sweep(cfg):
     import torch
     from paper_1812_03431_gb300 import rexi
-    N, nlat, nlon, M, B, layout, precision, kind, tau = cfg
+    N, nlat, nlon, M, B, layout, precision, kind, tau, arith = cfg
     al, be, _ = rc.rexi_coefficients(M, 0.2)
     S = inputs.random_spectral(N, B, 900 + N + B)
     plan = rexi.Plan(N, nlat, nlon, tau=tau, max_batch=B, layout=layout, precision=precision, alpha=al, beta=be,
-                     solver="phi" if kind == "phi" else "delta", fsphere=kind == "fsphere")
+                     solver="phi" if kind == "phi" else "delta", fsphere=kind == "fsphere", solve_arith=arith)
 
     def spectral_ref(X):
         if kind == "phi":
