@@ -401,11 +401,15 @@ def main():
                              solve_arith=arith)
         plan.close()
 
-    # the paper's geopotential-only solver on the same workload (FP64 form), for comparison
-    phi = None
-    if not args.no_phi_solver and "fp64" in results:
+    # the paper's geopotential-only solver on the same workload, for comparison: in the
+    # plain FP64 form, and in the chosen form's arithmetic (mixed transforms, float-float solves)
+    phi = {}
+    phi_forms = [("fp64", "fp64", "fp64"), ("mixed_fp32x2", "mixed", "fp32x2")]
+    for name, prec, arith in phi_forms if not args.no_phi_solver else []:
+        if name not in results:
+            continue
         plan = rexi.Plan(W["N"], W["nlat"], W["nlon"], M=W["M"], h=W["h"], tau=W["tau"], max_batch=B,
-                         precision="fp64", solver="phi")
+                         precision=prec, solver="phi", solve_arith=arith)
         pslots = plan.tune(B)
         x = plan.synthesize(S)
         y = torch.empty_like(x)
@@ -423,12 +427,13 @@ def main():
         torch.cuda.synchronize()
         pms = replica_max_ms(e0.elapsed_time(e1) / args.steps, dist)
         stages, ncalls = plan.profile_read()
-        f = results["fp64"]["y"]
-        phi = {"value": world * 1e3 / pms, "ms_per_step": pms, "pole_slots": pslots,
-               "stage_ms": {k: v / max(ncalls, 1) for k, v in stages.items()},
-               "difference_vs_delta_form": float((y - f).norm() / f.norm()),
-               "note": "REXI_SOLVER_PHI: the paper's Phi-only system (Sec. 4.3, 5), pentadiagonal per "
-                       "(pole, m, parity); a different truncation, so it differs at the highest degrees"}
+        f = results[name]["y"]
+        phi[name] = {"value": world * 1e3 / pms, "ms_per_step": pms, "pole_slots": pslots,
+                     "stage_ms": {k: v / max(ncalls, 1) for k, v in stages.items()},
+                     "difference_vs_delta_form": float((y - f).norm() / f.norm()),
+                     "note": "REXI_SOLVER_PHI: the paper's Phi-only system (Sec. 4.3, 5), pentadiagonal per "
+                             "(pole, m, parity); a different truncation, so it differs from the delta "
+                             "elimination at the highest degrees; compared with the %s form" % name}
         plan.close()
 
     chosen = forms[0][0]
@@ -485,8 +490,10 @@ def main():
         y = results[chosen]["y"]
         line["vs_mixed_fp64_solves"] = {"rel_l2": float((y - f).norm() / f.norm()),
                                         "bitwise_equal": bool(torch.equal(y, f))}
-    if phi is not None:
-        line["phi_solver_form"] = phi
+    if "fp64" in phi:
+        line["phi_solver_form"] = phi["fp64"]
+    if "mixed_fp32x2" in phi:
+        line["phi_solver_chosen_form"] = phi["mixed_fp32x2"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
         try:

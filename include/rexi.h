@@ -93,7 +93,7 @@ enum { REXI_SOLVE_FP64 = 0,    /* banded solves and pole sum in binary64 (defaul
                                   binary64.  Values must lie in binary32's range: magnitudes
                                   above ~3e38 overflow and below ~1e-31 lose relative precision
                                   (the SWE states and factors of Sec. 6 are within 1e-20 .. 1e6).
-                                  REXI_SOLVER_DELTA on the rotating sphere only. */
+                                  Either solver, on the rotating sphere only. */
 
 typedef struct rexi_plan rexi_plan;
 typedef struct rexi_ragged rexi_ragged;

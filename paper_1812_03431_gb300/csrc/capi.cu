@@ -297,9 +297,9 @@ rexi_status rexi_plan_create(const rexi_params *prm, rexi_plan **out) {
     return REXI_EINVAL;
   }
   if ((p.solve_arith != REXI_SOLVE_FP64 && p.solve_arith != REXI_SOLVE_FP32X2) ||
-      (p.solve_arith == REXI_SOLVE_FP32X2 && (p.solver != REXI_SOLVER_DELTA || p.fsphere))) {
-    set_error("rexi_plan_create: solve_arith must be REXI_SOLVE_FP64 or REXI_SOLVE_FP32X2 (the latter with "
-              "REXI_SOLVER_DELTA on the rotating sphere)");
+      (p.solve_arith == REXI_SOLVE_FP32X2 && p.fsphere)) {
+    set_error("rexi_plan_create: solve_arith must be REXI_SOLVE_FP64 or REXI_SOLVE_FP32X2 (the latter on the "
+              "rotating sphere)");
     return REXI_EINVAL;
   }
   Plan *pl = new Plan();

@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "ff.h"
 #include "rexi_internal.h"
 
 namespace rexi {
@@ -73,10 +74,12 @@ struct PhiSetupArgs {
   const double *zc;    // [nspec][12] Z2(-2, 0, +2), Z3(-4 .. +4), Z6(-2, 0, +2)
   const double2 *alpha, *beta;
   double2 *fac;        // [7][nrows][P]: l1, l2, u1, u2, 1/u0, zeta weights zp, zm
+                       // (float-float plans: [nrows][P][7], converted after this kernel)
   const int4 *sys;     // per (m, p): {m, n0, len, row0}
   int nsys, P, N;
   int64_t nrows;
   PhiConsts c;
+  int interleaved;
 };
 
 __global__ void phi_factor_kernel(PhiSetupArgs a) {
@@ -104,7 +107,9 @@ __global__ void phi_factor_kernel(PhiSetupArgs a) {
   auto lap = [&](int n) { return -(double)n * (n + 1.0) / a2; };
   const int64_t base = base_of(N, m);
   const int64_t NR = a.nrows, P = a.P;
-  auto put = [&](int comp, int64_t row, double2 v) { a.fac[((int64_t)comp * NR + row) * P + k] = v; };
+  auto put = [&](int comp, int64_t row, double2 v) {
+    a.fac[a.interleaved ? (row * P + k) * 7 + comp : ((int64_t)comp * NR + row) * P + k] = v;
+  };
   const double2 zero = make_double2(0, 0), one = make_double2(1, 0);
   const double2 bal = cmul(be, al);
   const double wz = c.q / (c.tau * pb);
@@ -155,11 +160,12 @@ __global__ void phi_factor_kernel(PhiSetupArgs a) {
 // ---- per step: the pole-independent right-hand-side coefficients Q_p -------------------
 struct PhiRhsArgs {
   const double2 *sin;  // [3][nspec][B]
-  double2 *q;          // [5][nspec][B]  Q0 .. Q4
+  double2 *q;          // [5][nspec][B]  Q0 .. Q4 (float-float plans: float-float values)
   const int32_t *m_of;
   int N, B;
   int64_t nspec;
   PhiConsts c;
+  int ff;
 };
 
 __device__ __forceinline__ double eps_nm(int n, int m) {
@@ -265,13 +271,18 @@ __global__ void phi_rhs_kernel(PhiRhsArgs a) {
     Q[0] = cadd(cadd(cscale(m4p, t4 * F * F * F * F), cscale(m3z, -t4 * pb * F * F * F)),
                 cscale(m2U, -t4 * pb * F * F * g));
 #pragma unroll
-    for (int p = 0; p < 5; ++p) a.q[((int64_t)p * a.nspec + ix) * B + b] = Q[p];
+    for (int p = 0; p < 5; ++p) {
+      const int64_t o = ((int64_t)p * a.nspec + ix) * B + b;
+      if (a.ff) reinterpret_cast<float4 *>(a.q)[o] = ff::csplit(Q[p]);
+      else a.q[o] = Q[p];
+    }
   }
 }
 
 // ---- per step: the pentadiagonal solves and the beta-weighted sums --------------------
 struct PhiSolveArgs {
   const double2 *fac, *q, *alpha, *beta;
+  const float4 *abf;  // float-float plans: alpha, beta, beta alpha per pole ([3][P])
   double2 *part;  // [3][nspec][slots][B]: (sum beta Phi, zeta couplings, sum beta alpha Phi)
   const int4 *sys;
   double2 *ybuf;
@@ -378,6 +389,137 @@ __device__ __forceinline__ void phi_sweep(const PhiSolveArgs &a, const int (&k)[
   }
 }
 
+// The same sweeps in float-float arithmetic (ff.h) on the FP32 pipes: factors
+// [nrows][P][7], right-hand-side coefficients, sweep intermediates and slot partials
+// hold float-float values in their double2 slots; each row's data is prefetched into
+// L2 three rows ahead.
+__device__ __forceinline__ void l2_prefetch(const void *p) { asm volatile("prefetch.global.L2 [%0];" : : "l"(p)); }
+
+template <int KC>
+__device__ __forceinline__ void phi_sweep_ff(const PhiSolveArgs &a, const int (&k)[KC], int m, int n0, int len,
+                                             int64_t row0, int64_t base, const float4 *qb, float4 *pP, float4 *pZ,
+                                             float4 *pD, int64_t rstride, bool first, float4 *ybuf) {
+  constexpr int D = 3;  // rows prefetched ahead into L2
+  const int64_t NS = a.nspec, RS = (int64_t)a.P * 7;
+  const int N = a.N, B = a.B;
+  float4 al[KC], be[KC], bal[KC];
+  const float4 *fk[KC];  // factor (comp, row i, pole c) at fk[c] + i RS + comp
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    al[c] = a.abf[k[c]];
+    be[c] = a.abf[a.P + k[c]];
+    bal[c] = a.abf[2 * a.P + k[c]];
+    fk[c] = reinterpret_cast<const float4 *>(a.fac) + (row0 * a.P + k[c]) * 7;
+  }
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto pf_fwd = [&](int i) {
+    const int64_t ix = base + n0 + 2 * i;
+#pragma unroll
+    for (int p = 0; p < 5; ++p) l2_prefetch(qb + ((int64_t)p * NS + ix) * B);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) l2_prefetch(fk[c] + (int64_t)i * RS + 1);
+  };
+  auto pf_bwd = [&](int i) {
+    const int n = n0 + 2 * i;
+    const int64_t ix = base + n;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      const float4 *f = fk[c] + (int64_t)i * RS;  // factors 2..6
+      l2_prefetch(f + 2);
+      l2_prefetch(f + 6);
+      l2_prefetch(ybuf + ((int64_t)i * KC + c) * 32);
+    }
+    if (!first) {
+      l2_prefetch(pP + ix * rstride);
+      l2_prefetch(pD + ix * rstride);
+      if (n + 1 <= N) l2_prefetch(pZ + (ix + 1) * rstride);
+    }
+  };
+  // forward: y_i = rhs_i - l1 y_{i-1} - l2 y_{i-2},  rhs = (((Q4 a + Q3) a + Q2) a + Q1) a + Q0
+  float4 y1[KC], y2[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) y1[c] = y2[c] = zero;
+  for (int j = 1; j <= D && j < len; ++j) pf_fwd(j);
+  for (int i = 0; i < len; ++i) {
+    if (i + D < len) pf_fwd(i + D);
+    const int64_t ix = base + n0 + 2 * i;
+    float4 Q[5];
+#pragma unroll
+    for (int p = 0; p < 5; ++p) Q[p] = __ldg(qb + ((int64_t)p * NS + ix) * B);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      const float4 *f = fk[c] + (int64_t)i * RS;
+      ff::CAcc r = ff::cacc(Q[3]);
+      ff::cmac(r, Q[4], al[c]);
+#pragma unroll
+      for (int p = 2; p >= 0; --p) {
+        ff::CAcc r2 = ff::cacc(Q[p]);
+        ff::cmac(r2, ff::raw(r), al[c]);
+        r = r2;
+      }
+      ff::cmsub(r, __ldg(f + 0), y1[c]);
+      ff::cmsub(r, __ldg(f + 1), y2[c]);
+      const float4 yv = ff::raw(r);
+      ybuf[((int64_t)i * KC + c) * 32] = yv;
+      y2[c] = y1[c];
+      y1[c] = yv;
+    }
+  }
+  // backward: x_i = (y_i - u1 x_{i+1} - u2 x_{i+2}) / u0, with the sums
+  float4 x1[KC], x2[KC], zmn[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) x1[c] = x2[c] = zmn[c] = zero;
+  for (int j = len - 2; j >= 0 && j >= len - 1 - D; --j) pf_bwd(j);
+  for (int i = len - 1; i >= 0; --i) {
+    if (i - D >= 0) pf_bwd(i - D);
+    const int n = n0 + 2 * i;
+    const int64_t ix = base + n;
+    float4 xv[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      const float4 *f = fk[c] + (int64_t)i * RS;
+      ff::CAcc r = ff::cacc(ybuf[((int64_t)i * KC + c) * 32]);
+      ff::cmsub(r, __ldg(f + 2), x1[c]);
+      ff::cmsub(r, __ldg(f + 3), x2[c]);
+      ff::CAcc x = ff::czero();
+      ff::cmac(x, ff::raw(r), __ldg(f + 4));
+      xv[c] = ff::raw(x);
+    }
+    ff::CAcc accP = first ? ff::czero() : ff::cacc(pP[ix * rstride]);
+    ff::CAcc accD = first ? ff::czero() : ff::cacc(pD[ix * rstride]);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      ff::cmac(accP, be[c], xv[c]);
+      ff::cmac(accD, bal[c], xv[c]);
+    }
+    pP[ix * rstride] = ff::raw(accP);
+    pD[ix * rstride] = ff::raw(accD);
+    if (n + 1 <= N) {
+      ff::CAcc accZ = first ? ff::czero() : ff::cacc(pZ[(ix + 1) * rstride]);
+#pragma unroll
+      for (int c = 0; c < KC; ++c) {
+        ff::cmac(accZ, __ldg(fk[c] + (int64_t)i * RS + 5), xv[c]);
+        ff::cmac(accZ, zmn[c], x1[c]);
+      }
+      pZ[(ix + 1) * rstride] = ff::raw(accZ);
+    }
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      zmn[c] = __ldg(fk[c] + (int64_t)i * RS + 6);
+      x2[c] = x1[c];
+      x1[c] = xv[c];
+    }
+  }
+  if (n0 - 1 >= m) {
+    const int64_t ix = base + n0 - 1;
+    ff::CAcc accZ = first ? ff::czero() : ff::cacc(pZ[ix * rstride]);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) ff::cmac(accZ, zmn[c], x1[c]);
+    pZ[ix * rstride] = ff::raw(accZ);
+  }
+}
+
+template <bool FF>
 __global__ void __launch_bounds__(128) phi_solve_kernel(PhiSolveArgs a) {
   const int lane = threadIdx.x & 31;
   const int wslot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -406,14 +548,29 @@ __global__ void __launch_bounds__(128) phi_solve_kernel(PhiSolveArgs a) {
     const double2 *qb = a.q + b;
     bool first = true;
     int k0 = slot;
-    for (; k0 + Sm < a.P; k0 += 2 * Sm) {
-      const int kp[2] = {k0, k0 + Sm};
-      phi_sweep<2>(a, kp, m, n0, len, sy.w, base, qb, pP, pZ, pD, rstride, first, ybuf);
-      first = false;
-    }
-    if (k0 < a.P) {
-      const int kp[1] = {k0};
-      phi_sweep<1>(a, kp, m, n0, len, sy.w, base, qb, pP, pZ, pD, rstride, first, ybuf);
+    if constexpr (FF) {
+      const float4 *fq = reinterpret_cast<const float4 *>(qb);
+      float4 *fP = reinterpret_cast<float4 *>(pP), *fZ = reinterpret_cast<float4 *>(pZ),
+             *fD = reinterpret_cast<float4 *>(pD), *fy = reinterpret_cast<float4 *>(ybuf);
+      for (; k0 + Sm < a.P; k0 += 2 * Sm) {
+        const int kp[2] = {k0, k0 + Sm};
+        phi_sweep_ff<2>(a, kp, m, n0, len, sy.w, base, fq, fP, fZ, fD, rstride, first, fy);
+        first = false;
+      }
+      if (k0 < a.P) {
+        const int kp[1] = {k0};
+        phi_sweep_ff<1>(a, kp, m, n0, len, sy.w, base, fq, fP, fZ, fD, rstride, first, fy);
+      }
+    } else {
+      for (; k0 + Sm < a.P; k0 += 2 * Sm) {
+        const int kp[2] = {k0, k0 + Sm};
+        phi_sweep<2>(a, kp, m, n0, len, sy.w, base, qb, pP, pZ, pD, rstride, first, ybuf);
+        first = false;
+      }
+      if (k0 < a.P) {
+        const int kp[1] = {k0};
+        phi_sweep<1>(a, kp, m, n0, len, sy.w, base, qb, pP, pZ, pD, rstride, first, ybuf);
+      }
     }
   }
 }
@@ -433,6 +590,7 @@ struct PhiReduceArgs {
   double inv_tp, qz;      // 1 / (tau Phibar), 2 Omega tau / (tau Phibar)
 };
 
+template <bool FF>
 __global__ void phi_reduce_kernel(PhiReduceArgs a) {
   const int64_t total = 3 * a.nspec * a.B;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -445,17 +603,24 @@ __global__ void phi_reduce_kernel(PhiReduceArgs a) {
     double2 acc = make_double2(0, 0);
     if (!(fl & 2)) {
       if (fl & 1) {
-        const double2 *p = a.part + fi * a.slots * a.B + b;
         const int Sm = a.slots_m[a.m_of[ix]];
-        int s = 0;
-        for (; s + 8 <= Sm; s += 8) {
-          double2 v[8];
+        if constexpr (FF) {  // float-float partials added in slot order, rounded once
+          const float4 *p = reinterpret_cast<const float4 *>(a.part) + fi * a.slots * a.B + b;
+          ff::CAcc fa = ff::czero();
+          for (int s = 0; s < Sm; ++s) ff::cadd(fa, __ldcs(p + (int64_t)s * a.B));
+          acc = make_double2(f32_to_f64(fa.re.s) + f32_to_f64(fa.re.e), f32_to_f64(fa.im.s) + f32_to_f64(fa.im.e));
+        } else {
+          const double2 *p = a.part + fi * a.slots * a.B + b;
+          int s = 0;
+          for (; s + 8 <= Sm; s += 8) {
+            double2 v[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + (int64_t)(s + u) * a.B);
+            for (int u = 0; u < 8; ++u) v[u] = __ldcs(p + (int64_t)(s + u) * a.B);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) acc = cadd(acc, v[u]);
+            for (int u = 0; u < 8; ++u) acc = cadd(acc, v[u]);
+          }
+          for (; s < Sm; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
         }
-        for (; s < Sm; ++s) acc = cadd(acc, p[(int64_t)s * a.B]);
       }
       const int64_t NB = a.nspec * a.B;
       const int64_t sb = ix * a.B + b;
@@ -498,16 +663,19 @@ cudaError_t launch_phi_factor(Plan &pl, cudaStream_t st) {
   a.N = pl.N;
   a.nrows = pl.nrows;
   a.c = phi_consts(pl);
+  a.interleaved = pl.ff ? 1 : 0;
   const int64_t total = (int64_t)a.P * a.nsys;
   phi_factor_kernel<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(a);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && pl.ff) e = launch_to_ff(pl, pl.fac_fwd, (int64_t)7 * pl.nrows * pl.P, st);
+  return e;
 }
 
 // right-hand sides Q_p, then the persistent pentadiagonal solve into the slot partials
 cudaError_t launch_phi_solve(Plan &pl, const SolveLayout &lay, const double2 *sin, int B, cudaStream_t st) {
   const PhiConsts c = phi_consts(pl);
   {
-    PhiRhsArgs r{sin, pl.phi_q, pl.m_of_dev, pl.N, B, pl.nspec, c};
+    PhiRhsArgs r{sin, pl.phi_q, pl.m_of_dev, pl.N, B, pl.nspec, c, pl.ff ? 1 : 0};
     const int64_t total = pl.nspec * B;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 127) / 128, (int64_t)pl.num_sms * 16));
     phi_rhs_kernel<<<blocks, 128, 0, st>>>(r);
@@ -520,6 +688,7 @@ cudaError_t launch_phi_solve(Plan &pl, const SolveLayout &lay, const double2 *si
     s.q = pl.phi_q;
     s.alpha = pl.alpha_dev;
     s.beta = pl.beta_dev;
+    s.abf = reinterpret_cast<const float4 *>(pl.phi_abf);
     s.part = pl.partial;
     s.sys = pl.sys_dev;
     s.ybuf = pl.yscratch;
@@ -538,7 +707,8 @@ cudaError_t launch_phi_solve(Plan &pl, const SolveLayout &lay, const double2 *si
     s.nrows = pl.nrows;
     cudaError_t e = cudaMemsetAsync(pl.counter, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    phi_solve_kernel<<<pl.resident_warps / 4, 128, 0, st>>>(s);
+    if (pl.ff) phi_solve_kernel<true><<<pl.resident_warps / 4, 128, 0, st>>>(s);
+    else phi_solve_kernel<false><<<pl.resident_warps / 4, 128, 0, st>>>(s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -566,7 +736,8 @@ cudaError_t launch_phi_reduce(Plan &pl, const SolveLayout &lay, const double2 *s
   r.qz = c.q / (c.tau * c.phibar);
   const int64_t total = 3 * pl.nspec * B;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)pl.num_sms * 8);
-  phi_reduce_kernel<<<blocks, 256, 0, st>>>(r);
+  if (pl.ff) phi_reduce_kernel<true><<<blocks, 256, 0, st>>>(r);
+  else phi_reduce_kernel<false><<<blocks, 256, 0, st>>>(r);
   return cudaGetLastError();
 }
 

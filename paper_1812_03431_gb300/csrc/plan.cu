@@ -272,6 +272,23 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
     if ((e = dalloc(&pl->fac_fwd, nfac, &bytes))) return fail("factors", e);
     if ((e = launch_phi_factor(*pl, 0))) return fail("factor setup", e);
     if ((e = dalloc(&pl->phi_q, (size_t)5 * NS * prm.max_batch, &bytes))) return fail("phi rhs", e);
+    if (pl->ff) {  // alpha, beta and beta alpha as float-float values (hi = fl32(x), lo = fl32(x - hi))
+      auto split = [](double x) {
+        const float hi = (float)x;
+        return std::make_pair(hi, (float)(x - (double)hi));
+      };
+      std::vector<float4> abf(3 * (size_t)P);
+      for (int k = 0; k < P; ++k) {
+        const cplx v[3] = {pl->alpha[k], pl->beta[k], pl->beta[k] * pl->alpha[k]};
+        for (int j = 0; j < 3; ++j) {
+          const auto re = split(v[j].real()), im = split(v[j].imag());
+          abf[(size_t)j * P + k] = make_float4(re.first, re.second, im.first, im.second);
+        }
+      }
+      float4 *d = nullptr;
+      if ((e = upload(&d, abf, &bytes))) return fail("phi poles", e);
+      pl->phi_abf = reinterpret_cast<double2 *>(d);
+    }
   } else if (!prm.fsphere) {
     const size_t nfac = (size_t)F_NCOMP * pl->nrows * P;
     if ((e = dalloc(&pl->fac_fwd, nfac, &bytes))) return fail("factors", e);
@@ -564,7 +581,7 @@ void free_plan(Plan *pl) {
                   pl->scale_syn_out, pl->mscale_fwd, pl->mscale_c, pl->mscale_adj, pl->mscale_one,
                   pl->zd_syn, pl->zd_ana_adj, pl->zd_one, pl->zd_mone, pl->fft.tw_dev, pl->fft.tw32_dev, pl->four,
                   pl->s_in, pl->s_out, pl->s_ff, pl->partial, pl->yscratch, pl->counter, pl->tc_tab_ana,
-                  pl->tc_tab_syn, pl->tc_work_ana, pl->tc_work_syn, pl->dev_err, pl->phi_zc, pl->phi_q};
+                  pl->tc_tab_syn, pl->tc_work_ana, pl->tc_work_syn, pl->dev_err, pl->phi_zc, pl->phi_q, pl->phi_abf};
   for (cudaEvent_t ev : pl->prof_ev) cudaEventDestroy(ev);
   for (void *p : ptrs)
     if (p) cudaFree(p);

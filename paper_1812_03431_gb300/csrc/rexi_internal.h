@@ -161,6 +161,7 @@ struct Plan {
   // sum of the beta_k; its factors [7][nrows][P] live in fac_fwd
   double *phi_zc = nullptr;
   double2 *phi_q = nullptr;
+  double2 *phi_abf = nullptr;  // float-float plans: alpha, beta, beta alpha per pole ([3][P] float4)
   double2 sumb{};
 
   // float-float solves (REXI_SOLVE_FP32X2): the factors hold float-float values in place

@@ -28,7 +28,10 @@ N, NLAT, NLON, T = 128, 192, 384, 1.5 * 86400.0
 # (M, dt): too few poles for the step; the paper's dt = 800 s and 1600 s with M = 512; a
 # dt near its 3200 s that divides 1.5 days; one 1.5-day step with enough poles to cover
 # tau * omega_max = 819 (h M = 823)
-CONFIGS = [(16, 800.0), (512, 800.0), (512, 1600.0), (512, 3240.0), (4116, T)]
+CONFIGS = [(16, 800.0, "fp64"), (512, 800.0, "fp64"), (512, 1600.0, "fp64"), (512, 3240.0, "fp64"),
+           (4116, T, "fp64"),
+           # the float-float solves (solve_arith="fp32x2") on the paper's dt and on the long step
+           (512, 800.0, "fp32x2"), (4116, T, "fp32x2")]
 
 
 @pytest.fixture(scope="module")
@@ -39,18 +42,18 @@ def bumps():
     S0 = gs.analyse(x0)
     h_exact = gs.synthesise(integrate.exact(S0, N, T, C))[0, 0]
     h_rk4 = gs.synthesise(integrate.rk4(S0, N, 50.0, int(T / 50.0), C))[0, 0]
-    return dict(x0=x0, gs=gs, S0=S0, h_exact=h_exact, h_rk4=h_rk4, report=[])
+    return dict(x0=x0, gs=gs, S0=S0, h_exact=h_exact, h_rk4=h_rk4, report=[], refs={})
 
 
-@pytest.mark.parametrize("M,dt", CONFIGS)
-def test_bump_propagation(bumps, M, dt):
+@pytest.mark.parametrize("M,dt,arith", CONFIGS)
+def test_bump_propagation(bumps, M, dt, arith):
     import torch
     from paper_1812_03431_gb300 import rexi
     nsteps = int(round(T / dt))
     assert abs(nsteps * dt - T) < 1e-6
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plan = rexi.Plan(N, NLAT, NLON, M=M, tau=dt, max_batch=1, layout="spectral")
+    plan = rexi.Plan(N, NLAT, NLON, M=M, tau=dt, max_batch=1, layout="spectral", solve_arith=arith)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -70,8 +73,10 @@ def test_bump_propagation(bumps, M, dt):
     P = plan.info()["P"]
     plan.close()
 
-    al, be, _ = rc.rexi_coefficients(M, 0.2)
-    ref = integrate.rexi_modal(bumps["S0"], N, al, be, dt, nsteps, C)
+    if (M, dt) not in bumps["refs"]:
+        al, be, _ = rc.rexi_coefficients(M, 0.2)
+        bumps["refs"][M, dt] = integrate.rexi_modal(bumps["S0"], N, al, be, dt, nsteps, C)
+    ref = bumps["refs"][M, dt]
     par = max(np.linalg.norm(S[:, f] - ref[:, f]) / np.linalg.norm(ref[:, f]) for f in range(3))
     assert par < 1e-9
     h_ref = bumps["gs"].synthesise(ref)[0, 0]
@@ -84,7 +89,7 @@ def test_bump_propagation(bumps, M, dt):
         assert err_exact < 0.02 * np.abs(bumps["h_exact"]).max()
     if dt == T:
         assert err_exact < 1e-3 < rk4_err  # one REXI step beats the 2592-step RK4 reference
-    bumps["report"].append(dict(M=M, P=P, dt=dt, steps=nsteps, setup_s=t_setup, tune_s=t_tune, pole_slots=slots,
+    bumps["report"].append(dict(M=M, P=P, dt=dt, steps=nsteps, solve_arith=arith, setup_s=t_setup, tune_s=t_tune, pole_slots=slots,
                                 run_s=runs[1],
                                 linf_h_vs_exact_m=err_exact, linf_h_vs_rk4_50s_m=err_rk4,
                                 rk4_50s_vs_exact_m=rk4_err, parity_rel_l2=par))

@@ -200,8 +200,6 @@ def test_ragged_fp32x2_matches_per_plan_steps(torch, rexi):
 
 def test_rejected_combinations(torch, rexi):
     with pytest.raises(rexi.RexiError):
-        rexi.Plan(15, 16, 32, M=8, layout="spectral", solver="phi", solve_arith="fp32x2")
-    with pytest.raises(rexi.RexiError):
         rexi.Plan(15, 16, 32, M=8, layout="spectral", fsphere=True, solve_arith="fp32x2")
 
 

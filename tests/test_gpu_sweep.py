@@ -40,8 +40,8 @@ def configs(count=48, seed=4242):
         kind = str(rng.choice(["delta", "delta", "phi", "fsphere"]))
         tau = float(rng.choice([600.0, 1800.0, 3600.0, 7200.0]))
         arith = str(rng_arith.choice(["fp64", "fp32x2"]))
-        if kind != "delta":
-            arith = "fp64"  # float-float solves serve the delta elimination on the rotating sphere
+        if kind == "fsphere":
+            arith = "fp64"  # float-float solves serve the banded solvers on the rotating sphere
         out.append((N, nlat, nlon, M, B, layout, precision, kind, tau, arith))
     return out
 
