@@ -203,13 +203,15 @@ def full_size_case():
     return dict(N=N, nlat=nlat, nlon=nlon, B=B, tau=tau, al=al, be=be, x=x, ref=gs(x0))
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("mixed", 1e-5)])
-def test_full_size_grid_step_bench_launch(torch, rexi, full_size_case, precision, tol):
-    """The bench's launch: T341, 1024x512, K=256, tau=1200 s, batch 16, grid layout.
-    The oracle computes the whole grid-layout step for state 0 of the batch."""
+@pytest.mark.parametrize("precision,arith,tol", [("fp64", "fp64", TOL), ("mixed", "fp64", 1e-5),
+                                                ("mixed", "fp32x2", 1e-5)])
+def test_full_size_grid_step_bench_launch(torch, rexi, full_size_case, precision, arith, tol):
+    """The bench's launches: T341, 1024x512, K=256, tau=1200 s, batch 16, grid layout, in each
+    of its forms (mixed transforms with float-float solves is the chosen one).  The oracle
+    computes the whole grid-layout step for state 0 of the batch."""
     c = full_size_case
     plan = rexi.Plan(c["N"], c["nlat"], c["nlon"], tau=c["tau"], max_batch=c["B"], alpha=c["al"], beta=c["be"],
-                     precision=precision)
+                     precision=precision, solve_arith=arith)
     plan.tune(c["B"])  # the layout the bench times
     got = plan.step(torch.from_numpy(c["x"]).cuda()).cpu().numpy()
     plan.close()
