@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "ff.h"
 #include "rexi_internal.h"
@@ -283,6 +284,7 @@ __global__ void phi_rhs_kernel(PhiRhsArgs a) {
 struct PhiSolveArgs {
   const double2 *fac, *q, *alpha, *beta;
   const float4 *abf;  // float-float plans: alpha, beta, beta alpha per pole ([3][P])
+  int ffil;           // float-float factors interleaved ([nrows][P][7]) or pole-fastest ([7][nrows][P])
   double2 *part;  // [3][nspec][slots][B]: (sum beta Phi, zeta couplings, sum beta alpha Phi)
   const int4 *sys;
   double2 *ybuf;
@@ -395,21 +397,23 @@ __device__ __forceinline__ void phi_sweep(const PhiSolveArgs &a, const int (&k)[
 // L2 three rows ahead.
 __device__ __forceinline__ void l2_prefetch(const void *p) { asm volatile("prefetch.global.L2 [%0];" : : "l"(p)); }
 
-template <int KC>
+template <int KC, bool IL>
 __device__ __forceinline__ void phi_sweep_ff(const PhiSolveArgs &a, const int (&k)[KC], int m, int n0, int len,
                                              int64_t row0, int64_t base, const float4 *qb, float4 *pP, float4 *pZ,
                                              float4 *pD, int64_t rstride, bool first, float4 *ybuf) {
   constexpr int D = 3;  // rows prefetched ahead into L2
-  const int64_t NS = a.nspec, RS = (int64_t)a.P * 7;
+  // factor (comp, row i, pole c) at fk[c] + i RS + comp CS: interleaved (IL) rows of P x 7
+  // values, or the pole-fastest layout [7][nrows][P]
+  const int64_t NS = a.nspec, RS = IL ? (int64_t)a.P * 7 : (int64_t)a.P, CS = IL ? 1 : a.nrows * a.P;
   const int N = a.N, B = a.B;
   float4 al[KC], be[KC], bal[KC];
-  const float4 *fk[KC];  // factor (comp, row i, pole c) at fk[c] + i RS + comp
+  const float4 *fk[KC];
 #pragma unroll
   for (int c = 0; c < KC; ++c) {
     al[c] = a.abf[k[c]];
     be[c] = a.abf[a.P + k[c]];
     bal[c] = a.abf[2 * a.P + k[c]];
-    fk[c] = reinterpret_cast<const float4 *>(a.fac) + (row0 * a.P + k[c]) * 7;
+    fk[c] = reinterpret_cast<const float4 *>(a.fac) + (IL ? (row0 * a.P + k[c]) * 7 : row0 * a.P + k[c]);
   }
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   auto pf_fwd = [&](int i) {
@@ -417,7 +421,10 @@ __device__ __forceinline__ void phi_sweep_ff(const PhiSolveArgs &a, const int (&
 #pragma unroll
     for (int p = 0; p < 5; ++p) l2_prefetch(qb + ((int64_t)p * NS + ix) * B);
 #pragma unroll
-    for (int c = 0; c < KC; ++c) l2_prefetch(fk[c] + (int64_t)i * RS + 1);
+    for (int c = 0; c < KC; ++c) {  // factors 0 and 1
+      l2_prefetch(fk[c] + (int64_t)i * RS);
+      l2_prefetch(fk[c] + (int64_t)i * RS + CS);
+    }
   };
   auto pf_bwd = [&](int i) {
     const int n = n0 + 2 * i;
@@ -425,8 +432,13 @@ __device__ __forceinline__ void phi_sweep_ff(const PhiSolveArgs &a, const int (&
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;  // factors 2..6
-      l2_prefetch(f + 2);
-      l2_prefetch(f + 6);
+      if (IL) {
+        l2_prefetch(f + 2);
+        l2_prefetch(f + 6);
+      } else {
+#pragma unroll
+        for (int q = 2; q <= 6; ++q) l2_prefetch(f + q * CS);
+      }
       l2_prefetch(ybuf + ((int64_t)i * KC + c) * 32);
     }
     if (!first) {
@@ -457,8 +469,8 @@ __device__ __forceinline__ void phi_sweep_ff(const PhiSolveArgs &a, const int (&
         ff::cmac(r2, ff::raw(r), al[c]);
         r = r2;
       }
-      ff::cmsub(r, __ldg(f + 0), y1[c]);
-      ff::cmsub(r, __ldg(f + 1), y2[c]);
+      ff::cmsub(r, __ldg(f + 0 * CS), y1[c]);
+      ff::cmsub(r, __ldg(f + 1 * CS), y2[c]);
       const float4 yv = ff::raw(r);
       ybuf[((int64_t)i * KC + c) * 32] = yv;
       y2[c] = y1[c];
@@ -479,10 +491,10 @@ __device__ __forceinline__ void phi_sweep_ff(const PhiSolveArgs &a, const int (&
     for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;
       ff::CAcc r = ff::cacc(ybuf[((int64_t)i * KC + c) * 32]);
-      ff::cmsub(r, __ldg(f + 2), x1[c]);
-      ff::cmsub(r, __ldg(f + 3), x2[c]);
+      ff::cmsub(r, __ldg(f + 2 * CS), x1[c]);
+      ff::cmsub(r, __ldg(f + 3 * CS), x2[c]);
       ff::CAcc x = ff::czero();
-      ff::cmac(x, ff::raw(r), __ldg(f + 4));
+      ff::cmac(x, ff::raw(r), __ldg(f + 4 * CS));
       xv[c] = ff::raw(x);
     }
     ff::CAcc accP = first ? ff::czero() : ff::cacc(pP[ix * rstride]);
@@ -498,14 +510,14 @@ __device__ __forceinline__ void phi_sweep_ff(const PhiSolveArgs &a, const int (&
       ff::CAcc accZ = first ? ff::czero() : ff::cacc(pZ[(ix + 1) * rstride]);
 #pragma unroll
       for (int c = 0; c < KC; ++c) {
-        ff::cmac(accZ, __ldg(fk[c] + (int64_t)i * RS + 5), xv[c]);
+        ff::cmac(accZ, __ldg(fk[c] + (int64_t)i * RS + 5 * CS), xv[c]);
         ff::cmac(accZ, zmn[c], x1[c]);
       }
       pZ[(ix + 1) * rstride] = ff::raw(accZ);
     }
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      zmn[c] = __ldg(fk[c] + (int64_t)i * RS + 6);
+      zmn[c] = __ldg(fk[c] + (int64_t)i * RS + 6 * CS);
       x2[c] = x1[c];
       x1[c] = xv[c];
     }
@@ -552,15 +564,20 @@ __global__ void __launch_bounds__(128) phi_solve_kernel(PhiSolveArgs a) {
       const float4 *fq = reinterpret_cast<const float4 *>(qb);
       float4 *fP = reinterpret_cast<float4 *>(pP), *fZ = reinterpret_cast<float4 *>(pZ),
              *fD = reinterpret_cast<float4 *>(pD), *fy = reinterpret_cast<float4 *>(ybuf);
-      for (; k0 + Sm < a.P; k0 += 2 * Sm) {
-        const int kp[2] = {k0, k0 + Sm};
-        phi_sweep_ff<2>(a, kp, m, n0, len, sy.w, base, fq, fP, fZ, fD, rstride, first, fy);
-        first = false;
-      }
-      if (k0 < a.P) {
-        const int kp[1] = {k0};
-        phi_sweep_ff<1>(a, kp, m, n0, len, sy.w, base, fq, fP, fZ, fD, rstride, first, fy);
-      }
+      auto sweeps = [&](auto il) {
+        constexpr bool IL = decltype(il)::value;
+        for (; k0 + Sm < a.P; k0 += 2 * Sm) {
+          const int kp[2] = {k0, k0 + Sm};
+          phi_sweep_ff<2, IL>(a, kp, m, n0, len, sy.w, base, fq, fP, fZ, fD, rstride, first, fy);
+          first = false;
+        }
+        if (k0 < a.P) {
+          const int kp[1] = {k0};
+          phi_sweep_ff<1, IL>(a, kp, m, n0, len, sy.w, base, fq, fP, fZ, fD, rstride, first, fy);
+        }
+      };
+      if (a.ffil) sweeps(std::true_type{});
+      else sweeps(std::false_type{});
     } else {
       for (; k0 + Sm < a.P; k0 += 2 * Sm) {
         const int kp[2] = {k0, k0 + Sm};
@@ -663,7 +680,7 @@ cudaError_t launch_phi_factor(Plan &pl, cudaStream_t st) {
   a.N = pl.N;
   a.nrows = pl.nrows;
   a.c = phi_consts(pl);
-  a.interleaved = pl.ff ? 1 : 0;
+  a.interleaved = pl.ffil ? 1 : 0;
   const int64_t total = (int64_t)a.P * a.nsys;
   phi_factor_kernel<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
@@ -689,6 +706,7 @@ cudaError_t launch_phi_solve(Plan &pl, const SolveLayout &lay, const double2 *si
     s.alpha = pl.alpha_dev;
     s.beta = pl.beta_dev;
     s.abf = reinterpret_cast<const float4 *>(pl.phi_abf);
+    s.ffil = pl.ffil ? 1 : 0;
     s.part = pl.partial;
     s.sys = pl.sys_dev;
     s.ybuf = pl.yscratch;

@@ -103,6 +103,7 @@ void free_plan(Plan *pl);
 rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   pl->prm = prm;
   pl->ff = prm.solve_arith == REXI_SOLVE_FP32X2;
+  pl->ffil = pl->ff && prm.max_batch >= 8;
   const int N = prm.ntrunc;
   pl->N = N;
   pl->nlat = prm.nlat;

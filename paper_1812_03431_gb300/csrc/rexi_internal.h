@@ -125,7 +125,7 @@ struct Plan {
   int32_t *m_of_dev = nullptr;
 
   // solve factors (forward and adjoint): [F_NCOMP][nrows][P] double2; float-float plans
-  // hold [nrows][P][F_NCOMP] float-float values (float4 in the double2 slots)
+  // hold float-float values (float4 in the double2 slots), as [nrows][P][F_NCOMP] when ffil
   double2 *fac_fwd = nullptr, *fac_adj = nullptr;
   double2 *alpha_dev = nullptr, *beta_dev = nullptr;
   // pole-independent parts: W[idx] = sum_k beta_k/s_{k,n} (zeta), scalar S_Phi
@@ -168,6 +168,11 @@ struct Plan {
   // of binary64 ones, and s_ff [3][nspec][B] the step's input states split the same way
   bool ff = false;
   double2 *s_ff = nullptr;
+  // float-float factor layout: interleaved ([nrows][P][comp], the factors of a (row, pole)
+  // adjacent) when a warp's lanes share their poles (max_batch >= 8: 8 or 16 states per
+  // warp); otherwise the pole-fastest layout of the binary64 factors, where a warp's lanes
+  // hold consecutive poles and its loads coalesce
+  bool ffil = false;
 
   // workspaces (max_batch)
   double2 *four = nullptr;     // [nlat][N+1][3 B] complex (FP64 or FP32 pairs in mixed mode)
@@ -209,13 +214,14 @@ cudaError_t launch_solve(Plan &pl, const SolveLayout &lay, bool adjoint, const d
 // One plan's view for the solve kernels: factors, internal states, partial sums,
 // systems and the lane layout of its batch.
 struct SolveView {
-  const double2 *fac;   // [F_NCOMP][nrows][P] (float-float plans: [nrows][P][F_NCOMP])
+  const double2 *fac;   // [F_NCOMP][nrows][P] (float-float plans with ffil: [nrows][P][F_NCOMP])
   const double2 *sin;   // [3][nspec][B]
   double2 *part;        // [3][nspec][slots][B]
   const int4 *sys;      // per (m, p): {m, n0, len, row0}
   int P, N, B, bw, kk, slots, pole_begin, pole_end;
   int64_t nspec, nrows;
   const int32_t *slots_m;  // per zonal order slot count (<= slots), or null for slots everywhere
+  int ffil;                // float-float factors interleaved (Plan::ffil)
 };
 SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, double2 *part, int B,
                     int pole_begin, int pole_end);

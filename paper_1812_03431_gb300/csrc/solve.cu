@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <string>
 
 #include "ff.h"
@@ -298,18 +299,21 @@ __device__ __forceinline__ float4 ldf(const float4 *p) { return __ldg(p); }
 // bring the line holding p into L2 (no register result, no wait)
 __device__ __forceinline__ void l2_prefetch(const void *p) { asm volatile("prefetch.global.L2 [%0];" : : "l"(p)); }
 
-template <int KC>
+template <int KC, bool IL>
 __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k)[KC], int n0, int len, int nmin,
                                                int64_t row0, int64_t base_idx, const float4 *sPhi,
                                                const float4 *sZeta, const float4 *sDel, float4 *pPhi,
                                                float4 *pZeta, float4 *pDel, int64_t rstride, bool first,
                                                float4 *ybuf) {
   constexpr int D = 3;  // rows prefetched ahead into L2
-  const int64_t RS = (int64_t)a.P * F_NCOMP;  // row stride of the interleaved factors
+  // factor (comp, row i, pole c) at fk[c] + i RS + comp CS: interleaved (IL) rows of
+  // P x F_NCOMP values, or the pole-fastest layout [F_NCOMP][nrows][P]
+  const int64_t RS = IL ? (int64_t)a.P * F_NCOMP : (int64_t)a.P;
+  const int64_t CS = IL ? 1 : a.nrows * a.P;
   const int N = a.N, B = a.B;
-  // factor (comp, row i, pole c) at fk[c] + i RS + comp
   const float4 *fk[KC];
-  for (int c = 0; c < KC; ++c) fk[c] = reinterpret_cast<const float4 *>(a.fac) + (row0 * a.P + k[c]) * F_NCOMP;
+  for (int c = 0; c < KC; ++c)
+    fk[c] = reinterpret_cast<const float4 *>(a.fac) + (IL ? (row0 * a.P + k[c]) * F_NCOMP : row0 * a.P + k[c]);
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   // Every row's data (states, factors, sweep intermediates, slot partials) is prefetched
   // into L2 D rows ahead, so that the row's own loads find it there; the prefetches hold
@@ -322,10 +326,15 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
     l2_prefetch(sDel + ix * B);
     l2_prefetch(sPhi + ix * B);
 #pragma unroll
-    for (int c = 0; c < KC; ++c) {  // factors 0..3 of the 144-byte record: at most two lines
+    for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;
-      l2_prefetch(f);
-      l2_prefetch(f + 3);
+      if (IL) {  // factors 0..3 of the 144-byte record: at most two lines
+        l2_prefetch(f);
+        l2_prefetch(f + 3);
+      } else {
+#pragma unroll
+        for (int q = F_L; q <= F_F; ++q) l2_prefetch(f + q * CS);
+      }
     }
   };
   auto pf_bwd = [&](int i) {
@@ -334,8 +343,13 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;  // factors 4..8
-      l2_prefetch(f + 4);
-      l2_prefetch(f + 8);
+      if (IL) {
+        l2_prefetch(f + 4);
+        l2_prefetch(f + 8);
+      } else {
+#pragma unroll
+        for (int q = F_C; q <= F_ZM; ++q) l2_prefetch(f + q * CS);
+      }
       l2_prefetch(ybuf + ((int64_t)i * KC + c) * 32);
     }
     if (!first) {
@@ -359,10 +373,10 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
     for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;
       ff::CAcc y = ff::cacc(d0);
-      ff::cmsub(y, ldf(f + F_G), p0);
-      ff::cmsub(y, ldf(f + F_E), zprev);
-      ff::cmsub(y, ldf(f + F_F), zn);
-      ff::cmsub(y, ldf(f + F_L), yprev[c]);
+      ff::cmsub(y, ldf(f + F_G * CS), p0);
+      ff::cmsub(y, ldf(f + F_E * CS), zprev);
+      ff::cmsub(y, ldf(f + F_F * CS), zn);
+      ff::cmsub(y, ldf(f + F_L * CS), yprev[c]);
       const float4 yv = ff::raw(y);
       ybuf[((int64_t)i * KC + c) * 32] = yv;
       yprev[c] = yv;
@@ -381,7 +395,7 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       ff::CAcc w = ff::cacc(ybuf[((int64_t)i * KC + c) * 32]);
-      ff::cmsub(w, ldf(fk[c] + (int64_t)i * RS + F_C), wnext[c]);
+      ff::cmsub(w, ldf(fk[c] + (int64_t)i * RS + F_C * CS), wnext[c]);
       wv[c] = ff::raw(w);
     }
     ff::CAcc accD = first ? ff::czero() : ff::cacc(pDel[ix * rstride]);
@@ -389,8 +403,8 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;
-      ff::cmac(accD, ldf(f + F_BD), wv[c]);
-      ff::cmac(accP, ldf(f + F_BAD), wv[c]);
+      ff::cmac(accD, ldf(f + F_BD * CS), wv[c]);
+      ff::cmac(accP, ldf(f + F_BAD * CS), wv[c]);
     }
     pDel[ix * rstride] = ff::raw(accD);
     pPhi[ix * rstride] = ff::raw(accP);
@@ -398,14 +412,14 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
       ff::CAcc accZ = first ? ff::czero() : ff::cacc(pZeta[(ix + 1) * rstride]);
 #pragma unroll
       for (int c = 0; c < KC; ++c) {
-        ff::cmac(accZ, ldf(fk[c] + (int64_t)i * RS + F_ZP), wv[c]);
+        ff::cmac(accZ, ldf(fk[c] + (int64_t)i * RS + F_ZP * CS), wv[c]);
         ff::cmac(accZ, zmnext[c], wnext[c]);
       }
       pZeta[(ix + 1) * rstride] = ff::raw(accZ);
     }
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      zmnext[c] = ldf(fk[c] + (int64_t)i * RS + F_ZM);
+      zmnext[c] = ldf(fk[c] + (int64_t)i * RS + F_ZM * CS);
       wnext[c] = wv[c];
     }
   }
@@ -452,17 +466,22 @@ __device__ __forceinline__ void solve_item(const SolveView &a, int wm, int wg, i
                  *fDel = reinterpret_cast<const float4 *>(sDel);
     float4 *qPhi = reinterpret_cast<float4 *>(pPhi), *qZeta = reinterpret_cast<float4 *>(pZeta),
            *qDel = reinterpret_cast<float4 *>(pDel), *fy = reinterpret_cast<float4 *>(ybuf);
-    for (; k0 + Sm < a.pole_end; k0 += 2 * Sm) {
-      const int kp[2] = {k0, k0 + Sm};
-      sweep_poles_ff<2>(a, kp, n0, len, nmin, row0, base_idx, fPhi, fZeta, fDel, qPhi, qZeta, qDel, rstride, first,
-                        fy);
-      first = false;
-    }
-    if (k0 < a.pole_end) {
-      const int kp[1] = {k0};
-      sweep_poles_ff<1>(a, kp, n0, len, nmin, row0, base_idx, fPhi, fZeta, fDel, qPhi, qZeta, qDel, rstride, first,
-                        fy);
-    }
+    auto sweeps = [&](auto il) {
+      constexpr bool IL = decltype(il)::value;
+      for (; k0 + Sm < a.pole_end; k0 += 2 * Sm) {
+        const int kp[2] = {k0, k0 + Sm};
+        sweep_poles_ff<2, IL>(a, kp, n0, len, nmin, row0, base_idx, fPhi, fZeta, fDel, qPhi, qZeta, qDel, rstride,
+                              first, fy);
+        first = false;
+      }
+      if (k0 < a.pole_end) {
+        const int kp[1] = {k0};
+        sweep_poles_ff<1, IL>(a, kp, n0, len, nmin, row0, base_idx, fPhi, fZeta, fDel, qPhi, qZeta, qDel, rstride,
+                              first, fy);
+      }
+    };
+    if (a.ffil) sweeps(std::true_type{});
+    else sweeps(std::false_type{});
   } else {
     for (; k0 + Sm < a.pole_end; k0 += 2 * Sm) {
       const int kp[2] = {k0, k0 + Sm};
@@ -792,7 +811,7 @@ cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st) {
   a.phibar = pl.prm.gravity * pl.prm.mean_depth;
   a.q = 2.0 * pl.prm.omega * pl.prm.tau;
   a.adjoint = adjoint ? 1 : 0;
-  a.interleaved = pl.ff ? 1 : 0;
+  a.interleaved = pl.ffil ? 1 : 0;
   int64_t total = (int64_t)a.P * a.nsys;
   factor_setup_kernel<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
@@ -826,6 +845,7 @@ SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double
   v.kk = lay.kk;
   v.slots = lay.slots;
   v.slots_m = lay.slots_m_dev;
+  v.ffil = pl.ffil ? 1 : 0;
   v.pole_begin = pole_begin;
   v.pole_end = pole_end;
   v.nspec = pl.nspec;
@@ -1023,6 +1043,7 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
     a.v.kk = slots;
     a.v.slots = slots;
     a.v.slots_m = nullptr;
+    a.v.ffil = pl.ffil ? 1 : 0;
     a.v.pole_begin = 0;
     a.v.pole_end = pl.P;
     a.v.nspec = pl.nspec;
