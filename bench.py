@@ -27,7 +27,15 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORK = dict(N=341, nlat=512, nlon=1024, M=256, h=0.2, tau=1200.0, batch=16, seed=1005)
+# The metric's workload (the default) and the specification's other single-GPU workloads,
+# timed with --workload: T127 with 64 states, and a single T1279 state.  Seeds follow the
+# input recipe (1000 + the workload's place in the specification; the metric's run 1005).
+WORKLOADS = {
+    "t341_b16": dict(N=341, nlat=512, nlon=1024, M=256, h=0.2, tau=1200.0, batch=16, seed=1005),
+    "t127_b64": dict(N=127, nlat=192, nlon=384, M=256, h=0.2, tau=7200.0, batch=64, seed=1001),
+    "t1279_b1": dict(N=1279, nlat=1920, nlon=3840, M=512, h=0.2, tau=21600.0, batch=1, seed=1004),
+}
+WORK = dict(WORKLOADS["t341_b16"])
 METRIC = "REXI steps/s at T341, K=256 poles: chosen vs plain FP64 form at stated error"
 # (name, transforms, solve arithmetic); the first is the chosen form.  mixed_fp32x2: 3xTF32
 # Legendre and FP32 FFTs, float-float banded solves and pole sum; mixed: the same transforms
@@ -274,11 +282,17 @@ def replica_max_ms(ms, dist):
 
 
 def workload_config():
-    return {"workload": "T-REXI step, linear SWE on the sphere: T341, 1024x512 Gaussian grid, K=M=256 "
-                        "(P=535 poles), h=0.2, tau=1200 s, 16 seeded n^-3 states, grid layout",
-            "global_batch": WORK["batch"], "truncation": WORK["N"], "grid": [WORK["nlat"], WORK["nlon"]],
-            "poles": 2 * (WORK["M"] + 11) + 1, "parallelism": "replicas",
-            "l2": "inputs (201 MB) and factors (4.5 GB) larger than L2, no flush"}
+    W = WORK
+    P = 2 * (W["M"] + 11) + 1
+    grid_mb = W["batch"] * 3 * W["nlat"] * W["nlon"] * 8 / 1e6
+    fac_gb = 9 * rows_of(W["N"]) * P * 16 / 1e9
+    return {"workload": "T-REXI step, linear SWE on the sphere: T%d, %dx%d Gaussian grid, K=M=%d (P=%d poles), "
+                        "h=%g, tau=%g s, %d seeded n^-3 state%s, grid layout"
+                        % (W["N"], W["nlon"], W["nlat"], W["M"], P, W["h"], W["tau"], W["batch"],
+                           "s" if W["batch"] > 1 else ""),
+            "global_batch": W["batch"], "truncation": W["N"], "grid": [W["nlat"], W["nlon"]],
+            "poles": P, "parallelism": "replicas",
+            "l2": "inputs (%.0f MB) and factors (%.1f GB) larger than L2, no flush" % (grid_mb, fac_gb)}
 
 
 def main():
@@ -292,7 +306,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-phi-solver", action="store_true",
                     help="skip timing the paper's geopotential-only solver next to the default one")
+    ap.add_argument("--workload", default="t341_b16", choices=sorted(WORKLOADS),
+                    help="t341_b16: the metric's workload; the others time further workloads of the "
+                         "specification (no CPU baseline, no Phi-only solver, no traffic figure)")
     args = ap.parse_args()
+    WORK.clear()
+    WORK.update(WORKLOADS[args.workload])
+    default_workload = args.workload == "t341_b16"
+    if not default_workload:
+        args.no_cpu_baseline = True
+        args.no_phi_solver = True
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -454,18 +477,23 @@ def main():
     traffic = traffic_t170[tkey] * rows_of(W["N"]) / rows_of(170)
     dtypes = {"mixed_fp32x2": "f64 i/o; float-float (2 x f32) solves + pole sum; 3xtf32 legendre; f32 fft",
               "mixed": "f64 solves + pole sum; 3xtf32 legendre; f32 fft", "fp64": "f64"}
+    metric = METRIC if default_workload else "REXI steps/s at T%d, K=%d poles, %d state%s: chosen vs plain FP64 " \
+        "form at stated error" % (W["N"], W["M"], B, "s" if B > 1 else "")
+    if not default_workload:
+        traffic = None  # the captured traffic is for 16 states; it does not scale by rows alone
     line = {
-        "metric": METRIC, "value": world * 1e3 / r["ms"], "unit": "steps/s", "n_gpus": world,
+        "metric": metric, "value": world * 1e3 / r["ms"], "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtypes[chosen],
         "data": "synthetic", "config": {**workload_config(), "form": chosen, "pole_slots": r["slots"], "layout_shape": r["shape"]},
         "roofline": {"bound": "alu", "kernel": kname,
                      "achieved": achieved, "peak": peak, "unit": roof_unit, "frac": achieved / peak,
                      "traffic": traffic,
-                     "traffic_source": "ncu dram bytes at T170/K256/B16 with %d pole slots, layout shape %d "
-                                       "(the captured layout nearest the bench's %d, shape %d), scaled by rows "
-                                       "to T341" % (tkey[0], tkey[1], r["slots"], r["shape"]),
-                     "dram_gbs": traffic / (solve_ms * 1e-3) / 1e9,
+                     "traffic_source": ("ncu dram bytes at T170/K256/B16 with %d pole slots, layout shape %d "
+                                        "(the captured layout nearest the bench's %d, shape %d), scaled by rows "
+                                        "to T341" % (tkey[0], tkey[1], r["slots"], r["shape"]))
+                     if default_workload else "not captured for this workload",
+                     "dram_gbs": traffic / (solve_ms * 1e-3) / 1e9 if traffic else None,
                      "peak_source": peak_source, "algorithmic_per_launch": amount, "launch_ms": solve_ms},
         "state_steps_per_s": world * B * 1e3 / r["ms"],
         "stage_ms": r["stages"],
