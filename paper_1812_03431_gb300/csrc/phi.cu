@@ -1,5 +1,5 @@
 // The paper's geopotential-only solver (Sec. 4.3 and 5) as an alternative to the
-// delta elimination, FP64.
+// delta elimination, in binary64 or (REXI_SOLVE_FP32X2) float-float arithmetic.
 //
 // Per pole alpha (tau kept explicit, f = F mu with F = 2 Omega, g = 2 Omega / a):
 //   alpha Phi - tau Phibar div V = Phi0,   A V = V0 + tau grad Phi,   D = alpha^2 + tau^2 f^2.

@@ -1,5 +1,5 @@
 // Banded shifted solves and the beta-weighted pole sum (paper Sec. 4.2, Sec. 5,
-// Algorithm 1), FP64.
+// Algorithm 1), in binary64 or in float-float arithmetic (ff.h) on the FP32 pipes.
 //
 // Per zonal order m, (alpha + tau L_m) X = U couples (Phi_n, zeta_n, delta_n)
 // with L_m of Eq. (1) in spectral form:
@@ -20,13 +20,14 @@
 //   y_i = delta0_n - g Phi0_n - e zeta0_{n-1} - f zeta0_{n+1} - l y_{i-1}
 // and a backward sweep  w_i = y_i - Chat w_{i+1}  (delta_n = w_i / d'_i, folded
 // into the weights) accumulating beta-weighted sums of delta, Phi and zeta in
-// FP64.  The poles are split into `slots` groups summed separately (each in
-// ascending k) and reduced in slot order, so results are bit-reproducible.
+// FP64 (solve_kernel<false>) or float-float (solve_kernel<true>, for plans with
+// REXI_SOLVE_FP32X2).  The poles are split into `slots` groups summed separately
+// (each in ascending k) and reduced in slot order, so results are bit-reproducible.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <type_traits>
 #include <string>
+#include <type_traits>
 
 #include "ff.h"
 #include "rexi_internal.h"
