@@ -61,7 +61,8 @@ typedef enum {
   REXI_EINVAL = -1,   /* bad argument, size or alignment */
   REXI_ENOMEM = -2,   /* device or host allocation failed */
   REXI_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
-  REXI_ERANGE = -4,   /* tau * max|omega| outside the poles' valid range (strict plans only) */
+  REXI_ERANGE = -4,   /* tau * max|omega| outside the poles' valid range (strict plans only);
+                         for REXI_SOLVE_FP32X2: a value beyond binary32's range */
   REXI_ETIMEOUT = -5  /* a bounded device-side wait expired */
 } rexi_status;
 
@@ -159,7 +160,8 @@ rexi_status rexi_coefficients(int32_t M, double h, int32_t normalize,
  * (those of the adjoint are built on the first rexi_step_adjoint call), and
  * workspaces for max_batch states.  Allocates device memory; synchronises the
  * device once.  *out is NULL on failure (REXI_ENOMEM when the device memory does
- * not suffice). */
+ * not suffice; REXI_ERANGE when a REXI_SOLVE_FP32X2 plan's factors exceed
+ * binary32's range, as do those of rexi_step_adjoint's first call). */
 rexi_status rexi_plan_create(const rexi_params *params, rexi_plan **out);
 
 /* One T-REXI step (Algorithm 1): out = Re sum_k beta_k (alpha_k + tau L)^{-1} in,
@@ -278,7 +280,11 @@ rexi_status rexi_profile_read(rexi_plan *plan, double *stage_ms, int32_t n, int3
 /* Synchronise the device and report whether any kernel of this plan gave up a
  * bounded device-side wait (tensor-core completion barriers) since the last
  * check: REXI_ETIMEOUT (and the flag is cleared) or REXI_OK.  Kernels that give
- * up skip their outputs, free their tensor memory and return. */
+ * up skip their outputs, free their tensor memory and return.  For
+ * REXI_SOLVE_FP32X2 plans it also reports REXI_ERANGE when a step's input (or a
+ * Phi-only right-hand side) held a finite value beyond binary32's range since the
+ * last check: such values become infinite in float-float, and the outputs of that
+ * step are not finite. */
 rexi_status rexi_check_device(rexi_plan *plan);
 
 /* Free everything the plan holds; NULL-safe.  The caller synchronises streams

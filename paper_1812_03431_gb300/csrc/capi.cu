@@ -113,6 +113,7 @@ rexi_status ensure_adjoint_factors(Plan &pl) {
   e = launch_factor_setup(pl, true, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail("adjoint factor setup", e);
+  if (pl.ff) return take_range_error(pl, "adjoint float-float factors");
   return REXI_OK;
 }
 
@@ -528,10 +529,15 @@ rexi_status rexi_check_device(rexi_plan *plan) {
   int flag = 0;
   e = cudaMemcpy(&flag, pl.dev_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail("rexi_check_device", e);
-  if (flag) {
-    cudaMemset(pl.dev_err, 0, sizeof(int));
+  if (flag) cudaMemset(pl.dev_err, 0, sizeof(int));
+  if (flag & DEV_ERR_TIMEOUT) {
     set_error("a bounded device-side wait expired; the affected outputs were not written");
     return REXI_ETIMEOUT;
+  }
+  if (flag & DEV_ERR_RANGE) {
+    set_error("a float-float solve met a value beyond binary32's range (|x| > 3.4e38); its outputs are "
+              "not finite; use REXI_SOLVE_FP64 for such states");
+    return REXI_ERANGE;
   }
   return REXI_OK;
 }

@@ -116,6 +116,12 @@ __device__ __forceinline__ float4 csplit(double2 z) {
   return make_float4(r.x, r.y, i.x, i.y);
 }
 
+// true when a finite binary64 component of z became infinite in the split (|x| above
+// binary32's largest finite value)
+__device__ __forceinline__ bool split_overflow(double2 z, float4 v) {
+  return (isinf(v.x) && isfinite(z.x)) || (isinf(v.z) && isfinite(z.y));
+}
+
 // float-float -> binary64 (hi + lo rounded once)
 __device__ __forceinline__ double join(float hi, float lo) { return (double)hi + (double)lo; }
 __device__ __forceinline__ double2 cjoin(float4 v) { return make_double2(join(v.x, v.y), join(v.z, v.w)); }

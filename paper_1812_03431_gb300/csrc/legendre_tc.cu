@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(THREADS) leg_ana_tc_kernel(TcArgs a) {
     if (!ok) break;
   }
   if (!ok) {
-    if (tid == 0) atomicExch(a.err, 1);
+    if (tid == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
   } else {
     // epilogue: TMEM lane = row of the tile (warp w owns lanes 32w .. 32w + 31)
     // warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile) for half w / 4 of the states
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(THREADS) leg_syn_tc_kernel(TcArgs a) {
     if (!ok) break;
   }
   if (!ok) {
-    if (tid == 0) atomicExch(a.err, 1);
+    if (tid == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
   } else {
     const int wq = warp & 3, half = warp >> 2;
     const int j = jt * TM + wq * 32 + (tid & 31);
@@ -581,8 +581,6 @@ cudaError_t tc_setup(Plan &pl) {
   if ((e = cudaMalloc(&pl.tc_tab_ana, bytes_a))) return e;
   if ((e = cudaMalloc(&pl.tc_tab_syn, bytes_s))) return e;
   pl.bytes += bytes_a + bytes_s;
-  if ((e = cudaMalloc(&pl.dev_err, sizeof(int)))) return e;
-  cudaMemset(pl.dev_err, 0, sizeof(int));
   PackArgs pa{pl.tabP, pl.tabH, pl.tc_tab_ana, nullptr, N, J, 0, nb, blk_a_dev};
   pack_tables_kernel<<<(unsigned)nb, 256>>>(pa);
   if ((e = cudaGetLastError())) return e;

@@ -167,6 +167,7 @@ struct PhiRhsArgs {
   int64_t nspec;
   PhiConsts c;
   int ff;
+  int *err;            // device error word (DEV_ERR_RANGE)
 };
 
 __device__ __forceinline__ double eps_nm(int n, int m) {
@@ -274,8 +275,13 @@ __global__ void phi_rhs_kernel(PhiRhsArgs a) {
 #pragma unroll
     for (int p = 0; p < 5; ++p) {
       const int64_t o = ((int64_t)p * a.nspec + ix) * B + b;
-      if (a.ff) reinterpret_cast<float4 *>(a.q)[o] = ff::csplit(Q[p]);
-      else a.q[o] = Q[p];
+      if (a.ff) {
+        const float4 f = ff::csplit(Q[p]);
+        if (ff::split_overflow(Q[p], f)) atomicOr(a.err, DEV_ERR_RANGE);
+        reinterpret_cast<float4 *>(a.q)[o] = f;
+      } else {
+        a.q[o] = Q[p];
+      }
     }
   }
 }
@@ -692,7 +698,7 @@ cudaError_t launch_phi_factor(Plan &pl, cudaStream_t st) {
 cudaError_t launch_phi_solve(Plan &pl, const SolveLayout &lay, const double2 *sin, int B, cudaStream_t st) {
   const PhiConsts c = phi_consts(pl);
   {
-    PhiRhsArgs r{sin, pl.phi_q, pl.m_of_dev, pl.N, B, pl.nspec, c, pl.ff ? 1 : 0};
+    PhiRhsArgs r{sin, pl.phi_q, pl.m_of_dev, pl.N, B, pl.nspec, c, pl.ff ? 1 : 0, pl.dev_err};
     const int64_t total = pl.nspec * B;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 127) / 128, (int64_t)pl.num_sms * 16));
     phi_rhs_kernel<<<blocks, 128, 0, st>>>(r);

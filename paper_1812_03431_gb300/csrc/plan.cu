@@ -119,6 +119,10 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   cudaGetDevice(&pl->device);
   cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
 
+  // device error word (rexi_check_device; the float-float factor split below reports to it)
+  if ((e = dalloc(&pl->dev_err, 1, &bytes))) return fail("error word", e);
+  if ((e = cudaMemset(pl->dev_err, 0, sizeof(int)))) return fail("error word", e);
+
   // ---- poles
   if (prm.alpha && prm.beta) {
     pl->P = prm.npoles;
@@ -272,6 +276,10 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
     const size_t nfac = (size_t)7 * pl->nrows * P;
     if ((e = dalloc(&pl->fac_fwd, nfac, &bytes))) return fail("factors", e);
     if ((e = launch_phi_factor(*pl, 0))) return fail("factor setup", e);
+    if (pl->ff) {
+      const rexi_status r = take_range_error(*pl, "plan: float-float factors");
+      if (r != REXI_OK) return r;
+    }
     if ((e = dalloc(&pl->phi_q, (size_t)5 * NS * prm.max_batch, &bytes))) return fail("phi rhs", e);
     if (pl->ff) {  // alpha, beta and beta alpha as float-float values (hi = fl32(x), lo = fl32(x - hi))
       auto split = [](double x) {
@@ -294,6 +302,10 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
     const size_t nfac = (size_t)F_NCOMP * pl->nrows * P;
     if ((e = dalloc(&pl->fac_fwd, nfac, &bytes))) return fail("factors", e);
     if ((e = launch_factor_setup(*pl, false, 0))) return fail("factor setup", e);
+    if (pl->ff) {
+      const rexi_status r = take_range_error(*pl, "plan: float-float factors");
+      if (r != REXI_OK) return r;
+    }
   }
 
   // ---- grid, Legendre tables, FFT
@@ -354,9 +366,6 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
 
   if (prm.precision == REXI_MIXED) {
     if ((e = tc_setup(*pl))) return fail("tensor-core tables", e);
-  } else {
-    if ((e = dalloc(&pl->dev_err, 1, &bytes))) return fail("error word", e);
-    cudaMemset(pl->dev_err, 0, sizeof(int));
   }
 
   // ---- workspaces

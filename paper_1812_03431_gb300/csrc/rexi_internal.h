@@ -103,6 +103,12 @@ struct FftPlan {
 
 enum FacComp { F_L = 0, F_G, F_E, F_F, F_C, F_BD, F_BAD, F_ZP, F_ZM, F_NCOMP };
 
+// bits of a plan's device error word (rexi_check_device)
+enum DevErr {
+  DEV_ERR_TIMEOUT = 1,  // a bounded wait (tensor-core completion barrier) expired
+  DEV_ERR_RANGE = 2     // a finite binary64 value outside binary32's range met a float-float split
+};
+
 // Poles a lane sweeps at once in the solve kernel; the forward-sweep buffer holds lmax
 // rows of that many values per lane.
 inline int sweep_width(bool) { return 2; }
@@ -154,7 +160,7 @@ struct Plan {
   uint32_t *tc_tab_ana = nullptr, *tc_tab_syn = nullptr;
   int4 *tc_work_ana = nullptr, *tc_work_syn = nullptr;
   int tc_nwork_ana = 0, tc_nwork_syn = 0;
-  int *dev_err = nullptr;  // set by a kernel whose bounded wait expired
+  int *dev_err = nullptr;  // device error word: DEV_ERR_* bits
 
   // geopotential-only solver (REXI_SOLVER_PHI): Z coefficients [nspec][12] (Z2, Z3, Z6
   // entries by degree offset), right-hand-side coefficients Q_p [5][nspec][max_batch],
@@ -231,6 +237,8 @@ cudaError_t launch_solve_ragged(const SolveView *views_dev, const WorkItem *item
 // states into out (float-float values in double2 slots)
 cudaError_t launch_to_ff(Plan &pl, double2 *v, int64_t n, cudaStream_t st);
 cudaError_t launch_split_state(Plan &pl, const double2 *in, double2 *out, int64_t n, cudaStream_t st);
+// reads and clears DEV_ERR_RANGE after a synchronisation: REXI_ERANGE when set
+rexi_status take_range_error(Plan &pl, const char *what);
 cudaError_t launch_reduce(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin,
                           double2 *sout, int B, bool single_pole, int pole, cudaStream_t st);
 cudaError_t launch_transpose_in(const double2 *user, double2 *sint, int64_t nspec, int B,

@@ -740,16 +740,26 @@ __global__ void fsphere_kernel(FsphereArgs a) {
   }
 }
 
-// In-place binary64 -> float-float conversion of complex values (factors, once per plan).
-__global__ void to_ff_kernel(double2 *v, int64_t n) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-    reinterpret_cast<float4 *>(v)[t] = ff::csplit(v[t]);
+// In-place binary64 -> float-float conversion of complex values (factors, once per plan);
+// a value beyond binary32's range sets DEV_ERR_RANGE.
+__global__ void to_ff_kernel(double2 *v, int64_t n, int *err) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double2 z = v[t];
+    const float4 f = ff::csplit(z);
+    if (ff::split_overflow(z, f)) atomicOr(err, DEV_ERR_RANGE);
+    reinterpret_cast<float4 *>(v)[t] = f;
+  }
 }
 
-// States for a float-float solve: in (binary64) -> out (float-float), once per step.
-__global__ void split_state_kernel(const double2 *in, float4 *out, int64_t n) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-    out[t] = ff::csplit(in[t]);
+// States for a float-float solve: in (binary64) -> out (float-float), once per step; a
+// value beyond binary32's range sets DEV_ERR_RANGE (rexi_check_device reports it).
+__global__ void split_state_kernel(const double2 *in, float4 *out, int64_t n, int *err) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double2 z = in[t];
+    const float4 f = ff::csplit(z);
+    if (ff::split_overflow(z, f)) atomicOr(err, DEV_ERR_RANGE);
+    out[t] = f;
+  }
 }
 
 // [rows][cols] -> [cols][rows] of double2 via 32x32 shared tiles (tiles indexed
@@ -822,14 +832,30 @@ cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st) {
 
 cudaError_t launch_to_ff(Plan &pl, double2 *v, int64_t n, cudaStream_t st) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)pl.num_sms * 16));
-  to_ff_kernel<<<blocks, 256, 0, st>>>(v, n);
+  to_ff_kernel<<<blocks, 256, 0, st>>>(v, n, pl.dev_err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_split_state(Plan &pl, const double2 *in, double2 *out, int64_t n, cudaStream_t st) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)pl.num_sms * 16));
-  split_state_kernel<<<blocks, 256, 0, st>>>(in, reinterpret_cast<float4 *>(out), n);
+  split_state_kernel<<<blocks, 256, 0, st>>>(in, reinterpret_cast<float4 *>(out), n, pl.dev_err);
   return cudaGetLastError();
+}
+
+rexi_status take_range_error(Plan &pl, const char *what) {
+  int flag = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, pl.dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return REXI_ECUDA;
+  }
+  if (!(flag & DEV_ERR_RANGE)) return REXI_OK;
+  flag &= ~DEV_ERR_RANGE;
+  cudaMemcpy(pl.dev_err, &flag, sizeof(int), cudaMemcpyHostToDevice);
+  set_error(std::string(what) + ": a value exceeds binary32's range (|x| > 3.4e38), which float-float "
+            "arithmetic cannot hold; use REXI_SOLVE_FP64");
+  return REXI_ERANGE;
 }
 
 SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, double2 *part, int B,

@@ -305,7 +305,8 @@ class Plan:
         return dict(zip(keys, list(v)))
 
     def check_device(self):
-        """Raise RexiError(REXI_ETIMEOUT) if a bounded device wait of this plan expired."""
+        """Raise RexiError(REXI_ETIMEOUT) if a bounded device wait of this plan expired, or
+        RexiError(REXI_ERANGE) if a float-float solve met a value beyond binary32's range."""
         _check("rexi_check_device", load().rexi_check_device(self._h))
 
     STAGES = ["fft_fwd", "leg_ana", "solve", "reduce", "leg_syn", "fft_inv", "transpose_in", "transpose_out"]

@@ -227,3 +227,34 @@ def test_full_size_sampled_orders(torch, rexi):
     from oracle.sphere import idx
     sel = np.concatenate([np.arange(idx(m, m, N), idx(m, N, N) + 1) for m in ms])
     assert fieldwise(got[:2][..., sel], ref[..., sel]) < TOL
+
+
+@pytest.mark.parametrize("solver", ["delta", "phi"])
+def test_range_errors_reported(torch, rexi, solver):
+    """Float-float holds binary32's exponent range only.  A finite state value beyond it
+    (here 1e39) is reported by rexi_check_device as REXI_ERANGE (once: the flag is
+    cleared), and factors beyond it (a pole at 1e-45) fail plan creation with
+    REXI_ERANGE; binary64 solves take both."""
+    N, B = 15, 2
+    S = inputs.random_spectral(N, B, 5)
+    S_big = S.copy()
+    S_big[1, 0, 3] = 1e39
+    plan = rexi.Plan(N, 16, 32, M=8, max_batch=B, layout="spectral", solver=solver, solve_arith="fp32x2")
+    plan.step(torch.from_numpy(S).cuda())
+    plan.check_device()
+    plan.step(torch.from_numpy(S_big).cuda())
+    with pytest.raises(rexi.RexiError) as err:
+        plan.check_device()
+    assert err.value.status == rexi.REXI_ERANGE
+    plan.check_device()  # reported once
+    plan.close()
+    p64 = rexi.Plan(N, 16, 32, M=8, max_batch=B, layout="spectral", solver=solver)
+    y = p64.step(torch.from_numpy(S_big).cuda()).cpu().numpy()
+    p64.check_device()
+    assert np.all(np.isfinite(y))
+    p64.close()
+    al, be = np.array([1e-45 + 0j]), np.array([1.0 + 0j])
+    with pytest.raises(rexi.RexiError) as err:
+        rexi.Plan(N, 16, 32, layout="spectral", alpha=al, beta=be, solver=solver, solve_arith="fp32x2")
+    assert err.value.status == rexi.REXI_ERANGE
+    rexi.Plan(N, 16, 32, layout="spectral", alpha=al, beta=be, solver=solver).close()
