@@ -173,9 +173,24 @@ def test_static_step_matches_rexi_step(torch, rexi):
     plan.close()
 
 
+@pytest.mark.parametrize("B", [1, 3, 9, 16])
+def test_interleaved_plan_with_smaller_batches(torch, rexi, B):
+    """A plan for 16 states keeps its factors interleaved (a warp's lanes share poles); calls
+    with fewer states put different poles in a warp's lanes and stay within the bound."""
+    N, M = 31, 32
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    S = inputs.random_spectral(N, B, 60 + B)
+    plan = rexi.Plan(N, 64, 128, tau=3600.0, max_batch=16, layout="spectral", alpha=al, beta=be,
+                     solve_arith="fp32x2")
+    got = plan.step(torch.from_numpy(S).cuda()).cpu().numpy()
+    plan.close()
+    assert fieldwise(got, ostep.rexi_step_spectral(S, N, al, be, 3600.0, C)) < TOL
+
+
 def test_ragged_fp32x2_matches_per_plan_steps(torch, rexi):
-    plans = [rexi.Plan(N, 2 * N + 2, 4 * N + 4, M=M, tau=1200.0, max_batch=2, layout="spectral",
-                       solve_arith="fp32x2") for N, M in ((31, 32), (63, 64))]
+    # max_batch 2 (pole-fastest factors) and 8 (interleaved factors) in one launch
+    plans = [rexi.Plan(N, 2 * N + 2, 4 * N + 4, M=M, tau=1200.0, max_batch=mb, layout="spectral",
+                       solve_arith="fp32x2") for N, M, mb in ((31, 32, 2), (63, 64, 8))]
     state_plan = [0, 1, 1, 0]
     states = [torch.from_numpy(inputs.random_spectral(31 if p == 0 else 63, 1, 500 + s)[0]).cuda()
               for s, p in enumerate(state_plan)]
@@ -188,9 +203,10 @@ def test_ragged_fp32x2_matches_per_plan_steps(torch, rexi):
         Y = plan.step(torch.stack([states[s] for s in idx])).cpu().numpy()
         for r, s in enumerate(idx):
             assert relerr(outs[s].cpu().numpy(), Y[r]) < 1e-13
-    al, be = plans[0].coefficients()
-    ref = ostep.rexi_step_spectral(states[0].cpu().numpy()[None], 31, al, be, 1200.0, C)
-    assert fieldwise(outs[0].cpu().numpy()[None], ref) < TOL
+    for s_, p, N in ((0, 0, 31), (1, 1, 63)):  # one state of each layout against the oracle
+        al, be = plans[p].coefficients()
+        ref = ostep.rexi_step_spectral(states[s_].cpu().numpy()[None], N, al, be, 1200.0, C)
+        assert fieldwise(outs[s_].cpu().numpy()[None], ref) < TOL
     other = rexi.Plan(31, 64, 128, M=32, tau=1200.0, max_batch=2, layout="spectral")
     with pytest.raises(rexi.RexiError):
         rexi.Ragged([plans[0], other], 4)  # one solve arithmetic per ragged batch
