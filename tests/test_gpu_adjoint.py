@@ -25,14 +25,15 @@ def misfit(torch, autograd, plan, x0, y, nsteps, every):
     return ((u - y) ** 2).sum()
 
 
-def test_gradient_matches_oracle_adjoint(env):
+@pytest.mark.parametrize("arith", ["fp64", "fp32x2"])
+def test_gradient_matches_oracle_adjoint(env, arith):
     torch, rexi, autograd = env
     N, nlat, nlon, M, tau, steps = 31, 48, 96, 32, 3600.0, 3
     al, be, _ = rc.rexi_coefficients(M, 0.2)
     gs = ostep.GridStep(N, nlat, nlon, al, be, tau, C)
     x0 = gs.synthesise(inputs.random_spectral(N, 1, 61))
     y = gs.synthesise(inputs.random_spectral(N, 1, 62))
-    plan = rexi.Plan(N, nlat, nlon, tau=tau, alpha=al, beta=be)
+    plan = rexi.Plan(N, nlat, nlon, tau=tau, alpha=al, beta=be, solve_arith=arith)
     X = torch.from_numpy(x0).cuda().requires_grad_(True)
     J = misfit(torch, autograd, plan, X, torch.from_numpy(y).cuda(), steps, 0)
     J.backward()
@@ -47,11 +48,12 @@ def test_gradient_matches_oracle_adjoint(env):
     assert np.linalg.norm(got - g) / np.linalg.norm(g) < 1e-10
 
 
-def test_c4_rollout_fd_and_checkpointing(env):
+@pytest.mark.parametrize("arith", ["fp64", "fp32x2"])
+def test_c4_rollout_fd_and_checkpointing(env, arith):
     """T170 on 512x256, K=256, 8 steps of 3600 s, J = ||U(T) - y||^2, checkpoint every 2."""
     torch, rexi, autograd = env
     N, nlat, nlon, tau, steps = 170, 256, 512, 3600.0, 8
-    plan = rexi.Plan(N, nlat, nlon, M=256, tau=tau)
+    plan = rexi.Plan(N, nlat, nlon, M=256, tau=tau, solve_arith=arith)
     S0 = torch.from_numpy(inputs.random_spectral(N, 1, 1003)).cuda()
     x0 = plan.synthesize(S0)
     yS = torch.from_numpy(inputs.random_spectral(N, 1, 1013)).cuda()
@@ -73,11 +75,16 @@ def test_c4_rollout_fd_and_checkpointing(env):
     assert abs(fd - an) <= 1e-6 * abs(an)
 
 
-def test_dot_product_identity_gpu(env):
+# float-float solves carry 32x binary64's unit roundoff (2^-48 against 2^-53)
+DOT_TOL = {"fp64": 1e-13, "fp32x2": 3e-12}
+
+
+@pytest.mark.parametrize("arith", ["fp64", "fp32x2"])
+def test_dot_product_identity_gpu(env, arith):
     torch, rexi, _ = env
     for layout in ("grid", "spectral"):
         N, nlat, nlon = 63, 96, 192
-        plan = rexi.Plan(N, nlat, nlon, M=64, tau=3600.0, max_batch=2, layout=layout)
+        plan = rexi.Plan(N, nlat, nlon, M=64, tau=3600.0, max_batch=2, layout=layout, solve_arith=arith)
         if layout == "grid":
             x = torch.from_numpy(inputs.random_grid(2, nlat, nlon, 71)).cuda()
             y = torch.from_numpy(inputs.random_grid(2, nlat, nlon, 72)).cuda()
@@ -90,5 +97,5 @@ def test_dot_product_identity_gpu(env):
             lhs = float(torch.vdot(y.flatten(), plan.step(x).flatten()).real)
             rhs = float(torch.vdot(plan.step_adjoint(y).flatten(), x.flatten()).real)
             scale = float(plan.step(x).norm() * y.norm())
-        assert abs(lhs - rhs) < 1e-13 * scale
+        assert abs(lhs - rhs) < DOT_TOL[arith] * scale
         plan.close()
