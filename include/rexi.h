@@ -66,10 +66,11 @@ typedef enum {
   REXI_ETIMEOUT = -5  /* a bounded device-side wait expired */
 } rexi_status;
 
-enum { REXI_FP64 = 0,      /* every stage in FP64 */
+enum { REXI_FP64 = 0,      /* every transform in FP64 */
        REXI_MIXED = 1 };   /* Legendre contractions as 3xTF32 tensor-core products with FP32
-                              accumulation and FP32 longitude FFTs; banded solves and the
-                              beta-weighted pole sum stay FP64 */
+                              accumulation and FP32 longitude FFTs.  The banded solves and the
+                              beta-weighted pole sum follow `solve_arith` in both forms
+                              (binary64 by default). */
 enum { REXI_GRID = 0,      /* rexi_step in/out are grid states */
        REXI_SPECTRAL = 1 }; /* rexi_step in/out are spectral states */
 enum { REXI_SOLVER_DELTA = 0, /* per (pole, m, parity): Phi and zeta eliminated, a tridiagonal
