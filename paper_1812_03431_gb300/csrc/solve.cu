@@ -364,12 +364,24 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
   for (int c = 0; c < KC; ++c) yprev[c] = zero;
   float4 zprev = (n0 - 1 >= nmin) ? ldf(sZeta + (base_idx + n0 - 1) * B) : zero;
   for (int j = 1; j <= D && j < len; ++j) pf_fwd(j);
-  for (int i = 0; i < len; ++i) {
-    if (i + D < len) pf_fwd(i + D);
+  // the states, first in each row's chain, are loaded into registers one row ahead
+  auto ld_states = [&](int i, float4 &zn, float4 &d0, float4 &p0) {
     const int n = n0 + 2 * i;
     const int64_t ix = base_idx + n;
-    const float4 zn = (n + 1 <= N) ? ldf(sZeta + (ix + 1) * B) : zero;
-    const float4 d0 = ldf(sDel + ix * B), p0 = ldf(sPhi + ix * B);
+    zn = (n + 1 <= N) ? ldf(sZeta + (ix + 1) * B) : zero;
+    d0 = ldf(sDel + ix * B);
+    p0 = ldf(sPhi + ix * B);
+  };
+  float4 znc, d0c, p0c;
+  ld_states(0, znc, d0c, p0c);
+  for (int i = 0; i < len; ++i) {
+    if (i + D < len) pf_fwd(i + D);
+    float4 znn, d0n, p0n;
+    ld_states(i + 1 < len ? i + 1 : i, znn, d0n, p0n);
+    const float4 zn = znc, d0 = d0c, p0 = p0c;
+    znc = znn;
+    d0c = d0n;
+    p0c = p0n;
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;
@@ -388,19 +400,36 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
   float4 wnext[KC], zmnext[KC];
   for (int c = 0; c < KC; ++c) wnext[c] = zmnext[c] = zero;
   for (int j = len - 2; j >= 0 && j >= len - 1 - D; --j) pf_bwd(j);
+  // the sweep intermediates and the delta / Phi partials, first in each row's chains, are
+  // loaded into registers one row ahead
+  auto ld_heads = [&](int i, float4 (&y)[KC], float4 &pd, float4 &pp) {
+    const int64_t ix = base_idx + n0 + 2 * i;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) y[c] = ybuf[((int64_t)i * KC + c) * 32];
+    pd = first ? zero : pDel[ix * rstride];
+    pp = first ? zero : pPhi[ix * rstride];
+  };
+  float4 yc[KC], pdc, ppc;
+  ld_heads(len - 1, yc, pdc, ppc);
   for (int i = len - 1; i >= 0; --i) {
     if (i - D >= 0) pf_bwd(i - D);
     const int n = n0 + 2 * i;
     const int64_t ix = base_idx + n;
+    float4 yn[KC], pdn, ppn;
+    ld_heads(i > 0 ? i - 1 : i, yn, pdn, ppn);
     float4 wv[KC];
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      ff::CAcc w = ff::cacc(ybuf[((int64_t)i * KC + c) * 32]);
+      ff::CAcc w = ff::cacc(yc[c]);
       ff::cmsub(w, ldf(fk[c] + (int64_t)i * RS + F_C * CS), wnext[c]);
       wv[c] = ff::raw(w);
     }
-    ff::CAcc accD = first ? ff::czero() : ff::cacc(pDel[ix * rstride]);
-    ff::CAcc accP = first ? ff::czero() : ff::cacc(pPhi[ix * rstride]);
+    ff::CAcc accD = ff::cacc(pdc);
+    ff::CAcc accP = ff::cacc(ppc);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) yc[c] = yn[c];
+    pdc = pdn;
+    ppc = ppn;
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;
