@@ -537,8 +537,10 @@ __device__ __forceinline__ void phi_sweep_ff(const PhiSolveArgs &a, const int (&
   }
 }
 
+// float-float: capped at 128 registers (four CTAs per SM); a few spilled bytes cost less
+// than the fourth CTA gains (14.5 against 15.3 ms at T341 with 16 states)
 template <bool FF>
-__global__ void __launch_bounds__(128) phi_solve_kernel(PhiSolveArgs a) {
+__global__ void __launch_bounds__(128, FF ? 4 : 1) phi_solve_kernel(PhiSolveArgs a) {
   const int lane = threadIdx.x & 31;
   const int wslot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   double2 *ybuf = a.ybuf + (int64_t)wslot * a.lmax * 2 * 32 + lane;
