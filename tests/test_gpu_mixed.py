@@ -70,7 +70,8 @@ def test_mixed_balanced_flow_stays_steady(env):
 def test_c2_batched_mixed_vs_fp64(env):
     """T127 on 384x192, K=256 (P=535), 64 seeded states, tau=7200 s: the batched plain vs
     mixed-precision configuration.  The FP64 form matches the oracle (two states, 1e-10);
-    the mixed form matches the FP64 form state by state within the stated 1e-5."""
+    the mixed form, with binary64 and with float-float solves, matches the FP64 form state
+    by state within the stated 1e-5, and the two solve arithmetics agree to 1e-11."""
     torch, rexi = env
     N, nlat, nlon, M, B, tau = 127, 192, 384, 256, 64, 7200.0
     al, be, _ = rc.rexi_coefficients(M, 0.2)
@@ -78,14 +79,17 @@ def test_c2_batched_mixed_vs_fp64(env):
     x = gs.synthesise(inputs.random_spectral(N, B, 1001))
     X = torch.from_numpy(x).cuda()
     out = {}
-    for prec in ("fp64", "mixed"):
-        plan = rexi.Plan(N, nlat, nlon, tau=tau, max_batch=B, alpha=al, beta=be, precision=prec)
+    for prec, arith in (("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "fp32x2")):
+        plan = rexi.Plan(N, nlat, nlon, tau=tau, max_batch=B, alpha=al, beta=be, precision=prec,
+                         solve_arith=arith)
         plan.tune(B)
-        out[prec] = plan.step(X).cpu().numpy()
+        out[prec, arith] = plan.step(X).cpu().numpy()
         plan.check_device()
         plan.close()
     ref = gs(x[:2])
     for f in range(3):
-        assert rel(out["fp64"][:2, f], ref[:, f]) < 1e-10
-    worst = max(rel(out["mixed"][b, f], out["fp64"][b, f]) for b in range(B) for f in range(3))
-    assert worst < TOL_MIXED
+        assert rel(out["fp64", "fp64"][:2, f], ref[:, f]) < 1e-10
+    for arith in ("fp64", "fp32x2"):
+        worst = max(rel(out["mixed", arith][b, f], out["fp64", "fp64"][b, f]) for b in range(B) for f in range(3))
+        assert worst < TOL_MIXED
+    assert rel(out["mixed", "fp32x2"], out["mixed", "fp64"]) < 1e-11
