@@ -113,7 +113,15 @@ rexi_status ensure_adjoint_factors(Plan &pl) {
   e = launch_factor_setup(pl, true, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail("adjoint factor setup", e);
-  if (pl.ff) return take_range_error(pl, "adjoint float-float factors");
+  if (pl.ff) {
+    const rexi_status r = take_range_error(pl, "adjoint float-float factors");
+    if (r != REXI_OK) {  // not kept: every adjoint call on this plan fails the same way
+      cudaFree(pl.fac_adj);
+      pl.fac_adj = nullptr;
+      pl.bytes -= n * sizeof(double2);
+      return r;
+    }
+  }
   return REXI_OK;
 }
 
