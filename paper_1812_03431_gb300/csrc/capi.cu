@@ -102,7 +102,7 @@ rexi_status check_io2(const Plan &pl, const void *in, const void *out, int B, bo
 
 rexi_status ensure_adjoint_factors(Plan &pl) {
   if (pl.fac_adj || pl.prm.fsphere) return REXI_OK;
-  const size_t n = (size_t)F_NCOMP * pl.nrows * pl.P;
+  const size_t n = (size_t)fac_ncomp(pl) * pl.nrows * pl.P;
   cudaError_t e = cudaMalloc(&pl.fac_adj, n * sizeof(double2));
   if (e != cudaSuccess) {
     pl.fac_adj = nullptr;

@@ -59,6 +59,21 @@ __device__ __forceinline__ void add(Acc &acc, float xh, float xl) {
   acc.e = __fadd_rn(acc.e, __fadd_rn(t, xl));
 }
 
+// (ah + al)(bh + bl) as an unevaluated pair: the rounded product and its error terms
+__device__ __forceinline__ Acc prod(float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);  // exact error of p
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  return Acc{p, e};
+}
+
+// real r times complex z (both float-float), as an unnormalised pair per component
+__device__ __forceinline__ float4 rscale(float2 r, float4 z) {
+  const Acc a = prod(r.x, r.y, z.x, z.y), b = prod(r.x, r.y, z.z, z.w);
+  return make_float4(a.s, a.e, b.s, b.e);
+}
+
 // complex accumulator
 struct CAcc {
   Acc re, im;
@@ -96,6 +111,16 @@ __device__ __forceinline__ void cadd(CAcc &acc, float4 v) {
 // accumulator or a summand of add it is exact.  Values that are stored and read back
 // within a sweep skip the six-operation TwoSum this way.
 __device__ __forceinline__ float4 raw(const CAcc &a) { return make_float4(a.re.s, a.re.e, a.im.s, a.im.e); }
+
+// complex a b, unnormalised
+__device__ __forceinline__ float4 cmul(float4 a, float4 b) {
+  CAcc r{prod(a.x, a.y, b.x, b.y), prod(a.x, a.y, b.z, b.w)};
+  mac(r.re, -a.z, -a.w, b.z, b.w);
+  mac(r.im, a.z, a.w, b.x, b.y);
+  return raw(r);
+}
+
+__device__ __forceinline__ float4 cconj(float4 a) { return make_float4(a.x, a.y, -a.z, -a.w); }
 
 // normalised value of an accumulator (TwoSum: no condition on |s| against |e|)
 __device__ __forceinline__ float4 norm(const CAcc &a) {

@@ -299,7 +299,22 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
       pl->phi_abf = reinterpret_cast<double2 *>(d);
     }
   } else if (!prm.fsphere) {
-    const size_t nfac = (size_t)F_NCOMP * pl->nrows * P;
+    if (pl->ff && !pl->ffil) {  // compact float-float factors: tau G_n per idx and 1/alpha per pole
+      auto split = [](double x) { const float hi = (float)x; return make_float2(hi, (float)(x - (double)hi)); };
+      std::vector<float2> rows((size_t)NS);
+      for (int m = 0; m <= N; ++m)
+        for (int n = m; n <= N; ++n)
+          rows[(size_t)spec_idx(N, m, n)] = split(tau * (double)n * (n + 1.0) / (a * a));
+      std::vector<float4> ia((size_t)P);
+      for (int k = 0; k < P; ++k) {
+        const cplx v = 1.0 / pl->alpha[k];
+        const float2 re = split(v.real()), im = split(v.imag());
+        ia[(size_t)k] = make_float4(re.x, re.y, im.x, im.y);
+      }
+      if ((e = upload(&pl->ffc_rows, rows, &bytes))) return fail("compact factors", e);
+      if ((e = upload(&pl->ffc_ia, ia, &bytes))) return fail("compact factors", e);
+    }
+    const size_t nfac = (size_t)fac_ncomp(*pl) * pl->nrows * P;
     if ((e = dalloc(&pl->fac_fwd, nfac, &bytes))) return fail("factors", e);
     if ((e = launch_factor_setup(*pl, false, 0))) return fail("factor setup", e);
     if (pl->ff) {
@@ -591,7 +606,7 @@ void free_plan(Plan *pl) {
                   pl->scale_syn_out, pl->mscale_fwd, pl->mscale_c, pl->mscale_adj, pl->mscale_one,
                   pl->zd_syn, pl->zd_ana_adj, pl->zd_one, pl->zd_mone, pl->fft.tw_dev, pl->fft.tw32_dev, pl->four,
                   pl->s_in, pl->s_out, pl->s_ff, pl->partial, pl->yscratch, pl->counter, pl->tc_tab_ana,
-                  pl->tc_tab_syn, pl->tc_work_ana, pl->tc_work_syn, pl->dev_err, pl->phi_zc, pl->phi_q, pl->phi_abf};
+                  pl->tc_tab_syn, pl->tc_work_ana, pl->tc_work_syn, pl->dev_err, pl->phi_zc, pl->phi_q, pl->phi_abf, pl->ffc_rows, pl->ffc_ia};
   for (cudaEvent_t ev : pl->prof_ev) cudaEventDestroy(ev);
   for (void *p : ptrs)
     if (p) cudaFree(p);

@@ -103,6 +103,12 @@ struct FftPlan {
 
 enum FacComp { F_L = 0, F_G, F_E, F_F, F_C, F_BD, F_BAD, F_ZP, F_ZM, F_NCOMP };
 
+// factor c in the compact float-float set (F_G and F_BAD are formed in the sweep: -1)
+__host__ __device__ constexpr int compact_comp(int c) {
+  return c == F_G || c == F_BAD ? -1 : (c < F_G ? c : (c < F_BAD ? c - 1 : c - 2));
+}
+constexpr int F_NCOMPACT = F_NCOMP - 2;
+
 // bits of a plan's device error word (rexi_check_device)
 enum DevErr {
   DEV_ERR_TIMEOUT = 1,  // a bounded wait (tensor-core completion barrier) expired
@@ -179,6 +185,11 @@ struct Plan {
   // warp); otherwise the pole-fastest layout of the binary64 factors, where a warp's lanes
   // hold consecutive poles and its loads coalesce
   bool ffil = false;
+  // float-float plans with the pole-fastest layout keep 7 of the 9 factors (compact_comp):
+  // g = tau G_n / alpha and the Phi weight beta/d' tau Phibar / alpha (adjoint: -tau Phibar /
+  // conj(alpha) and -beta/d' tau G_n / conj(alpha)) are formed in the sweep from these
+  float2 *ffc_rows = nullptr;  // [nspec] tau G_n as float-float values
+  float4 *ffc_ia = nullptr;    // [P] 1/alpha as float-float values
 
   // workspaces (max_batch)
   double2 *four = nullptr;     // [nlat][N+1][3 B] complex (FP64 or FP32 pairs in mixed mode)
@@ -200,6 +211,9 @@ struct Plan {
   std::vector<int> prof_n;           // marks recorded per call
   int prof_calls = 0, prof_cap = 0;
 };
+
+// components stored per (row, pole) for the delta solver's factors of this plan
+inline int fac_ncomp(const Plan &pl) { return pl.ff && !pl.ffil ? F_NCOMPACT : F_NCOMP; }
 
 enum Stage { ST_FFT_FWD = 0, ST_LEG_ANA, ST_SOLVE, ST_REDUCE, ST_LEG_SYN, ST_FFT_INV, ST_TRANS_IN,
              ST_TRANS_OUT, kStages };
@@ -228,6 +242,10 @@ struct SolveView {
   int64_t nspec, nrows;
   const int32_t *slots_m;  // per zonal order slot count (<= slots), or null for slots everywhere
   int ffil;                // float-float factors interleaved (Plan::ffil)
+  int adj;                 // adjoint factors (the compact float-float set forms g and the Phi weight per direction)
+  const float2 *ffc_rows;  // compact float-float factors: tau G_n per idx
+  const float4 *ffc_ia;    // compact float-float factors: 1/alpha per pole
+  float2 ffc_tpb;          // tau Phibar as a float-float value
 };
 SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, double2 *part, int B,
                     int pole_begin, int pole_end);

@@ -74,6 +74,8 @@ struct SetupArgs {
   double tau, phibar, q;  // q = 2 Omega tau
   int adjoint;
   int interleaved;      // float-float plans: the nine factors of a (row, pole) are adjacent
+  int compact;          // float-float plans, pole-fastest: the 7 factors of compact_comp (g and
+                        // the Phi weight are formed in the sweep)
 };
 
 __device__ __forceinline__ int64_t sidx(int N, int m, int n) { return (int64_t)m * (2 * N + 3 - m) / 2 + (n - m); }
@@ -105,9 +107,13 @@ __global__ void factor_setup_kernel(SetupArgs a) {
   const int64_t NR = a.nrows, P = a.P;
   double2 *F = a.fac;
   auto at = [&](int comp, int64_t row) -> int64_t {
+    if (a.compact) comp = compact_comp(comp);
     return a.interleaved ? (row * P + k) * F_NCOMP + comp : ((int64_t)comp * NR + row) * P + k;
   };
-  auto put = [&](int comp, int64_t row, double2 v) { F[at(comp, row)] = v; };
+  auto put = [&](int comp, int64_t row, double2 v) {
+    if (a.compact && compact_comp(comp) < 0) return;  // formed in the sweep
+    F[at(comp, row)] = v;
+  };
   const double2 one = make_double2(1.0, 0.0);
 
   // first pass: d' and l, store d' temporarily in the F_C slot
@@ -312,6 +318,20 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
   const int64_t RS = IL ? (int64_t)a.P * F_NCOMP : (int64_t)a.P;
   const int64_t CS = IL ? 1 : a.nrows * a.P;
   const int N = a.N, B = a.B;
+  // factor slots: all nine when interleaved; the compact seven otherwise (IL false), where
+  // g and the Phi weight are formed from 1/alpha (conj in the adjoint) and per-row reals
+  constexpr int oL = IL ? F_L : compact_comp(F_L), oE = IL ? F_E : compact_comp(F_E),
+                oF = IL ? F_F : compact_comp(F_F), oC = IL ? F_C : compact_comp(F_C),
+                oBD = IL ? F_BD : compact_comp(F_BD), oZP = IL ? F_ZP : compact_comp(F_ZP),
+                oZM = IL ? F_ZM : compact_comp(F_ZM);
+  float4 ia[KC], cpw[KC];  // compact: 1/alpha per pole; forward Phi weight factor ia tau Phibar
+  if constexpr (!IL) {
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      ia[c] = a.adj ? ff::cconj(__ldg(a.ffc_ia + k[c])) : __ldg(a.ffc_ia + k[c]);
+      cpw[c] = ff::rscale(a.ffc_tpb, ia[c]);
+    }
+  }
   const float4 *fk[KC];
   for (int c = 0; c < KC; ++c)
     fk[c] = reinterpret_cast<const float4 *>(a.fac) + (IL ? (row0 * a.P + k[c]) * F_NCOMP : row0 * a.P + k[c]);
@@ -334,7 +354,7 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
         l2_prefetch(f + 3);
       } else {
 #pragma unroll
-        for (int q = F_L; q <= F_F; ++q) l2_prefetch(f + q * CS);
+        for (int q = oL; q <= oF; ++q) l2_prefetch(f + q * CS);
       }
     }
   };
@@ -349,7 +369,7 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
         l2_prefetch(f + 8);
       } else {
 #pragma unroll
-        for (int q = F_C; q <= F_ZM; ++q) l2_prefetch(f + q * CS);
+        for (int q = oC; q <= oZM; ++q) l2_prefetch(f + q * CS);
       }
       l2_prefetch(ybuf + ((int64_t)i * KC + c) * 32);
     }
@@ -382,14 +402,20 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
     znc = znn;
     d0c = d0n;
     p0c = p0n;
+    float4 rp0 = zero;  // compact: (tau G_n, or -tau Phibar in the adjoint) Phi0
+    if constexpr (!IL) {
+      const float2 rg = a.adj ? make_float2(-a.ffc_tpb.x, -a.ffc_tpb.y) : __ldg(a.ffc_rows + base_idx + n0 + 2 * i);
+      rp0 = ff::rscale(rg, p0);
+    }
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;
       ff::CAcc y = ff::cacc(d0);
-      ff::cmsub(y, ldf(f + F_G * CS), p0);
-      ff::cmsub(y, ldf(f + F_E * CS), zprev);
-      ff::cmsub(y, ldf(f + F_F * CS), zn);
-      ff::cmsub(y, ldf(f + F_L * CS), yprev[c]);
+      if constexpr (IL) ff::cmsub(y, ldf(f + F_G * CS), p0);
+      else ff::cmsub(y, ia[c], rp0);
+      ff::cmsub(y, ldf(f + oE * CS), zprev);
+      ff::cmsub(y, ldf(f + oF * CS), zn);
+      ff::cmsub(y, ldf(f + oL * CS), yprev[c]);
       const float4 yv = ff::raw(y);
       ybuf[((int64_t)i * KC + c) * 32] = yv;
       yprev[c] = yv;
@@ -421,7 +447,7 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       ff::CAcc w = ff::cacc(yc[c]);
-      ff::cmsub(w, ldf(fk[c] + (int64_t)i * RS + F_C * CS), wnext[c]);
+      ff::cmsub(w, ldf(fk[c] + (int64_t)i * RS + oC * CS), wnext[c]);
       wv[c] = ff::raw(w);
     }
     ff::CAcc accD = ff::cacc(pdc);
@@ -430,11 +456,25 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
     for (int c = 0; c < KC; ++c) yc[c] = yn[c];
     pdc = pdn;
     ppc = ppn;
+    if constexpr (IL) {
 #pragma unroll
-    for (int c = 0; c < KC; ++c) {
-      const float4 *f = fk[c] + (int64_t)i * RS;
-      ff::cmac(accD, ldf(f + F_BD * CS), wv[c]);
-      ff::cmac(accP, ldf(f + F_BAD * CS), wv[c]);
+      for (int c = 0; c < KC; ++c) {
+        const float4 *f = fk[c] + (int64_t)i * RS;
+        ff::cmac(accD, ldf(f + F_BD * CS), wv[c]);
+        ff::cmac(accP, ldf(f + F_BAD * CS), wv[c]);
+      }
+    } else {  // u = (beta/d') w; delta += u, Phi += (Phi weight / (beta/d')) u
+      float2 rrow = make_float2(0.f, 0.f);  // adjoint: -tau G_n
+      if (a.adj) {
+        const float2 r = __ldg(a.ffc_rows + ix);
+        rrow = make_float2(-r.x, -r.y);
+      }
+#pragma unroll
+      for (int c = 0; c < KC; ++c) {
+        const float4 u = ff::cmul(ldf(fk[c] + (int64_t)i * RS + oBD * CS), wv[c]);
+        ff::cadd(accD, u);
+        ff::cmac(accP, a.adj ? ff::rscale(rrow, ia[c]) : cpw[c], u);
+      }
     }
     pDel[ix * rstride] = ff::raw(accD);
     pPhi[ix * rstride] = ff::raw(accP);
@@ -442,14 +482,14 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
       ff::CAcc accZ = first ? ff::czero() : ff::cacc(pZeta[(ix + 1) * rstride]);
 #pragma unroll
       for (int c = 0; c < KC; ++c) {
-        ff::cmac(accZ, ldf(fk[c] + (int64_t)i * RS + F_ZP * CS), wv[c]);
+        ff::cmac(accZ, ldf(fk[c] + (int64_t)i * RS + oZP * CS), wv[c]);
         ff::cmac(accZ, zmnext[c], wnext[c]);
       }
       pZeta[(ix + 1) * rstride] = ff::raw(accZ);
     }
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      zmnext[c] = ldf(fk[c] + (int64_t)i * RS + F_ZM * CS);
+      zmnext[c] = ldf(fk[c] + (int64_t)i * RS + oZM * CS);
       wnext[c] = wv[c];
     }
   }
@@ -852,10 +892,11 @@ cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st) {
   a.q = 2.0 * pl.prm.omega * pl.prm.tau;
   a.adjoint = adjoint ? 1 : 0;
   a.interleaved = pl.ffil ? 1 : 0;
+  a.compact = pl.ff && !pl.ffil ? 1 : 0;
   int64_t total = (int64_t)a.P * a.nsys;
   factor_setup_kernel<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && pl.ff) e = launch_to_ff(pl, a.fac, (int64_t)F_NCOMP * pl.nrows * pl.P, st);
+  if (e == cudaSuccess && pl.ff) e = launch_to_ff(pl, a.fac, (int64_t)fac_ncomp(pl) * pl.nrows * pl.P, st);
   return e;
 }
 
@@ -887,6 +928,16 @@ rexi_status take_range_error(Plan &pl, const char *what) {
   return REXI_ERANGE;
 }
 
+// the per-plan data of the compact float-float factor set (unused otherwise)
+void set_compact_view(const Plan &pl, bool adjoint, SolveView &v) {
+  const double tpb = pl.prm.tau * pl.prm.gravity * pl.prm.mean_depth;
+  const float hi = (float)tpb;
+  v.adj = adjoint ? 1 : 0;
+  v.ffc_rows = pl.ffc_rows;
+  v.ffc_ia = pl.ffc_ia;
+  v.ffc_tpb = make_float2(hi, (float)(tpb - (double)hi));
+}
+
 SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, double2 *part, int B,
                     int pole_begin, int pole_end) {
   SolveView v;
@@ -902,6 +953,7 @@ SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double
   v.slots = lay.slots;
   v.slots_m = lay.slots_m_dev;
   v.ffil = pl.ffil ? 1 : 0;
+  set_compact_view(pl, adjoint, v);
   v.pole_begin = pole_begin;
   v.pole_end = pole_end;
   v.nspec = pl.nspec;
@@ -1100,6 +1152,7 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
     a.v.slots = slots;
     a.v.slots_m = nullptr;
     a.v.ffil = pl.ffil ? 1 : 0;
+    set_compact_view(pl, false, a.v);
     a.v.pole_begin = 0;
     a.v.pole_end = pl.P;
     a.v.nspec = pl.nspec;
