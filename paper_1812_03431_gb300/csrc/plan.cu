@@ -299,7 +299,7 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
       pl->phi_abf = reinterpret_cast<double2 *>(d);
     }
   } else if (!prm.fsphere) {
-    if (pl->ff && !pl->ffil) {  // compact float-float factors: tau G_n per idx and 1/alpha per pole
+    if (pl->ff) {  // compact float-float factors: tau G_n per idx and 1/alpha per pole
       auto split = [](double x) { const float hi = (float)x; return make_float2(hi, (float)(x - (double)hi)); };
       std::vector<float2> rows((size_t)NS);
       for (int m = 0; m <= N; ++m)

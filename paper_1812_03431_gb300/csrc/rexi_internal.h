@@ -137,7 +137,8 @@ struct Plan {
   int32_t *m_of_dev = nullptr;
 
   // solve factors (forward and adjoint): [F_NCOMP][nrows][P] double2; float-float plans
-  // hold float-float values (float4 in the double2 slots), as [nrows][P][F_NCOMP] when ffil
+  // hold the compact set as float-float values (float4 in the double2 slots):
+  // [F_NCOMPACT][nrows][P], or [nrows][P][F_NCOMPACT] when ffil
   double2 *fac_fwd = nullptr, *fac_adj = nullptr;
   double2 *alpha_dev = nullptr, *beta_dev = nullptr;
   // pole-independent parts: W[idx] = sum_k beta_k/s_{k,n} (zeta), scalar S_Phi
@@ -185,9 +186,9 @@ struct Plan {
   // warp); otherwise the pole-fastest layout of the binary64 factors, where a warp's lanes
   // hold consecutive poles and its loads coalesce
   bool ffil = false;
-  // float-float plans with the pole-fastest layout keep 7 of the 9 factors (compact_comp):
-  // g = tau G_n / alpha and the Phi weight beta/d' tau Phibar / alpha (adjoint: -tau Phibar /
-  // conj(alpha) and -beta/d' tau G_n / conj(alpha)) are formed in the sweep from these
+  // float-float plans keep 7 of the 9 factors (compact_comp): g = tau G_n / alpha and the
+  // Phi weight beta/d' tau Phibar / alpha (adjoint: -tau Phibar / conj(alpha) and
+  // -beta/d' tau G_n / conj(alpha)) are formed in the sweep from these
   float2 *ffc_rows = nullptr;  // [nspec] tau G_n as float-float values
   float4 *ffc_ia = nullptr;    // [P] 1/alpha as float-float values
 
@@ -212,8 +213,9 @@ struct Plan {
   int prof_calls = 0, prof_cap = 0;
 };
 
-// components stored per (row, pole) for the delta solver's factors of this plan
-inline int fac_ncomp(const Plan &pl) { return pl.ff && !pl.ffil ? F_NCOMPACT : F_NCOMP; }
+// components stored per (row, pole) for the delta solver's factors of this plan (the
+// compact set for float-float plans)
+inline int fac_ncomp(const Plan &pl) { return pl.ff ? F_NCOMPACT : F_NCOMP; }
 
 enum Stage { ST_FFT_FWD = 0, ST_LEG_ANA, ST_SOLVE, ST_REDUCE, ST_LEG_SYN, ST_FFT_INV, ST_TRANS_IN,
              ST_TRANS_OUT, kStages };
@@ -234,7 +236,7 @@ cudaError_t launch_solve(Plan &pl, const SolveLayout &lay, bool adjoint, const d
 // One plan's view for the solve kernels: factors, internal states, partial sums,
 // systems and the lane layout of its batch.
 struct SolveView {
-  const double2 *fac;   // [F_NCOMP][nrows][P] (float-float plans with ffil: [nrows][P][F_NCOMP])
+  const double2 *fac;   // [F_NCOMP][nrows][P] (float-float: the compact set, interleaved when ffil)
   const double2 *sin;   // [3][nspec][B]
   double2 *part;        // [3][nspec][slots][B]
   const int4 *sys;      // per (m, p): {m, n0, len, row0}

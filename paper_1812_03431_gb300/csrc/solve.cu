@@ -67,15 +67,16 @@ __device__ __forceinline__ double2 cfma(double2 acc, double2 a, double2 b) {
 struct SetupArgs {
   const double *coef;   // [nspec][4] = sigma, ct, dt, G
   const double2 *alpha, *beta;
-  double2 *fac;         // [F_NCOMP][nrows][P], or [nrows][P][F_NCOMP] when interleaved
+  double2 *fac;         // [F_NCOMP][nrows][P]; float-float plans: the F_NCOMPACT set (compact),
+                        // as [F_NCOMPACT][nrows][P] or interleaved [nrows][P][F_NCOMPACT]
   const int4 *sys;      // per system (m, p): {m, n0, len, row0}
   int nsys, P, N;
   int64_t nrows;
   double tau, phibar, q;  // q = 2 Omega tau
   int adjoint;
-  int interleaved;      // float-float plans: the nine factors of a (row, pole) are adjacent
-  int compact;          // float-float plans, pole-fastest: the 7 factors of compact_comp (g and
-                        // the Phi weight are formed in the sweep)
+  int interleaved;      // float-float plans: the factors of a (row, pole) are adjacent
+  int compact;          // float-float plans: the 7 factors of compact_comp (g and the Phi
+                        // weight are formed in the sweep)
 };
 
 __device__ __forceinline__ int64_t sidx(int N, int m, int n) { return (int64_t)m * (2 * N + 3 - m) / 2 + (n - m); }
@@ -108,7 +109,7 @@ __global__ void factor_setup_kernel(SetupArgs a) {
   double2 *F = a.fac;
   auto at = [&](int comp, int64_t row) -> int64_t {
     if (a.compact) comp = compact_comp(comp);
-    return a.interleaved ? (row * P + k) * F_NCOMP + comp : ((int64_t)comp * NR + row) * P + k;
+    return a.interleaved ? (row * P + k) * F_NCOMPACT + comp : ((int64_t)comp * NR + row) * P + k;
   };
   auto put = [&](int comp, int64_t row, double2 v) {
     if (a.compact && compact_comp(comp) < 0) return;  // formed in the sweep
@@ -313,28 +314,24 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
                                                float4 *pZeta, float4 *pDel, int64_t rstride, bool first,
                                                float4 *ybuf) {
   constexpr int D = 3;  // rows prefetched ahead into L2
-  // factor (comp, row i, pole c) at fk[c] + i RS + comp CS: interleaved (IL) rows of
-  // P x F_NCOMP values, or the pole-fastest layout [F_NCOMP][nrows][P]
-  const int64_t RS = IL ? (int64_t)a.P * F_NCOMP : (int64_t)a.P;
+  // the compact factor set (compact_comp): factor (comp, row i, pole c) at
+  // fk[c] + i RS + comp CS, interleaved (IL) rows of P x F_NCOMPACT values or the
+  // pole-fastest layout [F_NCOMPACT][nrows][P]; g and the Phi weight are formed from 1/alpha
+  // (conj in the adjoint) and per-row reals
+  const int64_t RS = IL ? (int64_t)a.P * F_NCOMPACT : (int64_t)a.P;
   const int64_t CS = IL ? 1 : a.nrows * a.P;
   const int N = a.N, B = a.B;
-  // factor slots: all nine when interleaved; the compact seven otherwise (IL false), where
-  // g and the Phi weight are formed from 1/alpha (conj in the adjoint) and per-row reals
-  constexpr int oL = IL ? F_L : compact_comp(F_L), oE = IL ? F_E : compact_comp(F_E),
-                oF = IL ? F_F : compact_comp(F_F), oC = IL ? F_C : compact_comp(F_C),
-                oBD = IL ? F_BD : compact_comp(F_BD), oZP = IL ? F_ZP : compact_comp(F_ZP),
-                oZM = IL ? F_ZM : compact_comp(F_ZM);
-  float4 ia[KC], cpw[KC];  // compact: 1/alpha per pole; forward Phi weight factor ia tau Phibar
-  if constexpr (!IL) {
+  constexpr int oL = compact_comp(F_L), oE = compact_comp(F_E), oF = compact_comp(F_F), oC = compact_comp(F_C),
+                oBD = compact_comp(F_BD), oZP = compact_comp(F_ZP), oZM = compact_comp(F_ZM);
+  float4 ia[KC], cpw[KC];  // 1/alpha per pole; the forward Phi weight's factor ia tau Phibar
 #pragma unroll
-    for (int c = 0; c < KC; ++c) {
-      ia[c] = a.adj ? ff::cconj(__ldg(a.ffc_ia + k[c])) : __ldg(a.ffc_ia + k[c]);
-      cpw[c] = ff::rscale(a.ffc_tpb, ia[c]);
-    }
+  for (int c = 0; c < KC; ++c) {
+    ia[c] = a.adj ? ff::cconj(__ldg(a.ffc_ia + k[c])) : __ldg(a.ffc_ia + k[c]);
+    cpw[c] = ff::rscale(a.ffc_tpb, ia[c]);
   }
   const float4 *fk[KC];
   for (int c = 0; c < KC; ++c)
-    fk[c] = reinterpret_cast<const float4 *>(a.fac) + (IL ? (row0 * a.P + k[c]) * F_NCOMP : row0 * a.P + k[c]);
+    fk[c] = reinterpret_cast<const float4 *>(a.fac) + (IL ? (row0 * a.P + k[c]) * F_NCOMPACT : row0 * a.P + k[c]);
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   // Every row's data (states, factors, sweep intermediates, slot partials) is prefetched
   // into L2 D rows ahead, so that the row's own loads find it there; the prefetches hold
@@ -349,9 +346,9 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;
-      if (IL) {  // factors 0..3 of the 144-byte record: at most two lines
+      if (IL) {  // factors 0..2 of the 112-byte record: at most two lines
         l2_prefetch(f);
-        l2_prefetch(f + 3);
+        l2_prefetch(f + 2);
       } else {
 #pragma unroll
         for (int q = oL; q <= oF; ++q) l2_prefetch(f + q * CS);
@@ -364,9 +361,9 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;  // factors 4..8
-      if (IL) {
-        l2_prefetch(f + 4);
-        l2_prefetch(f + 8);
+      if (IL) {  // factors 3..6
+        l2_prefetch(f + 3);
+        l2_prefetch(f + 6);
       } else {
 #pragma unroll
         for (int q = oC; q <= oZM; ++q) l2_prefetch(f + q * CS);
@@ -403,7 +400,7 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
     d0c = d0n;
     p0c = p0n;
     float4 rp0 = zero;  // compact: (tau G_n, or -tau Phibar in the adjoint) Phi0
-    if constexpr (!IL) {
+    {
       const float2 rg = a.adj ? make_float2(-a.ffc_tpb.x, -a.ffc_tpb.y) : __ldg(a.ffc_rows + base_idx + n0 + 2 * i);
       rp0 = ff::rscale(rg, p0);
     }
@@ -411,8 +408,7 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
     for (int c = 0; c < KC; ++c) {
       const float4 *f = fk[c] + (int64_t)i * RS;
       ff::CAcc y = ff::cacc(d0);
-      if constexpr (IL) ff::cmsub(y, ldf(f + F_G * CS), p0);
-      else ff::cmsub(y, ia[c], rp0);
+      ff::cmsub(y, ia[c], rp0);
       ff::cmsub(y, ldf(f + oE * CS), zprev);
       ff::cmsub(y, ldf(f + oF * CS), zn);
       ff::cmsub(y, ldf(f + oL * CS), yprev[c]);
@@ -456,14 +452,7 @@ __device__ __forceinline__ void sweep_poles_ff(const SolveView &a, const int (&k
     for (int c = 0; c < KC; ++c) yc[c] = yn[c];
     pdc = pdn;
     ppc = ppn;
-    if constexpr (IL) {
-#pragma unroll
-      for (int c = 0; c < KC; ++c) {
-        const float4 *f = fk[c] + (int64_t)i * RS;
-        ff::cmac(accD, ldf(f + F_BD * CS), wv[c]);
-        ff::cmac(accP, ldf(f + F_BAD * CS), wv[c]);
-      }
-    } else {  // u = (beta/d') w; delta += u, Phi += (Phi weight / (beta/d')) u
+    {  // u = (beta/d') w; delta += u, Phi += (Phi weight / (beta/d')) u
       float2 rrow = make_float2(0.f, 0.f);  // adjoint: -tau G_n
       if (a.adj) {
         const float2 r = __ldg(a.ffc_rows + ix);
@@ -892,7 +881,7 @@ cudaError_t launch_factor_setup(Plan &pl, bool adjoint, cudaStream_t st) {
   a.q = 2.0 * pl.prm.omega * pl.prm.tau;
   a.adjoint = adjoint ? 1 : 0;
   a.interleaved = pl.ffil ? 1 : 0;
-  a.compact = pl.ff && !pl.ffil ? 1 : 0;
+  a.compact = pl.ff ? 1 : 0;
   int64_t total = (int64_t)a.P * a.nsys;
   factor_setup_kernel<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
