@@ -202,9 +202,14 @@ rexi_status rexi_integrate(rexi_plan *plan, const void *in_dev, void *out_dev, i
  *   - Sizes whose scratch would exceed 64 MiB (3 nspec batch x 32 B for the two
  *     state copies, plus the pole-slot partial sums, the sweep buffers of four
  *     warps per SM and the work list) return REXI_EINVAL with the needed size.
+ *     The sweep buffers grow with the GPU's number of SMs and with N but not with
+ *     the batch, so the largest truncation served at all depends on the GPU (on a
+ *     152-SM GB300, N up to about 170 for one state); the message says when no
+ *     batch fits.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current and caches it for the life
+ *     of the device context; make that first call before any stream capture.
+ *     First calls from several host threads are serialised by a lock.
  *   - All calls share the one array and it keeps the last call's contents; the
  *     work counter is cleared on the stream at the start of every call.  Calls
  *     that overlap on the GPU (other streams, other threads) race on it.
@@ -287,6 +292,14 @@ rexi_status rexi_profile_read(rexi_plan *plan, double *stage_ms, int32_t n, int3
  * last check: such values become infinite in float-float, and the outputs of that
  * step are not finite. */
 rexi_status rexi_check_device(rexi_plan *plan);
+
+/* Test hook (no counterpart in the paper): ORs `bits` (1: a bounded device-side wait
+ * expired, 2: a float-float range error; other bits are rejected) into the plan's
+ * device error word from the host, as a kernel that gave up would, so that the
+ * reporting path of rexi_check_device can be tested without making a kernel wait
+ * out its limit.  Synchronises the device.  REXI_EINVAL for a NULL plan or unknown
+ * bits. */
+rexi_status rexi_inject_device_error(rexi_plan *plan, int32_t bits);
 
 /* Free everything the plan holds; NULL-safe.  The caller synchronises streams
  * that still use the plan first. */

@@ -550,6 +550,21 @@ rexi_status rexi_check_device(rexi_plan *plan) {
   return REXI_OK;
 }
 
+rexi_status rexi_inject_device_error(rexi_plan *plan, int32_t bits) {
+  if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
+  if (bits <= 0 || (bits & ~(DEV_ERR_TIMEOUT | DEV_ERR_RANGE))) {
+    set_error("rexi_inject_device_error: bits must be a non-empty set of 1 (timeout) and 2 (range)");
+    return REXI_EINVAL;
+  }
+  Plan &pl = *plan->pl;
+  cudaError_t e = cudaDeviceSynchronize();
+  int flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, pl.dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  flag |= bits;
+  if (e == cudaSuccess) e = cudaMemcpy(pl.dev_err, &flag, sizeof(int), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? REXI_OK : cuda_fail("rexi_inject_device_error", e);
+}
+
 const char *rexi_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

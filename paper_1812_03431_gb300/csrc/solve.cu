@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <type_traits>
 
@@ -1051,7 +1052,11 @@ constexpr size_t kStaticScratchBytes = (size_t)64 << 20;  // 64 MiB, held by eve
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void *g_static_addr[kMaxDevices] = {};  // device address of g_static_scratch, per device ordinal
+// device address of g_static_scratch per device ordinal, looked up once per device; the
+// mutex orders first calls that race from several host threads.  The address stays valid
+// for the life of the device context (a cudaDeviceReset ends it, together with every plan).
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices] = {};
 
 __global__ void static_items_kernel(WorkItem *items, int nitems, int nb, int bw, const int4 *sys) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1072,36 +1077,59 @@ rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t
     set_error("rexi_step_static: no usable current device");
     return REXI_ECUDA;
   }
-  // scratch layout for this call (one pole group; lanes (state, parity, pole slot))
-  int bw = 1;
-  while (bw < B && bw < 16) bw *= 2;
-  const int kk = 32 / (2 * bw);
-  const int slots = std::min(kk, pl.P);
-  const int nb = (B + bw - 1) / bw;
-  const int nitems = (pl.N + 1) * nb;
+  // scratch layout for a batch (one pole group; lanes (state, parity, pole slot))
+  struct StaticLayout {
+    int bw, kk, slots, nb, nitems;
+    size_t state_b, part_b, y_b, item_b, ffstate_b, need;
+  };
+  auto layout_of = [&pl](int nb_states) {
+    StaticLayout L;
+    L.bw = 1;
+    while (L.bw < nb_states && L.bw < 16) L.bw *= 2;
+    L.kk = 32 / (2 * L.bw);
+    L.slots = std::min(L.kk, pl.P);
+    L.nb = (nb_states + L.bw - 1) / L.bw;
+    L.nitems = (pl.N + 1) * L.nb;
+    const int warps = pl.num_sms * 4;
+    L.state_b = align256((size_t)3 * pl.nspec * nb_states * sizeof(double2));
+    L.part_b = align256((size_t)3 * pl.nspec * L.slots * nb_states * sizeof(double2));
+    L.y_b = align256((size_t)warps * pl.lmax * sweep_width(pl.ff) * 32 * sizeof(double2));
+    L.item_b = align256((size_t)L.nitems * sizeof(WorkItem));
+    L.ffstate_b = pl.ff ? L.state_b : 0;  // float-float copy of the input states
+    L.need = 2 * L.state_b + L.part_b + L.y_b + L.item_b + 256 + L.ffstate_b;
+    return L;
+  };
+  const StaticLayout SL = layout_of(B);
+  const int bw = SL.bw, slots = SL.slots, nb = SL.nb, nitems = SL.nitems;
   const int warps = pl.num_sms * 4;
-  const size_t state_b = align256((size_t)3 * pl.nspec * B * sizeof(double2));
-  const size_t part_b = align256((size_t)3 * pl.nspec * slots * B * sizeof(double2));
-  const size_t y_b = align256((size_t)warps * pl.lmax * sweep_width(pl.ff) * 32 * sizeof(double2));
-  const size_t item_b = align256((size_t)nitems * sizeof(WorkItem));
-  const size_t ffstate_b = pl.ff ? state_b : 0;  // float-float copy of the input states
-  const size_t need = 2 * state_b + part_b + y_b + item_b + 256 + ffstate_b;
-  if (need > kStaticScratchBytes) {
-    set_error("rexi_step_static: this truncation and batch need " + std::to_string(need) +
+  const size_t state_b = SL.state_b, part_b = SL.part_b, y_b = SL.y_b, item_b = SL.item_b;
+  if (SL.need > kStaticScratchBytes) {
+    // the sweep buffers (four warps per SM) do not shrink with the batch: when even one
+    // state does not fit, no batch does
+    const bool any_batch = layout_of(1).need > kStaticScratchBytes;
+    set_error("rexi_step_static: this truncation and batch need " + std::to_string(SL.need) +
               " bytes of scratch, above the fixed limit of " + std::to_string(kStaticScratchBytes) +
-              " bytes (64 MiB); use rexi_step or a smaller batch");
+              " bytes (64 MiB); " +
+              (any_batch ? std::string("this truncation is not supported at any batch size on this GPU (the "
+                                       "sweep buffers grow with its number of SMs); use rexi_step")
+                         : std::string("use rexi_step or a smaller batch")));
     return REXI_EINVAL;
   }
-  if (!g_static_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error(std::string("rexi_step_static: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-      return REXI_ECUDA;
+  void *addr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_static_scratch);
+      if (e != cudaSuccess || !p) {
+        set_error(std::string("rexi_step_static: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+        return REXI_ECUDA;
+      }
+      g_static_addr[dev] = p;
     }
-    g_static_addr[dev] = p;
+    addr = g_static_addr[dev];
   }
-  unsigned char *base = static_cast<unsigned char *>(g_static_addr[dev]);
+  unsigned char *base = static_cast<unsigned char *>(addr);
   double2 *s_in = reinterpret_cast<double2 *>(base);
   double2 *s_out = reinterpret_cast<double2 *>(base + state_b);
   double2 *part = reinterpret_cast<double2 *>(base + 2 * state_b);

@@ -69,6 +69,8 @@ SIGNATURES = {
     "rexi_check_device": (_I32, [_VP]),
     "rexi_destroy": (None, [_VP]),
     "rexi_last_error": (ctypes.c_char_p, []),
+    "rexi_measure_fp64_fma": (_I32, [_I32, _DP, _DP, _VP]),
+    "rexi_inject_device_error": (_I32, [_VP, _I32]),
 }
 
 
@@ -122,6 +124,15 @@ def rexi_coefficients(M, h, normalize=True):
         M, h, int(normalize), al.ctypes.data_as(_DP), be.ctypes.data_as(_DP), ctypes.byref(n),
         ctypes.byref(eps)))
     return al.view(np.complex128)[: n.value].copy(), be.view(np.complex128)[: n.value].copy(), eps.value
+
+
+def rexi_measure_fp64_fma(reps=5, stream=None):
+    """Measured binary64 FMA rate of the current device (TFLOP/s, best of ``reps``
+    launches) and that launch's milliseconds (include/rexi_measure.h)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check("rexi_measure_fp64_fma", load().rexi_measure_fp64_fma(int(reps), ctypes.byref(tf), ctypes.byref(ms),
+                                                                  _stream_handle(stream)))
+    return tf.value, ms.value
 
 
 def _stream_handle(stream):
@@ -308,6 +319,11 @@ class Plan:
         """Raise RexiError(REXI_ETIMEOUT) if a bounded device wait of this plan expired, or
         RexiError(REXI_ERANGE) if a float-float solve met a value beyond binary32's range."""
         _check("rexi_check_device", load().rexi_check_device(self._h))
+
+    def inject_device_error(self, bits):
+        """rexi_inject_device_error: set error bits (1 timeout, 2 range) in the plan's device
+        error word from the host, for tests of check_device."""
+        _check("rexi_inject_device_error", load().rexi_inject_device_error(self._h, int(bits)))
 
     STAGES = ["fft_fwd", "leg_ana", "solve", "reduce", "leg_syn", "fft_inv", "transpose_in", "transpose_out"]
 

@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads and exports every symbol include/rexi.h declares (no GPU)."""
+"""The C-ABI library builds, loads and exports every symbol include/*.h declares (no GPU)."""
 import ctypes
 import os
 import re
@@ -10,9 +10,10 @@ from conftest import ROOT
 
 
 def header_functions():
-    src = open(os.path.join(ROOT, "include", "rexi.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(rexi_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(rexi_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")

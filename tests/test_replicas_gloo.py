@@ -65,5 +65,5 @@ def test_kernel_rooflines_arithmetic():
     assert k["solve"]["unit"] == "Tops/s" and k["reduce"]["unit"] == "GB/s"
     ns = (W["N"] + 1) * (W["N"] + 2) // 2
     assert k["reduce"]["algorithmic"] == 34 * 3 * ns * W["batch"] * 16
-    assert [f[0] for f in bench.FORMS] == ["mixed_fp32x2", "mixed", "fp64"]
+    assert [f[0] for f in bench.FORMS] == ["mixed", "fp64", "ff_solve"]  # the chosen form first
     assert bench.rows_of(341) == 58652
