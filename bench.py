@@ -62,7 +62,7 @@ FF_OPS_PER_ROW = 36 * 12
 # batch 16, by (pole slots, layout shape); traffic per row is constant, so a launch of the
 # bench workload moves this times rows(T341) / rows(T170).  Re-captured after each change
 # of the solve kernel.
-SOLVE_TRAFFIC_T170 = {(32, 0): 12.64e9, (32, 1): 12.58e9}
+SOLVE_TRAFFIC_T170 = {(32, 0): 12.64e9, (32, 1): 12.58e9, (0, 2): None}  # (0, 2): the fused solve
 SOLVE_FF_TRAFFIC_T170 = {(32, 0): 11.64e9}  # the float-float kernel (solve_kernel<true>)
 
 
@@ -437,6 +437,8 @@ def main():
                     help="auto: time every form, the first (chosen) one gives value")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle's step of state 0 (error vs oracle)")
+    ap.add_argument("--no-fp64-peak", action="store_true",
+                    help="skip measuring the FP64 FMA rate (the roofline then divides by the derived rate)")
     ap.add_argument("--no-phi-solver", action="store_true",
                     help="skip timing the paper's geopotential-only solver next to the default one")
     ap.add_argument("--workload", default="t341_b16", choices=sorted(WORKLOADS),
@@ -502,10 +504,12 @@ def main():
                              "elimination at the highest degrees; compared with the %s form" % name}
 
     # the measured FP64 FMA rate: the solve's roofline divides by it
-    clocks = ClockSampler(local)
-    clocks.start()
-    fp64_tf, fp64_ms = rexi.rexi_measure_fp64_fma(5)
-    fp64_clocks = clocks.stop()
+    fp64_tf, fp64_ms, fp64_clocks = None, None, None
+    if not args.no_fp64_peak:
+        clocks = ClockSampler(local)
+        clocks.start()
+        fp64_tf, fp64_ms = rexi.rexi_measure_fp64_fma(5)
+        fp64_clocks = clocks.stop()
 
     chosen = forms[0][0]
     r = results[chosen]
@@ -517,19 +521,24 @@ def main():
         traffic_t170, kname = SOLVE_FF_TRAFFIC_T170, "solve_kernel<true> (float-float banded solves + pole sum)"
         roof_unit, peak_source = "Tops/s", "derived: 152 SMs x 128 FP32 lanes x sm_max_mhz (ops = adds, mults, FMAs)"
     else:
-        amount, peak = FLOPS_PER_ROW * B * P * rows_of(W["N"]), fp64_tf
+        amount, peak = FLOPS_PER_ROW * B * P * rows_of(W["N"]), fp64_tf or fp64_peak_tflops(sm_mhz)
         traffic_t170, kname = SOLVE_TRAFFIC_T170, "solve_kernel<false> (FP64 banded solves + pole sum)"
-        roof_unit, peak_source = "TFLOP/s", "measured: rexi_measure_fp64_fma, best of 5 (FP64 FMA chains)"
+        roof_unit = "TFLOP/s"
+        peak_source = ("measured: rexi_measure_fp64_fma, best of 5 per shape (FP64 FMA chains)" if fp64_tf else
+                       "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz")
     achieved = amount / (solve_ms * 1e-3) / 1e12
     tkey = min(traffic_t170, key=lambda k: (k[1] != r["shape"], abs(k[0] - r["slots"])))
-    traffic = traffic_t170[tkey] * rows_of(W["N"]) / rows_of(170)
+    traffic = traffic_t170[tkey] * rows_of(W["N"]) / rows_of(170) if traffic_t170[tkey] else None
+    if r["shape"] == 2:
+        kname = "solve_fused_kernel (FP64 banded solves, beta-weighted pole sum on chip)"
     dtypes = {"mixed": "f64 solves + pole sum; 3xtf32 legendre; f32 fft", "fp64": "f64",
               "ff_solve": "f64 i/o; float-float (2 x f32) solves + pole sum; 3xtf32 legendre; f32 fft"}
     metric = METRIC if default_workload else "REXI steps/s at T%d, K=%d poles, %d state%s: chosen vs plain FP64 " \
         "form at stated error" % (W["N"], W["M"], B, "s" if B > 1 else "")
     if not default_workload:
         traffic = None  # the captured traffic is for 16 states; it does not scale by rows alone
-    launches = {"fp64": 6, "fp32x2": 7}[r["solve_arith"]]
+    # one kernel per timed stage, plus the float-float solve's state split
+    launches = sum(1 for v in r["stages"].values() if v > 0) + (1 if r["solve_arith"] == "fp32x2" else 0)
     line = {
         "metric": metric, "value": world * 1e3 / r["ms"], "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
@@ -540,9 +549,9 @@ def main():
                      "achieved": achieved, "peak": peak, "unit": roof_unit, "frac": achieved / peak,
                      "traffic": traffic,
                      "traffic_source": ("ncu dram bytes at T170/K256/B16 with %d pole slots, layout shape %d "
-                                        "(the captured layout nearest the bench's %d, shape %d), scaled by rows "
-                                        "to T341" % (tkey[0], tkey[1], r["slots"], r["shape"]))
-                     if default_workload else "not captured for this workload",
+                                        "(the captured layout nearest the bench's %d, shape %d; shape 2 = fused), "
+                                        "scaled by rows to T341" % (tkey[0], tkey[1], r["slots"], r["shape"]))
+                     if default_workload and traffic else "not captured for this workload or kernel",
                      "dram_gbs": traffic / (solve_ms * 1e-3) / 1e9 if traffic else None,
                      "peak_source": peak_source, "algorithmic_per_launch": amount, "launch_ms": solve_ms},
         "fp64_peak": {"tflops": fp64_tf, "ms": fp64_ms, "clocks": fp64_clocks,

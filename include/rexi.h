@@ -118,8 +118,12 @@ typedef struct {
   int32_t strict_range; /* 1: plan creation fails with REXI_ERANGE when tau * max|omega|
                            exceeds h (M - 10), the range where Re of the REXI symbol
                            matches cos to the fit level */
-  int32_t pole_slots;   /* 0: autotuned; else number of pole groups summed separately in
-                           the solve kernel (a deterministic tuning knob, any >= 1) */
+  int32_t pole_slots;   /* 0: the default solve -- with binary64 solves of the delta solver
+                           on the rotating sphere, the fused solve that keeps the pole sum
+                           on chip (one kernel, every output written once), else the
+                           pole-slot solve; > 0: the pole-slot solve with this many pole
+                           groups summed separately, then reduced in slot order (a
+                           deterministic tuning knob, any >= 1) */
   const double *alpha;  /* optional: P complex poles (re, im interleaved); NULL -> computed */
   const double *beta;   /* optional: P complex weights, used as given (no renormalisation) */
   int32_t npoles;       /* P when alpha/beta are given */
@@ -237,22 +241,26 @@ rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *
  * the banded solve and the slot reduction at this batch size for 1, 2, 4, ... pole
  * groups (the number of partial sums per coefficient, which trades load balance
  * against reduction work) in two shapes -- 0: the same number of groups for every
- * zonal order; 1: groups in proportion to the order's system length -- keeps the
- * fastest for later steps with this batch and writes its slot count to *slots and
- * its shape to *shape (either may be NULL).  Synchronous; uses the plan's
- * workspaces, so no step of this plan may be in flight. */
+ * zonal order; 1: groups in proportion to the order's system length -- and, where it
+ * applies (binary64 delta solver on the rotating sphere), shape 2: the fused solve
+ * with the pole sum on chip and no slots.  Keeps the fastest for later steps with
+ * this batch and writes its slot count (0 for shape 2) to *slots and its shape to
+ * *shape (either may be NULL).  Synchronous; uses the plan's workspaces, so no step
+ * of this plan may be in flight. */
 rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots, int32_t *shape);
 
 /* Sets the pole-slot layout for steps with this batch size without timing (for instance
  * from a cache of earlier rexi_tune results): slots >= 1 (rounded down to a multiple of
  * the lanes a warp gives each state and capped by the partial-sum buffer) and shape 0
- * or 1 as for rexi_tune; the slot count used is written to *used (may be NULL).
- * Results are deterministic for any layout; only the order of the final pole sum
- * changes.  Synchronous, like rexi_tune. */
+ * or 1 as for rexi_tune, or shape 2 (slots ignored) for the fused solve, REXI_EINVAL
+ * where that does not apply; the slot count used (0 for shape 2) is written to *used
+ * (may be NULL).  Results are deterministic for any layout; only the order of the
+ * final pole sum changes.  Synchronous, like rexi_tune. */
 rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t shape, int32_t *used);
 
 /* Host-side description of a plan: writes up to 8 int64 values
- * {N, nspec, P, nlat, nlon, max_batch, pole_slots, device bytes held}. */
+ * {N, nspec, P, nlat, nlon, max_batch, pole_slots, device bytes held}; pole_slots is
+ * that of steps with max_batch states, 0 when they use the fused solve. */
 rexi_status rexi_plan_info(const rexi_plan *plan, int64_t *info, int32_t n);
 
 /* Ragged batches (mixed truncations and pole counts): the banded solves of
@@ -276,8 +284,8 @@ void rexi_ragged_destroy(rexi_ragged *rg);
 /* Optional per-stage timing: with max_calls > 0 the next max_calls calls of
  * rexi_step / rexi_step_adjoint record CUDA events on their stream around each
  * stage (0 FFT forward, 1 Legendre analysis, 2 banded solve + pole sum,
- * 3 slot reduction, 4 Legendre synthesis, 5 FFT inverse, 6/7 layout
- * transposes).  max_calls = 0 turns it off.  rexi_profile_read waits for the
+ * 3 slot reduction (zero with the fused solve, which has none), 4 Legendre
+ * synthesis, 5 FFT inverse, 6/7 layout transposes).  max_calls = 0 turns it off.  rexi_profile_read waits for the
  * recorded events, writes the summed milliseconds per stage to stage_ms[0..n)
  * and the number of timed calls to *calls, and restarts the count. */
 rexi_status rexi_profile_enable(rexi_plan *plan, int32_t max_calls);

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librexi.so")
 SOURCES = ["coeffs.cpp", "plan.cu", "solve.cu", "phi.cu", "fft.cu", "legendre.cu", "legendre_tc.cu", "capi.cu",
-           "ragged.cu", "peak.cu"]
+           "ragged.cu", "peak.cu", "solve_fused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

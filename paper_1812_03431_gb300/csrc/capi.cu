@@ -23,6 +23,7 @@ void free_plan(Plan *pl);
 rexi_status step_static(Plan &pl, const void *in, void *out, int B, cudaStream_t st);
 rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out);
 rexi_status set_layout(Plan &pl, int B, int slots, int shape, int *used);
+const FusedLayout *fused_layout(Plan &pl, int B);
 
 namespace {
 
@@ -142,6 +143,12 @@ rexi_status core(Plan &pl, int B, bool adjoint, cudaStream_t st, Marks &mk) {
     mk.mark(ST_REDUCE);
     e = launch_phi_reduce(pl, *lay, pl.s_in, pl.s_out, B, st);
     return e == cudaSuccess ? REXI_OK : cuda_fail("phi reduce", e);
+  }
+  const FusedLayout *fl = fused_layout(pl, B);
+  if (fl) {  // the pole sum stays on chip: one kernel, outputs written once
+    mk.mark(ST_SOLVE);
+    cudaError_t e = launch_solve_fused(pl, *fl, adjoint, pl.s_in, pl.s_out, B, st);
+    return e == cudaSuccess ? REXI_OK : cuda_fail("solve", e);
   }
   mk.mark(ST_SOLVE);
   cudaError_t e = launch_solve(pl, *lay, adjoint, pl.s_in, B, 0, pl.P, true, st);
@@ -456,8 +463,9 @@ rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots, int32_t *s
 rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t shape, int32_t *used) {
   if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
   Plan &pl = *plan->pl;
-  if (batch < 1 || batch > pl.prm.max_batch || slots < 1) {
-    set_error("rexi_set_pole_slots: batch must be in [1, max_batch] and slots >= 1");
+  if (batch < 1 || batch > pl.prm.max_batch || (shape != 2 && slots < 1) || shape < 0 || shape > 2) {
+    set_error("rexi_set_pole_slots: batch must be in [1, max_batch], shape 0, 1 or 2, and slots >= 1 for "
+              "shapes 0 and 1");
     return REXI_EINVAL;
   }
   if (pl.prm.fsphere) {  // no banded solves, no layout
@@ -473,9 +481,10 @@ rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, i
 rexi_status rexi_plan_info(const rexi_plan *plan, int64_t *info, int32_t n) {
   if (!plan || !plan->pl || !info) { set_error("null argument"); return REXI_EINVAL; }
   const Plan &pl = *plan->pl;
-  int slots = 0;
+  int slots = 0;  // 0 when steps of max_batch states use the fused solve (no slot partials)
   auto it = pl.layouts.find(pl.prm.max_batch);
-  if (it != pl.layouts.end()) slots = it->second.slots;
+  auto us = pl.use_slots.find(pl.prm.max_batch);
+  if (it != pl.layouts.end() && us != pl.use_slots.end() && us->second) slots = it->second.slots;
   const int64_t v[8] = {pl.N, pl.nspec, pl.P, pl.nlat, pl.nlon, pl.prm.max_batch, slots, (int64_t)pl.bytes};
   for (int i = 0; i < n && i < 8; ++i) info[i] = v[i];
   return REXI_OK;

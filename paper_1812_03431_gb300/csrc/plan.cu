@@ -510,9 +510,38 @@ rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out) {
   return REXI_OK;
 }
 
+// The fused solve's layout for steps of B states, or null when the slot-partial path
+// serves them: float-float solves, the Phi-only solver, the f-sphere, an explicit
+// pole_slots at plan creation, a slot layout chosen for this batch (rexi_tune,
+// rexi_set_pole_slots), or running sums too large for shared memory.
+const FusedLayout *fused_layout(Plan &pl, int B) {
+  if (pl.ff || pl.prm.solver != REXI_SOLVER_DELTA || pl.prm.fsphere) return nullptr;
+  auto us = pl.use_slots.find(B);
+  if (us != pl.use_slots.end() ? us->second : pl.slots_override > 0) return nullptr;
+  auto it = pl.fused.find(B);
+  if (it == pl.fused.end()) {
+    FusedLayout F;
+    if (!build_fused_layout(pl, B, F)) F = FusedLayout{};  // st == 0: not available
+    it = pl.fused.emplace(B, F).first;
+  }
+  return it->second.st > 0 ? &it->second : nullptr;
+}
+
 // A given slot count for batch B: the layout with slots / kk pole groups replaces any
-// earlier one for that batch.
+// earlier one for that batch.  Shape 2 selects the fused solve instead (REXI_EINVAL where
+// it does not apply).
 rexi_status set_layout(Plan &pl, int B, int slots, int shape, int *used) {
+  if (shape == 2) {
+    pl.use_slots[B] = false;
+    if (!fused_layout(pl, B)) {
+      pl.use_slots[B] = true;
+      set_error("rexi_set_pole_slots: the fused solve (shape 2) needs binary64 solves of the delta solver on "
+                "the rotating sphere, with running sums that fit in shared memory");
+      return REXI_EINVAL;
+    }
+    if (used) *used = 0;
+    return REXI_OK;
+  }
   SolveLayout L;
   int bw = 1;
   while (bw < B && bw < 16) bw *= 2;
@@ -525,6 +554,7 @@ rexi_status set_layout(Plan &pl, int B, int slots, int shape, int *used) {
     pl.layouts.erase(it);
   }
   pl.layouts.emplace(B, L);
+  pl.use_slots[B] = true;
   if (used) *used = L.slots;
   return REXI_OK;
 }
@@ -585,6 +615,16 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
       cudaFree(L.items_dev);
     }
   }
+  // the fused solve (no slot partials, no reduction) competes with the best slot layout
+  float fused_ms = 1e30f;
+  pl.use_slots[B] = false;
+  if (const FusedLayout *F = fused_layout(pl, B)) {
+    launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 2; ++rep) launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&fused_ms, e0, e1);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   auto it = pl.layouts.find(B);
@@ -593,8 +633,10 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
     pl.layouts.erase(it);
   }
   pl.layouts.emplace(B, bestL);
-  if (slots_out) *slots_out = bestL.slots;
-  if (shape_out) *shape_out = bestL.shape;
+  const bool fused_wins = fused_ms <= best;
+  pl.use_slots[B] = !fused_wins;
+  if (slots_out) *slots_out = fused_wins ? 0 : bestL.slots;
+  if (shape_out) *shape_out = fused_wins ? 2 : bestL.shape;
   return REXI_OK;
 }
 
@@ -611,6 +653,8 @@ void free_plan(Plan *pl) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto &kv : pl->layouts)
+    if (kv.second.items_dev) cudaFree(kv.second.items_dev);
+  for (auto &kv : pl->fused)
     if (kv.second.items_dev) cudaFree(kv.second.items_dev);
   delete pl;
 }

@@ -92,6 +92,16 @@ struct SolveLayout {
   int32_t *slots_m_dev = nullptr;
 };
 
+// CTA shape and work list of the fused solve (solve_fused.cu) for one batch size: ST
+// states per CTA tile over WS warps of SB states; WP warps split the poles when the tile
+// has fewer than four states.  items: (system 2 m + p, first state), longest first.
+struct FusedLayout {
+  int sb = 0, ws = 0, wp = 0, st = 0;
+  int nitems = 0;
+  int2 *items_dev = nullptr;
+  size_t smem = 0;  // dynamic shared memory per CTA (running sums and the exchange buffer)
+};
+
 struct FftPlan {
   int n;
   int nstages;
@@ -204,6 +214,10 @@ struct Plan {
 
   std::map<int, SolveLayout> layouts;  // per batch size
   int slots_override = 0;
+  // fused solve (binary64 delta solver): per batch size its layout, and whether the slot
+  // layout above was chosen instead (rexi_tune, rexi_set_pole_slots, pole_slots)
+  std::map<int, FusedLayout> fused;
+  std::map<int, bool> use_slots;
 
   // optional per-stage timing with CUDA events on the launching stream
   bool prof = false;
@@ -251,6 +265,11 @@ struct SolveView {
 };
 SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double2 *sin, double2 *part, int B,
                     int pole_begin, int pole_end);
+// fused solve: eligible plans (binary64 delta solver on the rotating sphere) whose running
+// sums fit in shared memory; sin -> sout ([3][nspec][B]) with no partial sums and no reduction
+bool build_fused_layout(Plan &pl, int B, FusedLayout &F);
+cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, const double2 *sin, double2 *sout,
+                               int B, cudaStream_t st);
 cudaError_t launch_solve_ragged(const SolveView *views_dev, const WorkItem *items, int nitems, double2 *ybuf,
                                 int lmax, unsigned *counter, int resident_warps, bool ff, cudaStream_t st);
 // float-float solves: convert n complex values in place (factors), or split n binary64

@@ -1,0 +1,359 @@
+// Banded shifted solves with the beta-weighted pole sum kept on chip (paper Sec. 4.2,
+// Sec. 5, Algorithm 1), binary64.
+//
+// The systems and factors are those of solve.cu: per (pole k, zonal order m, parity p)
+// a complex tridiagonal system in delta over the degrees n = n0 + 2 i, pre-factored per
+// plan, swept forward
+//   y_i = delta0_n - g Phi0_n - e zeta0_{n-1} - f zeta0_{n+1} - l y_{i-1}
+// and backward  w_i = y_i - Chat w_{i+1}, after which the step needs, per row i,
+//   Sum_k bd_{k,i} w_{k,i}   (delta),      Sum_k bad_{k,i} w_{k,i}   (Phi),
+//   Sum_k zp_{k,i} w_{k,i}   (zeta at n_i + 1),  Sum_k zm_{k,i} w_{k,i}   (zeta at n_i - 1),
+// with the factors bd, bad, zp, zm carrying beta_k (Algorithm 1's accumulation).
+//
+// Here one CTA owns a whole (m, p, tile of states) system for every pole, so that each
+// of those sums is complete inside the CTA and its result is written once:
+//   - lanes of a warp are (state in the warp, pole): a pass of the warp sweeps PL poles of
+//     SB states at once, lane by lane, and the warps of the CTA cover further states (WS
+//     groups) or further poles (WP groups);
+//   - after every R rows of the backward sweep the lanes trade roles through shared
+//     memory: lane (row r, state s, stream t) takes the w of all PL poles of that row and
+//     state and adds them to its stream's running sum with complex FMAs, in ascending
+//     pole order -- so the pole sum costs no additions beyond the FMAs that apply the
+//     weights, and its order is fixed (results are bit-reproducible);
+//   - the running sums of every (state, row, stream) stay in shared memory across the
+//     passes; at the end of the item the CTA adds the pole-independent terms
+//     (Sum beta/alpha Phi0, Sum beta/(alpha + i tau sigma_n) zeta0), takes the real part
+//     at m = 0 and writes each output coefficient once.
+// The forward-sweep values y go through a per-warp global buffer (L2-resident: one CTA
+// per SM, 128 lanes x lmax rows).  No partial sums leave the SM and no reduction kernel
+// follows.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "rexi_internal.h"
+
+namespace rexi {
+namespace {
+
+__device__ __forceinline__ double2 cfms_(double2 acc, double2 a, double2 b) {  // acc - a b
+  double re = fma(-a.x, b.x, acc.x);
+  re = fma(a.y, b.y, re);
+  double im = fma(-a.x, b.y, acc.y);
+  im = fma(-a.y, b.x, im);
+  return make_double2(re, im);
+}
+__device__ __forceinline__ double2 cfma_(double2 acc, double2 a, double2 b) {  // acc + a b
+  double re = fma(a.x, b.x, acc.x);
+  re = fma(-a.y, b.y, re);
+  double im = fma(a.x, b.y, acc.y);
+  im = fma(a.y, b.x, im);
+  return make_double2(re, im);
+}
+__device__ __forceinline__ double2 ldg2(const double2 *p) { return __ldg(p); }
+__device__ __forceinline__ void pf_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" : : "l"(p)); }
+__device__ __forceinline__ void pf_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" : : "l"(p)); }
+
+constexpr int kThreads = 128;  // four warps per CTA, one CTA per SM
+constexpr int kStreams = 4;    // delta, Phi, zeta at n + 1, zeta at n - 1
+
+struct FusedArgs {
+  const double2 *fac;   // [F_NCOMP][nrows][P]
+  const double2 *sin;   // [3][nspec][B]
+  double2 *sout;        // [3][nspec][B]
+  double2 *ybuf;        // [gridDim.x * 4 warps][lmax][32]
+  const int4 *sys;      // per (m, p): {m, n0, len, row0}
+  const int2 *items;    // (system 2 m + p, first state of the tile), longest first
+  unsigned *counter;
+  const double2 *wz;    // [nspec] Sum beta_k / (alpha_k + i tau sigma_n) (adjoint: its counterpart)
+  double2 sphi;         // Sum beta_k / alpha_k over the plan's poles
+  int nitems, P, N, B, WS, WP, lmax, pole_begin, pole_end, realm0;
+  int64_t nspec, nrows;
+};
+
+// SB states per warp, PL = 32 / SB poles per warp pass, R = 8 / SB rows per task round
+// (lanes = R rows x SB states x 4 streams).
+template <int SB>
+__global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
+  constexpr int PL = 32 / SB, R = 8 / SB;
+  extern __shared__ double2 smem[];
+  __shared__ int s_item;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ws = warp / a.WP, wp = warp - ws * a.WP;  // state group, pole group of this warp
+  const int ST = a.WS * SB;                           // states per CTA tile
+  const int lmax = a.lmax, N = a.N, B = a.B;
+  const int64_t NS = a.nspec, NR = a.nrows, P = a.P;
+  double2 *acc = smem;                                             // [WP][ST][lmax][4]
+  double2 *wb = smem + (size_t)a.WP * ST * lmax * kStreams + (size_t)warp * R * 32;  // [R][32]
+  double2 *ybuf = a.ybuf + ((size_t)blockIdx.x * 4 + warp) * (size_t)lmax * 32 + lane;
+  // sweep role: lane = (state s_sw, pole pl); task role: lane = (row r, state t_s, stream t)
+  const int s_sw = lane / PL, pl = lane - s_sw * PL;
+  const int t_r = lane / (4 * SB), t_s = (lane >> 2) % SB, t_t = lane & 3;
+  const int t_comp = t_t == 0 ? F_BD : (t_t == 1 ? F_BAD : (t_t == 2 ? F_ZP : F_ZM));
+
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= a.nitems) break;
+    const int2 item = a.items[it];
+    const int4 sy = a.sys[item.x];
+    const int m = sy.x, n0 = sy.y, len = sy.z;
+    const int64_t row0 = sy.w;
+    const int p = item.x & 1, b0 = item.y;
+    const int64_t base_idx = (int64_t)m * (2 * N + 3 - m) / 2 - m;  // idx(m, n) = base_idx + n
+    const int nmin = m > 1 ? m : 1;
+
+    // running sums of this item start at zero
+    for (int q = threadIdx.x; q < a.WP * ST * len * kStreams; q += kThreads) {
+      const int t = q % kStreams, rest = q / kStreams, i = rest % len, g = rest / len;  // g = wp * ST + st
+      acc[((size_t)g * lmax + i) * kStreams + t] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+
+    if (len > 0) {
+      const int bsw = b0 + ws * SB + s_sw;  // the sweep lane's state (clamped for loads)
+      const int bq = bsw < B ? bsw : b0;
+      const double2 *sPhi = a.sin + bq, *sZeta = a.sin + NS * B + bq, *sDel = a.sin + 2 * NS * B + bq;
+      const int npp = a.WP * PL;  // poles per CTA pass
+      for (int kb = a.pole_begin; kb < a.pole_end; kb += npp) {
+        const int kw = kb + wp * PL;                            // this warp's first pole
+        const int npa = min(PL, a.pole_end - kw);               // its active poles (warp-uniform)
+        if (npa <= 0) continue;
+        const int k = kw + min(pl, npa - 1);                    // inactive lanes repeat a valid pole
+        const double2 *fL = a.fac + ((int64_t)F_L * NR + row0) * P + k;
+        const double2 *fG = a.fac + ((int64_t)F_G * NR + row0) * P + k;
+        const double2 *fE = a.fac + ((int64_t)F_E * NR + row0) * P + k;
+        const double2 *fF = a.fac + ((int64_t)F_F * NR + row0) * P + k;
+        const double2 *fC = a.fac + ((int64_t)F_C * NR + row0) * P + k;
+
+        // ---- forward sweep; the next row's factors and states are loaded one row ahead
+        double2 yprev = make_double2(0.0, 0.0);
+        double2 zprev = (n0 - 1 >= nmin) ? ldg2(sZeta + (base_idx + n0 - 1) * B) : make_double2(0.0, 0.0);
+        double2 cl = ldg2(fL), cg = ldg2(fG), ce = ldg2(fE), cf = ldg2(fF);
+        double2 cd0 = ldg2(sDel + (base_idx + n0) * B), cp0 = ldg2(sPhi + (base_idx + n0) * B);
+        double2 czn = (n0 + 1 <= N) ? ldg2(sZeta + (base_idx + n0 + 1) * B) : make_double2(0.0, 0.0);
+        for (int i = 0; i < len; ++i) {
+          const int inx = i + 1 < len ? i + 1 : i;
+          if (i + 3 < len) {
+            const int64_t o = (int64_t)(i + 3) * P;
+            pf_l2(fL + o);
+            pf_l2(fG + o);
+            pf_l2(fE + o);
+            pf_l2(fF + o);
+          }
+          const int64_t on = (int64_t)inx * P;
+          const int nn = n0 + 2 * inx;
+          const double2 nl = ldg2(fL + on), ng = ldg2(fG + on), ne = ldg2(fE + on), nf = ldg2(fF + on);
+          const double2 nd0 = ldg2(sDel + (base_idx + nn) * B), np0 = ldg2(sPhi + (base_idx + nn) * B);
+          const double2 nzn = (nn + 1 <= N) ? ldg2(sZeta + (base_idx + nn + 1) * B) : make_double2(0.0, 0.0);
+          double2 y = cfms_(cd0, cg, cp0);
+          y = cfms_(y, ce, zprev);
+          y = cfms_(y, cf, czn);
+          y = cfms_(y, cl, yprev);
+          ybuf[(size_t)i * 32] = y;
+          yprev = y;
+          zprev = czn;
+          cl = nl; cg = ng; ce = ne; cf = nf;
+          cd0 = nd0; cp0 = np0; czn = nzn;
+        }
+
+        // ---- backward sweep; every R rows the lanes add the rows' w into the running sums
+        double2 wnext = make_double2(0.0, 0.0);
+        double2 cy = ybuf[(size_t)(len - 1) * 32], cc = ldg2(fC + (int64_t)(len - 1) * P);
+        int slot = 0;
+        for (int i = len - 1; i >= 0; --i) {
+          const int inx = i > 0 ? i - 1 : i;
+          if (i - 3 >= 0) pf_l2(fC + (int64_t)(i - 3) * P);
+          const double2 ny = ybuf[(size_t)inx * 32], nc = ldg2(fC + (int64_t)inx * P);
+          const double2 w = cfms_(cy, cc, wnext);
+          wb[slot * 32 + lane] = w;
+          wnext = w;
+          cy = ny;
+          cc = nc;
+          ++slot;
+          if (slot == R || i == 0) {
+            __syncwarp();
+            if (t_r < slot) {
+              const int ii = i + slot - 1 - t_r;  // the row this lane sums
+              double2 *ap = acc + (((size_t)wp * ST + ws * SB + t_s) * lmax + ii) * kStreams + t_t;
+              const double2 *W = a.fac + ((int64_t)t_comp * NR + row0 + ii) * P + kw;
+              const double2 *wv = wb + t_r * 32 + t_s * PL;
+              double2 s = *ap;
+              if (npa == PL) {
+#pragma unroll
+                for (int q = 0; q < PL; ++q) s = cfma_(s, ldg2(W + q), wv[q]);
+              } else {
+                for (int q = 0; q < npa; ++q) s = cfma_(s, ldg2(W + q), wv[q]);
+              }
+              *ap = s;
+              // the next round's weights (R rows further down) into L1
+              if (ii - R >= 0) {
+                const double2 *Wn = W - (int64_t)R * P;
+#pragma unroll
+                for (int q = 0; q < PL; q += 8)
+                  if (q < npa) pf_l1(Wn + q);  // poles of this pass only: every address inside the factors
+              }
+            }
+            __syncwarp();
+            slot = 0;
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- outputs of this item: delta and Phi at the degrees of parity p, zeta at the
+    // other parity; every coefficient of the item written once
+    {
+      const int nown = (N - (m + p)) >= 0 ? (N - (m + p)) / 2 + 1 : 0;          // n = m + p + 2 j
+      const int noth = (N - (m + 1 - p)) >= 0 ? (N - (m + 1 - p)) / 2 + 1 : 0;  // n = m + 1 - p + 2 j
+      const int tot = (nown + noth) * ST;
+      for (int q = threadIdx.x; q < tot; q += kThreads) {
+        const int st = q % ST, jj = q / ST;
+        const int b = b0 + st;
+        if (b >= B) continue;
+        auto sumacc = [&](int i, int t) {
+          double2 v = make_double2(0.0, 0.0);
+          for (int g = 0; g < a.WP; ++g) {
+            const double2 u = acc[(((size_t)g * ST + st) * lmax + i) * kStreams + t];
+            v.x += u.x;
+            v.y += u.y;
+          }
+          return v;
+        };
+        if (jj < nown) {
+          const int n = m + p + 2 * jj;
+          const int64_t ix = base_idx + n;
+          const int i = (n - n0) / 2;
+          const bool row = n >= n0 && i < len;
+          double2 dl = row ? sumacc(i, 0) : make_double2(0.0, 0.0);
+          double2 ph = row ? sumacc(i, 1) : make_double2(0.0, 0.0);
+          ph = cfma_(ph, a.sphi, a.sin[ix * B + b]);
+          if (a.realm0 && m == 0) {
+            dl.y = 0.0;
+            ph.y = 0.0;
+          }
+          a.sout[ix * B + b] = ph;
+          a.sout[(2 * NS + ix) * B + b] = dl;
+        } else {
+          const int n = m + 1 - p + 2 * (jj - nown);
+          const int64_t ix = base_idx + n;
+          double2 ze = make_double2(0.0, 0.0);
+          if (n > 0) {  // zeta_0^0 is not state
+            const int ia = (n - 1 - n0) / 2, ib = (n + 1 - n0) / 2;  // delta rows n - 1 and n + 1
+            if (n - 1 >= n0 && ia < len) ze = sumacc(ia, 2);
+            if (n + 1 >= n0 && ib < len) {
+              const double2 u = sumacc(ib, 3);
+              ze.x += u.x;
+              ze.y += u.y;
+            }
+            ze = cfma_(ze, a.wz[ix], a.sin[(NS + ix) * B + b]);
+            if (a.realm0 && m == 0) ze.y = 0.0;
+          }
+          a.sout[(NS + ix) * B + b] = ze;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// Work items and CTA shape of the fused solve for a batch of B states: ST states per
+// CTA tile (the smallest power of two >= B, at most 16), split over the four warps as
+// WS state groups of SB states; when the tile has fewer than four states the remaining
+// warps split the poles (WP groups).  Returns false when the running sums of a tile do
+// not fit in shared memory (the slot-partial path then serves the plan).
+bool build_fused_layout(Plan &pl, int B, FusedLayout &F) {
+  F = FusedLayout{};
+  int st = 1;
+  while (st < B && st < 16) st *= 2;
+  const int dev = pl.device;
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  for (; st >= 1; st /= 2) {
+    int sb, ws, wp;
+    if (st >= 4) { sb = st / 4; ws = 4; wp = 1; }
+    else { sb = 1; ws = st; wp = 4 / st; }
+    const size_t smem = ((size_t)wp * st * pl.lmax * kStreams + (size_t)4 * (8 / sb) * 32) * sizeof(double2);
+    if (smem + 1024 > (size_t)smem_max) continue;
+    F.sb = sb;
+    F.ws = ws;
+    F.wp = wp;
+    F.st = st;
+    F.smem = smem;
+    break;
+  }
+  if (F.st == 0) return false;
+  // items (system, first state), longest system first; m ascending breaks ties
+  struct Keyed { int2 it; int len; };
+  std::vector<Keyed> keyed;
+  for (int m = 0; m <= pl.N; ++m)
+    for (int p = 0; p < 2; ++p)
+      for (int b0 = 0; b0 < B; b0 += F.st) keyed.push_back(Keyed{make_int2(2 * m + p, b0), pl.sys[2 * m + p].len});
+  std::stable_sort(keyed.begin(), keyed.end(), [](const Keyed &x, const Keyed &y) { return x.len > y.len; });
+  std::vector<int2> items;
+  for (const Keyed &k : keyed) items.push_back(k.it);
+  F.nitems = (int)items.size();
+  cudaError_t e = cudaMalloc(&F.items_dev, items.size() * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMemcpy(F.items_dev, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (F.items_dev) cudaFree(F.items_dev);
+    F.items_dev = nullptr;
+    return false;
+  }
+  return true;
+}
+
+cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, const double2 *sin, double2 *sout,
+                               int B, cudaStream_t st) {
+  FusedArgs a;
+  a.fac = adjoint ? pl.fac_adj : pl.fac_fwd;
+  a.sin = sin;
+  a.sout = sout;
+  a.ybuf = pl.yscratch;  // sized for 16 warps x 2 poles per SM: four warps of one pole here
+  a.sys = pl.sys_dev;
+  a.items = F.items_dev;
+  a.counter = pl.counter;
+  a.wz = adjoint ? pl.w_adj : pl.w_fwd;
+  a.sphi = adjoint ? pl.sphi_adj : pl.sphi_fwd;
+  a.nitems = F.nitems;
+  a.P = pl.P;
+  a.N = pl.N;
+  a.B = B;
+  a.WS = F.ws;
+  a.WP = F.wp;
+  a.lmax = pl.lmax;
+  a.pole_begin = 0;
+  a.pole_end = pl.P;
+  a.realm0 = 1;
+  a.nspec = pl.nspec;
+  a.nrows = pl.nrows;
+  cudaError_t e = cudaMemsetAsync(pl.counter, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const int grid = pl.num_sms;
+  const int smem = (int)F.smem;
+  switch (F.sb) {
+    case 4:
+      e = cudaFuncSetAttribute(solve_fused_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) solve_fused_kernel<4><<<grid, kThreads, smem, st>>>(a);
+      break;
+    case 2:
+      e = cudaFuncSetAttribute(solve_fused_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) solve_fused_kernel<2><<<grid, kThreads, smem, st>>>(a);
+      break;
+    default:
+      e = cudaFuncSetAttribute(solve_fused_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) solve_fused_kernel<1><<<grid, kThreads, smem, st>>>(a);
+      break;
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace rexi

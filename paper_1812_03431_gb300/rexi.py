@@ -269,8 +269,9 @@ class Plan:
 
     def tune(self, batch, cache=None):
         """rexi_tune: time the solve and reduction for several pole-group counts and both
-        layout shapes at this batch size and keep the fastest; returns the chosen number
-        of pole slots (the shape is kept in ``self.layout_shape[batch]``).
+        slot-layout shapes at this batch size, and the fused solve (shape 2, no slots) where
+        it applies, and keep the fastest; returns the chosen number of pole slots (0 for the
+        fused solve; the shape is kept in ``self.layout_shape[batch]``).
 
         ``cache``: path of a JSON file of earlier choices keyed by the plan's shape (N,
         grid, P, batch, precision, solver, solve arithmetic) and the GPU's name; a hit sets the layout
@@ -296,7 +297,8 @@ class Plan:
 
     def set_pole_slots(self, batch, slots, shape=0):
         """rexi_set_pole_slots: use this pole-slot count and layout shape (0: the same groups
-        for every zonal order, 1: in proportion to the system length) for this batch size."""
+        for every zonal order, 1: in proportion to the system length; 2: the fused solve,
+        slots ignored) for this batch size."""
         n = _I32()
         _check("rexi_set_pole_slots", load().rexi_set_pole_slots(self._h, batch, slots, shape, ctypes.byref(n)))
         self.layout_shape[batch] = shape

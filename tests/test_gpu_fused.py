@@ -1,0 +1,111 @@
+"""The fused solve (the beta-weighted pole sum kept on chip, Sec. 5 / Algorithm 1) against the
+oracle and against the pole-slot solve with its separate reduction, over every CTA shape
+it takes: tiles of 1, 2, 4, 8 and 16 states (warps split over poles or states), ragged
+state tiles, pole counts below and above a warp's pole lanes, truncations up to the
+largest whose running sums fit in shared memory."""
+import numpy as np
+import pytest
+
+from oracle import rexi_coeffs as rc
+from oracle import step as ostep
+from oracle.swe import Consts
+from paper_1812_03431_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+C = Consts()
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def fieldwise(got, ref):
+    return max(relerr(got[:, f], ref[:, f]) for f in range(3))
+
+
+@pytest.mark.parametrize("N,M,B,tau", [(7, 1, 1, 600.0), (15, 16, 1, 3600.0), (21, 8, 2, 1800.0),
+                                       (23, 16, 3, 900.0), (31, 32, 4, 7200.0), (40, 16, 5, 3600.0),
+                                       (33, 32, 9, 1200.0), (24, 16, 16, 2400.0), (19, 8, 17, 3600.0)])
+def test_fused_step_matches_oracle_and_slot_solve(N, M, B, tau):
+    import torch
+    from paper_1812_03431_gb300 import rexi
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    S = inputs.random_spectral(N, B, 500 + N + B)
+    x = torch.from_numpy(S).cuda()
+    plan = rexi.Plan(N, 2 * N + 2, 4 * N + 4, tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
+    assert plan.set_pole_slots(B, 0, 2) == 0  # the fused solve
+    fused = plan.step(x).cpu().numpy()
+    np.testing.assert_array_equal(plan.step(x).cpu().numpy(), fused)  # bit-reproducible
+    plan.set_pole_slots(B, 8, 0)  # the pole-slot solve and its reduction
+    slot = plan.step(x).cpu().numpy()
+    plan.close()
+    ref = ostep.rexi_step_spectral(S, N, al, be, tau, C)
+    assert fieldwise(fused, ref) < TOL
+    assert fieldwise(fused, slot) < 1e-13  # the same sums in another order
+    assert np.all(fused[:, 1:, 0] == 0) and np.all(fused[:, :, : N + 1].imag == 0)
+
+
+def test_fused_is_the_default_and_drops_the_reduction():
+    import torch
+    from paper_1812_03431_gb300 import rexi
+    N, B = 31, 4
+    plan = rexi.Plan(N, 48, 96, M=32, max_batch=B, layout="spectral")
+    x = torch.from_numpy(inputs.random_spectral(N, B, 9)).cuda()
+    plan.profile_enable(1)
+    plan.step(x)
+    st, n = plan.profile_read()
+    assert n == 1 and st["solve"] > 0 and st["reduce"] == 0.0
+    assert plan.info()["pole_slots"] == 0
+    plan.close()
+    # an explicit pole_slots at plan creation selects the slot solve
+    plan = rexi.Plan(N, 48, 96, M=32, max_batch=B, layout="spectral", pole_slots=8)
+    plan.profile_enable(1)
+    plan.step(x)
+    st, _ = plan.profile_read()
+    assert st["reduce"] > 0
+    plan.close()
+
+
+def test_fused_not_offered_where_it_does_not_apply():
+    from paper_1812_03431_gb300 import rexi
+    for kw in (dict(solve_arith="fp32x2"), dict(solver="phi"), dict(fsphere=True)):
+        plan = rexi.Plan(15, 16, 32, M=8, max_batch=2, layout="spectral", **kw)
+        with pytest.raises(rexi.RexiError):
+            plan.set_pole_slots(2, 0, 2)
+        plan.close()
+
+
+def test_fused_adjoint_matches_oracle():
+    import torch
+    from paper_1812_03431_gb300 import rexi
+    N, M, B, tau = 27, 32, 3, 3600.0
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    G = inputs.random_spectral(N, B, 77)
+    plan = rexi.Plan(N, 56, 112, tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
+    got = plan.step_adjoint(torch.from_numpy(G).cuda()).cpu().numpy()
+    plan.close()
+    ref = ostep.rexi_step_spectral(G, N, al, be, tau, C, adjoint=True)
+    assert fieldwise(got, ref) < TOL
+
+
+def test_fused_large_truncation_smaller_tiles():
+    # T447 with 16 states: a 16-state tile's running sums (16 x 224 rows x 64 B) exceed
+    # shared memory, so the layout takes 8-state tiles; sampled orders against the oracle
+    import torch
+    from paper_1812_03431_gb300 import rexi
+    from oracle.sphere import idx
+    N, M, B, tau = 447, 32, 16, 600.0
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    S = inputs.random_spectral(N, B, 447)
+    x = torch.from_numpy(S).cuda()
+    plan = rexi.Plan(N, 450, 900, tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
+    got = plan.step(x).cpu().numpy()
+    plan.set_pole_slots(B, 16, 0)
+    slot = plan.step(x).cpu().numpy()
+    plan.close()
+    assert fieldwise(got, slot) < 1e-13
+    ms = [0, 1, 224, 446, 447]
+    ref = ostep.rexi_step_spectral(S[:2], N, al, be, tau, C, ms=ms)
+    sel = np.concatenate([np.arange(idx(m, m, N), idx(m, N, N) + 1) for m in ms])
+    assert fieldwise(got[:2][..., sel], ref[..., sel]) < TOL
