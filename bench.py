@@ -16,7 +16,9 @@ and every form's result for state 0 is compared with the CPU oracle's.
 
 `python bench.py [--gpus N --steps K --warmup W] [--impl reference]` prints
 one JSON line.  For N > 1 (torchrun) every rank runs an independent replica
-(the path has no exchange step) and value is the sum over ranks.
+by default (weak scaling: value is the sum over ranks); with `--shard poles` the
+ranks split the poles of one batch evenly and every step ends with an NCCL
+allreduce of the partial results (Sec. 6.4; strong scaling).
 """
 import argparse
 import json
@@ -298,6 +300,15 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def shard_allreduce(y, dist):
+    """The one reduction of Sec. 6.4 when the poles are split over ranks: every rank's
+    partial step is summed in place (NCCL on the GPU, gloo on the CPU)."""
+    if dist is not None:
+        import torch
+        dist.all_reduce(torch.view_as_real(y) if y.is_complex() else y, op=dist.ReduceOp.SUM)
+    return y
+
+
 def replica_max_ms(ms, dist):
     """Max of a per-rank time over all ranks (the slowest replica sets the job's time)."""
     if dist is None:
@@ -336,15 +347,27 @@ def relerr_fields(got, ref):
 
 def time_form(rexi, torch, name, prec, arith, x, args, dist, local, stream, solver="delta"):
     """Plan, tune, warm up and time one form of the step; returns its record (and the e2e run
-    for the chosen form)."""
+    for the chosen form).  With --shard poles each rank's plan holds its share of the poles
+    and a step ends with the allreduce of the partial results."""
     W = WORK
     B = W["batch"]
+    poles, sdist = None, None
+    if args.shard == "poles" and dist is not None:
+        P = 2 * (W["M"] + 11) + 1
+        poles, sdist = rexi.pole_shard(P, dist.get_rank(), dist.get_world_size()), dist
     plan = rexi.Plan(W["N"], W["nlat"], W["nlon"], M=W["M"], h=W["h"], tau=W["tau"], max_batch=B,
-                     precision=prec, solve_arith=arith, solver=solver)
+                     precision=prec, solve_arith=arith, solver=solver, poles=poles)
     slots = plan.tune(B)  # the library's autotuner picks the pole-slot count for this batch
     y = torch.empty_like(x)
+
+    def step(xx, yy, stream=None):
+        plan.step(xx, out=yy, stream=stream)
+        if sdist is not None:
+            with torch.cuda.stream(stream or torch.cuda.current_stream()):
+                shard_allreduce(yy, sdist)
+
     for _ in range(args.warmup):
-        plan.step(x, out=y)
+        step(x, y)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -355,7 +378,7 @@ def time_form(rexi, torch, name, prec, arith, x, args, dist, local, stream, solv
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        plan.step(x, out=y)
+        step(x, y)
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -367,11 +390,11 @@ def time_form(rexi, torch, name, prec, arith, x, args, dist, local, stream, solv
     ms = replica_max_ms(ms, dist)
     rec = dict(ms=ms, stages={k: v / max(ncalls, 1) for k, v in stages.items()}, clocks=ck, y=y,
                bytes=x.numel() * 8, info=plan.info(), slots=slots, shape=plan.layout_shape.get(B, 0),
-               precision=prec, solve_arith=arith, plan=plan)
+               precision=prec, solve_arith=arith, plan=plan, step=step, poles=poles)
     return rec
 
 
-def e2e_run(torch, plan, x, y, args, dist):
+def e2e_run(torch, step, x, y, args, dist):
     """End to end through the public API: every step copies its input from pinned host memory
     and its result back inside the timed region.  The copies run on their own streams with two
     device buffer pairs, so step i's result goes back and step i+1's input comes in while step
@@ -399,7 +422,7 @@ def e2e_run(torch, plan, x, y, args, dist):
             cs.wait_event(loaded)
             if copied_back[k] is not None:
                 cs.wait_event(copied_back[k])  # yd[k] of step i-2 is on the host
-            plan.step(xd[k], out=yd[k], stream=cs)
+            step(xd[k], yd[k], stream=cs)
             computed[k] = torch.cuda.Event()
             computed[k].record(cs)
             with torch.cuda.stream(d2h):
@@ -441,6 +464,9 @@ def main():
                     help="skip measuring the FP64 FMA rate (the roofline then divides by the derived rate)")
     ap.add_argument("--no-phi-solver", action="store_true",
                     help="skip timing the paper's geopotential-only solver next to the default one")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "poles"],
+                    help="N > 1: replicas (every rank steps its own batch, weak scaling) or poles (the ranks "
+                         "split the poles of one batch and allreduce the partial steps, strong scaling)")
     ap.add_argument("--workload", default="t341_b16", choices=sorted(WORKLOADS),
                     help="t341_b16: the metric's workload; the others time further workloads of the "
                          "specification (no CPU baseline, no Phi-only solver, no traffic figure)")
@@ -453,6 +479,9 @@ def main():
         args.no_phi_solver = True
     if WORK["N"] > ORACLE_MAX_N:
         args.no_oracle = True
+    if args.shard == "poles":  # one form, the chosen one, split over the ranks
+        args.form = FORMS[0][0]
+        args.no_phi_solver = True
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -482,7 +511,7 @@ def main():
     for i, (name, prec, arith) in enumerate(forms):
         r = time_form(rexi, torch, name, prec, arith, x, args, dist, local, stream)
         if i == 0:
-            r["ms_e2e"], r["e2e_same"] = e2e_run(torch, r["plan"], x, r["y"], args, dist)
+            r["ms_e2e"], r["e2e_same"] = e2e_run(torch, r["step"], x, r["y"], args, dist)
         r["plan"].close()
         r["y0"] = r["y"][0].cpu().numpy()
         results[name] = r
@@ -539,11 +568,16 @@ def main():
         traffic = None  # the captured traffic is for 16 states; it does not scale by rows alone
     # one kernel per timed stage, plus the float-float solve's state split
     launches = sum(1 for v in r["stages"].values() if v > 0) + (1 if r["solve_arith"] == "fp32x2" else 0)
+    sharded = args.shard == "poles" and world > 1
+    jobs = 1 if sharded else world  # replicas each step a batch; shards step one batch together
+    cfg = workload_config()
+    if sharded:
+        cfg["parallelism"] = "poles split over %d ranks (Sec. 6.4), NCCL allreduce of the grid result" % world
     line = {
-        "metric": metric, "value": world * 1e3 / r["ms"], "unit": "steps/s", "n_gpus": world,
+        "metric": metric, "value": jobs * 1e3 / r["ms"], "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": dtypes[chosen],
-        "data": "synthetic", "config": workload_config(),
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": dtypes[chosen],
+        "data": "synthetic", "config": cfg,
         "form": chosen, "solve_layout": {"pole_slots": r["slots"], "layout_shape": r["shape"]},
         "roofline": {"bound": "alu", "kernel": kname,
                      "achieved": achieved, "peak": peak, "unit": roof_unit, "frac": achieved / peak,
@@ -556,10 +590,10 @@ def main():
                      "peak_source": peak_source, "algorithmic_per_launch": amount, "launch_ms": solve_ms},
         "fp64_peak": {"tflops": fp64_tf, "ms": fp64_ms, "clocks": fp64_clocks,
                       "derived_tflops_at_max_clock": fp64_peak_tflops(sm_mhz)},
-        "state_steps_per_s": world * B * 1e3 / r["ms"],
+        "state_steps_per_s": jobs * B * 1e3 / r["ms"],
         "stage_ms": r["stages"],
         "kernels": kernel_rooflines(r["precision"], r["stages"], r["slots"], sm_mhz, r["solve_arith"], fp64_tf),
-        "e2e": {"value": world * 1e3 / r["ms_e2e"], "unit": "steps/s", "h2d_bytes_per_step": r["bytes"],
+        "e2e": {"value": jobs * 1e3 / r["ms_e2e"], "unit": "steps/s", "h2d_bytes_per_step": r["bytes"],
                 "d2h_bytes_per_step": r["bytes"], "copies": "pinned host, own streams, overlapping compute",
                 "result_matches_device_step": r["e2e_same"]},
         "gpu_launches": launches * args.steps,

@@ -140,6 +140,17 @@ typedef struct {
   int32_t solve_arith;  /* REXI_SOLVE_FP64 | REXI_SOLVE_FP32X2: arithmetic of the banded solves
                            and the beta-weighted pole sum (the transforms follow `precision`).
                            rexi_ragged_create needs the same value on every plan. */
+  int32_t pole_begin, pole_end; /* 0, 0: every pole.  Otherwise the plan keeps only the poles
+                           k in [pole_begin, pole_end) of the full ascending set (computed,
+                           and renormalised over the full set, or given by alpha/beta), and
+                           rexi_step returns the partial sum
+                             Re sum_{pole_begin <= k < pole_end} beta_k (alpha_k + tau L)^{-1} U,
+                           transforms included: the plans of a partition of the poles return
+                           outputs that add up to the full step (the paper's even split of
+                           the REXI terms over ranks and one reduction, Sec. 6.4; the sum is
+                           the caller's, e.g. an allreduce).  Such a plan's P and
+                           rexi_get_coefficients are those of its own poles; every call works
+                           on them.  Needs 0 <= pole_begin < pole_end <= P. */
 } rexi_params;
 
 /* Fill *p with the defaults above (ntrunc = 63, nlat = 96, nlon = 192, M = 128,

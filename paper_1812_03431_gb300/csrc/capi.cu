@@ -312,6 +312,14 @@ rexi_status rexi_plan_create(const rexi_params *prm, rexi_plan **out) {
     set_error("rexi_plan_create: solver must be REXI_SOLVER_DELTA or REXI_SOLVER_PHI (the latter on the rotating sphere)");
     return REXI_EINVAL;
   }
+  {
+    const int64_t Pfull = p.alpha ? p.npoles : 2 * ((int64_t)p.M + kGaussTerms) + 1;
+    if ((p.pole_begin != 0 || p.pole_end != 0) &&
+        (p.pole_begin < 0 || p.pole_end <= p.pole_begin || p.pole_end > Pfull)) {
+      set_error("rexi_plan_create: need 0 <= pole_begin < pole_end <= P (P = " + std::to_string(Pfull) + ")");
+      return REXI_EINVAL;
+    }
+  }
   if ((p.solve_arith != REXI_SOLVE_FP64 && p.solve_arith != REXI_SOLVE_FP32X2) ||
       (p.solve_arith == REXI_SOLVE_FP32X2 && p.fsphere)) {
     set_error("rexi_plan_create: solve_arith must be REXI_SOLVE_FP64 or REXI_SOLVE_FP32X2 (the latter on the "

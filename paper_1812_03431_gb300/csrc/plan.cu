@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <string>
 
 #include "rexi_internal.h"
 
@@ -135,6 +136,15 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
   } else {
     rexi_coeffs_host(prm.M, prm.h, prm.normalize != 0, pl->alpha, pl->beta, &pl->eps0);
     pl->P = (int)pl->alpha.size();
+  }
+  if (prm.pole_begin != 0 || prm.pole_end != 0) {  // this plan's share of the poles
+    if (prm.pole_begin < 0 || prm.pole_end <= prm.pole_begin || prm.pole_end > pl->P) {
+      set_error("plan: need 0 <= pole_begin < pole_end <= P (P = " + std::to_string(pl->P) + ")");
+      return REXI_EINVAL;
+    }
+    pl->alpha = std::vector<cplx>(pl->alpha.begin() + prm.pole_begin, pl->alpha.begin() + prm.pole_end);
+    pl->beta = std::vector<cplx>(pl->beta.begin() + prm.pole_begin, pl->beta.begin() + prm.pole_end);
+    pl->P = prm.pole_end - prm.pole_begin;
   }
   const int P = pl->P;
   const double tau = prm.tau, a = prm.radius, om = prm.omega;

@@ -31,7 +31,7 @@ class rexi_params(ctypes.Structure):
         ("strict_range", ctypes.c_int32), ("pole_slots", ctypes.c_int32),
         ("alpha", ctypes.POINTER(ctypes.c_double)), ("beta", ctypes.POINTER(ctypes.c_double)),
         ("npoles", ctypes.c_int32), ("fsphere", ctypes.c_int32), ("solver", ctypes.c_int32),
-        ("solve_arith", ctypes.c_int32),
+        ("solve_arith", ctypes.c_int32), ("pole_begin", ctypes.c_int32), ("pole_end", ctypes.c_int32),
     ]
 
 
@@ -135,6 +135,17 @@ def rexi_measure_fp64_fma(reps=5, stream=None):
     return tf.value, ms.value
 
 
+def pole_shard(P, rank, world):
+    """Rank `rank`'s contiguous share [begin, end) of P poles split evenly over `world`
+    ranks (sizes differ by at most one; the first P mod world ranks take one more), the
+    even split of the REXI terms over ranks of Sec. 6.4."""
+    if not (0 <= rank < world) or P < world:
+        raise ValueError("need 0 <= rank < world <= P")
+    q, r = divmod(P, world)
+    begin = rank * q + min(rank, r)
+    return begin, begin + q + (1 if rank < r else 0)
+
+
 def _stream_handle(stream):
     import torch
     if stream is None:
@@ -152,7 +163,8 @@ class Plan:
     def __init__(self, N, nlat=None, nlon=None, M=128, h=0.2, tau=3600.0, max_batch=1,
                  layout="grid", precision="fp64", normalize=True, alpha=None, beta=None,
                  radius=6.37122e6, omega=7.292e-5, gravity=9.80616, mean_depth=1.0e4,
-                 pole_slots=0, strict_range=False, fsphere=False, solver="delta", solve_arith="fp64"):
+                 pole_slots=0, strict_range=False, fsphere=False, solver="delta", solve_arith="fp64",
+                 poles=None):
         lib = load()
         p = rexi_params()
         lib.rexi_params_default(ctypes.byref(p))
@@ -174,6 +186,8 @@ class Plan:
         p.fsphere = 1 if fsphere else 0
         p.solver = {"delta": 0, "phi": 1}[solver]
         p.solve_arith = {"fp64": 0, "fp32x2": 1}[solve_arith]
+        if poles is not None:  # (begin, end): this plan's share of the poles (pole_shard)
+            p.pole_begin, p.pole_end = int(poles[0]), int(poles[1])
         self._keep = []
         if alpha is not None:
             al = np.ascontiguousarray(np.asarray(alpha, dtype=np.complex128)).view(np.float64)

@@ -16,6 +16,11 @@ TOL = 1e-10
 C = Consts()
 
 
+def grid(N):
+    from paper_1812_03431_gb300 import rexi
+    return 2 * N + 2, next(n for n in range(2 * N + 2, 8 * N + 16, 2) if rexi._smooth(n))
+
+
 def relerr(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
@@ -33,7 +38,7 @@ def test_fused_step_matches_oracle_and_slot_solve(N, M, B, tau):
     al, be, _ = rc.rexi_coefficients(M, 0.2)
     S = inputs.random_spectral(N, B, 500 + N + B)
     x = torch.from_numpy(S).cuda()
-    plan = rexi.Plan(N, 2 * N + 2, 4 * N + 4, tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
+    plan = rexi.Plan(N, *grid(N), tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
     assert plan.set_pole_slots(B, 0, 2) == 0  # the fused solve
     fused = plan.step(x).cpu().numpy()
     np.testing.assert_array_equal(plan.step(x).cpu().numpy(), fused)  # bit-reproducible
@@ -82,7 +87,7 @@ def test_fused_adjoint_matches_oracle():
     N, M, B, tau = 27, 32, 3, 3600.0
     al, be, _ = rc.rexi_coefficients(M, 0.2)
     G = inputs.random_spectral(N, B, 77)
-    plan = rexi.Plan(N, 56, 112, tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
+    plan = rexi.Plan(N, *grid(N), tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
     got = plan.step_adjoint(torch.from_numpy(G).cuda()).cpu().numpy()
     plan.close()
     ref = ostep.rexi_step_spectral(G, N, al, be, tau, C, adjoint=True)
