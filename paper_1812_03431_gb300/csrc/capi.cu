@@ -477,6 +477,10 @@ rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, i
     return REXI_EINVAL;
   }
   if (pl.prm.fsphere) {  // no banded solves, no layout
+    if (shape == 2) {
+      set_error("rexi_set_pole_slots: the fused solve (shape 2) does not apply to f-sphere plans");
+      return REXI_EINVAL;
+    }
     if (used) *used = 0;
     return REXI_OK;
   }
