@@ -25,7 +25,7 @@
 //     (Sum beta/alpha Phi0, Sum beta/(alpha + i tau sigma_n) zeta0), takes the real part
 //     at m = 0 and writes each output coefficient once.
 // The forward-sweep values y go through a per-warp global buffer (L2-resident: one CTA
-// per SM, 128 lanes x lmax rows).  No partial sums leave the SM and no reduction kernel
+// of eight warps per SM, 256 lanes x lmax rows).  No partial sums leave the SM and no reduction kernel
 // follows.
 #include <cuda_runtime.h>
 
@@ -56,14 +56,15 @@ __device__ __forceinline__ double2 ldg2(const double2 *p) { return __ldg(p); }
 __device__ __forceinline__ void pf_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" : : "l"(p)); }
 __device__ __forceinline__ void pf_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" : : "l"(p)); }
 
-constexpr int kThreads = 128;  // four warps per CTA, one CTA per SM
-constexpr int kStreams = 4;    // delta, Phi, zeta at n + 1, zeta at n - 1
+constexpr int kWarps = 8;              // two warps per SM sub-partition, one CTA per SM
+constexpr int kThreads = 32 * kWarps;
+constexpr int kStreams = 4;            // delta, Phi, zeta at n + 1, zeta at n - 1
 
 struct FusedArgs {
   const double2 *fac;   // [F_NCOMP][nrows][P]
   const double2 *sin;   // [3][nspec][B]
   double2 *sout;        // [3][nspec][B]
-  double2 *ybuf;        // [gridDim.x * 4 warps][lmax][32]
+  double2 *ybuf;        // [gridDim.x * kWarps][lmax][32]
   const int4 *sys;      // per (m, p): {m, n0, len, row0}
   const int2 *items;    // (system 2 m + p, first state of the tile), longest first
   unsigned *counter;
@@ -71,6 +72,11 @@ struct FusedArgs {
   double2 sphi;         // Sum beta_k / alpha_k over the plan's poles
   int nitems, P, N, B, WS, WP, lmax, pole_begin, pole_end, realm0;
   int64_t nspec, nrows;
+};
+
+// one forward-sweep row of one lane: its factors and the states it reads
+struct FwdRow {
+  double2 l, g, e, f, d0, p0, zn;
 };
 
 // SB states per warp, PL = 32 / SB poles per warp pass, R = 8 / SB rows per task round
@@ -85,9 +91,9 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
   const int ST = a.WS * SB;                           // states per CTA tile
   const int lmax = a.lmax, N = a.N, B = a.B;
   const int64_t NS = a.nspec, NR = a.nrows, P = a.P;
-  double2 *acc = smem;                                             // [WP][ST][lmax][4]
+  double2 *acc = smem;                                                               // [WP][ST][lmax][4]
   double2 *wb = smem + (size_t)a.WP * ST * lmax * kStreams + (size_t)warp * R * 32;  // [R][32]
-  double2 *ybuf = a.ybuf + ((size_t)blockIdx.x * 4 + warp) * (size_t)lmax * 32 + lane;
+  double2 *ybuf = a.ybuf + ((size_t)blockIdx.x * kWarps + warp) * (size_t)lmax * 32 + lane;
   // sweep role: lane = (state s_sw, pole pl); task role: lane = (row r, state t_s, stream t)
   const int s_sw = lane / PL, pl = lane - s_sw * PL;
   const int t_r = lane / (4 * SB), t_s = (lane >> 2) % SB, t_t = lane & 3;
@@ -120,60 +126,68 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
       const double2 *sPhi = a.sin + bq, *sZeta = a.sin + NS * B + bq, *sDel = a.sin + 2 * NS * B + bq;
       const int npp = a.WP * PL;  // poles per CTA pass
       for (int kb = a.pole_begin; kb < a.pole_end; kb += npp) {
-        const int kw = kb + wp * PL;                            // this warp's first pole
-        const int npa = min(PL, a.pole_end - kw);               // its active poles (warp-uniform)
+        const int kw = kb + wp * PL;               // this warp's first pole
+        const int npa = min(PL, a.pole_end - kw);  // its active poles (warp-uniform)
         if (npa <= 0) continue;
-        const int k = kw + min(pl, npa - 1);                    // inactive lanes repeat a valid pole
+        const int k = kw + min(pl, npa - 1);       // inactive lanes repeat a valid pole
         const double2 *fL = a.fac + ((int64_t)F_L * NR + row0) * P + k;
         const double2 *fG = a.fac + ((int64_t)F_G * NR + row0) * P + k;
         const double2 *fE = a.fac + ((int64_t)F_E * NR + row0) * P + k;
         const double2 *fF = a.fac + ((int64_t)F_F * NR + row0) * P + k;
         const double2 *fC = a.fac + ((int64_t)F_C * NR + row0) * P + k;
 
-        // ---- forward sweep; the next row's factors and states are loaded one row ahead
+        // ---- forward sweep, two rows per iteration: the next row's factors and states
+        // are loaded while the current row computes (two register sets, no copies)
+        auto load_fwd = [&](int i, FwdRow &r) {
+          const int64_t o = (int64_t)i * P;
+          const int n = n0 + 2 * i;
+          const int64_t ix = base_idx + n;
+          if (i + 4 < len) {
+            const int64_t o4 = o + 4 * P;
+            pf_l2(fL + o4);
+            pf_l2(fG + o4);
+            pf_l2(fE + o4);
+            pf_l2(fF + o4);
+          }
+          r.l = ldg2(fL + o);
+          r.g = ldg2(fG + o);
+          r.e = ldg2(fE + o);
+          r.f = ldg2(fF + o);
+          r.d0 = ldg2(sDel + ix * B);
+          r.p0 = ldg2(sPhi + ix * B);
+          r.zn = (n + 1 <= N) ? ldg2(sZeta + (ix + 1) * B) : make_double2(0.0, 0.0);
+        };
         double2 yprev = make_double2(0.0, 0.0);
         double2 zprev = (n0 - 1 >= nmin) ? ldg2(sZeta + (base_idx + n0 - 1) * B) : make_double2(0.0, 0.0);
-        double2 cl = ldg2(fL), cg = ldg2(fG), ce = ldg2(fE), cf = ldg2(fF);
-        double2 cd0 = ldg2(sDel + (base_idx + n0) * B), cp0 = ldg2(sPhi + (base_idx + n0) * B);
-        double2 czn = (n0 + 1 <= N) ? ldg2(sZeta + (base_idx + n0 + 1) * B) : make_double2(0.0, 0.0);
-        for (int i = 0; i < len; ++i) {
-          const int inx = i + 1 < len ? i + 1 : i;
-          if (i + 3 < len) {
-            const int64_t o = (int64_t)(i + 3) * P;
-            pf_l2(fL + o);
-            pf_l2(fG + o);
-            pf_l2(fE + o);
-            pf_l2(fF + o);
-          }
-          const int64_t on = (int64_t)inx * P;
-          const int nn = n0 + 2 * inx;
-          const double2 nl = ldg2(fL + on), ng = ldg2(fG + on), ne = ldg2(fE + on), nf = ldg2(fF + on);
-          const double2 nd0 = ldg2(sDel + (base_idx + nn) * B), np0 = ldg2(sPhi + (base_idx + nn) * B);
-          const double2 nzn = (nn + 1 <= N) ? ldg2(sZeta + (base_idx + nn + 1) * B) : make_double2(0.0, 0.0);
-          double2 y = cfms_(cd0, cg, cp0);
-          y = cfms_(y, ce, zprev);
-          y = cfms_(y, cf, czn);
-          y = cfms_(y, cl, yprev);
+        auto fwd = [&](int i, const FwdRow &r) {
+          double2 y = cfms_(r.d0, r.g, r.p0);
+          y = cfms_(y, r.e, zprev);
+          y = cfms_(y, r.f, r.zn);
+          y = cfms_(y, r.l, yprev);
           ybuf[(size_t)i * 32] = y;
           yprev = y;
-          zprev = czn;
-          cl = nl; cg = ng; ce = ne; cf = nf;
-          cd0 = nd0; cp0 = np0; czn = nzn;
+          zprev = r.zn;
+        };
+        {
+          FwdRow A, Bn;
+          load_fwd(0, A);
+          int i = 0;
+          for (; i + 1 < len; i += 2) {
+            load_fwd(i + 1, Bn);
+            fwd(i, A);
+            if (i + 2 < len) load_fwd(i + 2, A);
+            fwd(i + 1, Bn);
+          }
+          if (i < len) fwd(i, A);
         }
 
         // ---- backward sweep; every R rows the lanes add the rows' w into the running sums
         double2 wnext = make_double2(0.0, 0.0);
-        double2 cy = ybuf[(size_t)(len - 1) * 32], cc = ldg2(fC + (int64_t)(len - 1) * P);
         int slot = 0;
-        for (int i = len - 1; i >= 0; --i) {
-          const int inx = i > 0 ? i - 1 : i;
-          if (i - 3 >= 0) pf_l2(fC + (int64_t)(i - 3) * P);
-          const double2 ny = ybuf[(size_t)inx * 32], nc = ldg2(fC + (int64_t)inx * P);
-          const double2 w = cfms_(cy, cc, wnext);
+        auto bwd = [&](int i, double2 y, double2 c) {
+          const double2 w = cfms_(y, c, wnext);
           wb[slot * 32 + lane] = w;
           wnext = w;
-          cy = ny;
-          cc = nc;
           ++slot;
           if (slot == R || i == 0) {
             __syncwarp();
@@ -201,6 +215,23 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
             __syncwarp();
             slot = 0;
           }
+        };
+        {
+          double2 ya = ybuf[(size_t)(len - 1) * 32], ca = ldg2(fC + (int64_t)(len - 1) * P);
+          double2 yb, cb;
+          int i = len - 1;
+          for (; i - 1 >= 0; i -= 2) {
+            if (i - 4 >= 0) pf_l2(fC + (int64_t)(i - 4) * P);
+            yb = ybuf[(size_t)(i - 1) * 32];
+            cb = ldg2(fC + (int64_t)(i - 1) * P);
+            bwd(i, ya, ca);
+            if (i - 2 >= 0) {
+              ya = ybuf[(size_t)(i - 2) * 32];
+              ca = ldg2(fC + (int64_t)(i - 2) * P);
+            }
+            bwd(i - 1, yb, cb);
+          }
+          if (i == 0) bwd(0, ya, ca);
         }
       }
     }
@@ -265,22 +296,22 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
 }  // namespace
 
 // Work items and CTA shape of the fused solve for a batch of B states: ST states per
-// CTA tile (the smallest power of two >= B, at most 16), split over the four warps as
-// WS state groups of SB states; when the tile has fewer than four states the remaining
+// CTA tile (the smallest power of two >= B, at most 32), split over the eight warps as
+// WS state groups of SB states; when the tile has fewer than eight states the remaining
 // warps split the poles (WP groups).  Returns false when the running sums of a tile do
 // not fit in shared memory (the slot-partial path then serves the plan).
 bool build_fused_layout(Plan &pl, int B, FusedLayout &F) {
   F = FusedLayout{};
   int st = 1;
-  while (st < B && st < 16) st *= 2;
+  while (st < B && st < 32) st *= 2;
   const int dev = pl.device;
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   for (; st >= 1; st /= 2) {
     int sb, ws, wp;
-    if (st >= 4) { sb = st / 4; ws = 4; wp = 1; }
-    else { sb = 1; ws = st; wp = 4 / st; }
-    const size_t smem = ((size_t)wp * st * pl.lmax * kStreams + (size_t)4 * (8 / sb) * 32) * sizeof(double2);
+    if (st >= kWarps) { sb = st / kWarps; ws = kWarps; wp = 1; }
+    else { sb = 1; ws = st; wp = kWarps / st; }
+    const size_t smem = ((size_t)wp * st * pl.lmax * kStreams + (size_t)kWarps * (8 / sb) * 32) * sizeof(double2);
     if (smem + 1024 > (size_t)smem_max) continue;
     F.sb = sb;
     F.ws = ws;
@@ -316,7 +347,7 @@ cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, con
   a.fac = adjoint ? pl.fac_adj : pl.fac_fwd;
   a.sin = sin;
   a.sout = sout;
-  a.ybuf = pl.yscratch;  // sized for 16 warps x 2 poles per SM: four warps of one pole here
+  a.ybuf = pl.yscratch;  // sized for 16 warps x 2 poles per SM: eight warps of one pole here
   a.sys = pl.sys_dev;
   a.items = F.items_dev;
   a.counter = pl.counter;
