@@ -80,22 +80,28 @@ struct FwdRow {
 };
 
 // SB states per warp, PL = 32 / SB poles per warp pass, R = 8 / SB rows per task round
-// (lanes = R rows x SB states x 4 streams).
+// (lanes = R rows x SB states x 4 streams).  Shared memory: the running sums
+// [WP * ST][lmax * 4 + 1] (an odd plane stride spreads the states over the banks), then
+// per warp two exchange buffers of R rows x (32 + SB) values (a pad after every state's
+// PL lanes and a row stride of SB mod 8 put the R x SB (row, state) groups that a task
+// instruction reads on distinct banks).
 template <int SB>
 __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
-  constexpr int PL = 32 / SB, R = 8 / SB;
+  constexpr int PL = 32 / SB, R = 8 / SB, RS = 32 + SB;
   extern __shared__ double2 smem[];
   __shared__ int s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ws = warp / a.WP, wp = warp - ws * a.WP;  // state group, pole group of this warp
   const int ST = a.WS * SB;                           // states per CTA tile
   const int lmax = a.lmax, N = a.N, B = a.B;
+  const int ACS = lmax * kStreams + 1;                // running-sum plane stride
   const int64_t NS = a.nspec, NR = a.nrows, P = a.P;
-  double2 *acc = smem;                                                               // [WP][ST][lmax][4]
-  double2 *wb = smem + (size_t)a.WP * ST * lmax * kStreams + (size_t)warp * R * 32;  // [R][32]
+  double2 *acc = smem;                                                           // [WP * ST][ACS]
+  double2 *wbase = smem + (size_t)a.WP * ST * ACS + (size_t)warp * 2 * R * RS;  // [2][R][RS]
   double2 *ybuf = a.ybuf + ((size_t)blockIdx.x * kWarps + warp) * (size_t)lmax * 32 + lane;
   // sweep role: lane = (state s_sw, pole pl); task role: lane = (row r, state t_s, stream t)
   const int s_sw = lane / PL, pl = lane - s_sw * PL;
+  const int wslot = lane + s_sw;  // this lane's place in an exchange row
   const int t_r = lane / (4 * SB), t_s = (lane >> 2) % SB, t_t = lane & 3;
   const int t_comp = t_t == 0 ? F_BD : (t_t == 1 ? F_BAD : (t_t == 2 ? F_ZP : F_ZM));
 
@@ -116,7 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
     // running sums of this item start at zero
     for (int q = threadIdx.x; q < a.WP * ST * len * kStreams; q += kThreads) {
       const int t = q % kStreams, rest = q / kStreams, i = rest % len, g = rest / len;  // g = wp * ST + st
-      acc[((size_t)g * lmax + i) * kStreams + t] = make_double2(0.0, 0.0);
+      acc[(size_t)g * ACS + i * kStreams + t] = make_double2(0.0, 0.0);
     }
     __syncthreads();
 
@@ -125,11 +131,13 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
       const int bq = bsw < B ? bsw : b0;
       const double2 *sPhi = a.sin + bq, *sZeta = a.sin + NS * B + bq, *sDel = a.sin + 2 * NS * B + bq;
       const int npp = a.WP * PL;  // poles per CTA pass
+      const int nr = (len + R - 1) / R;  // task rounds of the backward sweep
       for (int kb = a.pole_begin; kb < a.pole_end; kb += npp) {
         const int kw = kb + wp * PL;               // this warp's first pole
         const int npa = min(PL, a.pole_end - kw);  // its active poles (warp-uniform)
         if (npa <= 0) continue;
-        const int k = kw + min(pl, npa - 1);       // inactive lanes repeat a valid pole
+        const bool active = pl < npa;              // inactive lanes repeat a valid pole, add zero
+        const int k = kw + min(pl, npa - 1);
         const double2 *fL = a.fac + ((int64_t)F_L * NR + row0) * P + k;
         const double2 *fG = a.fac + ((int64_t)F_G * NR + row0) * P + k;
         const double2 *fE = a.fac + ((int64_t)F_E * NR + row0) * P + k;
@@ -181,57 +189,56 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
           if (i < len) fwd(i, A);
         }
 
-        // ---- backward sweep; every R rows the lanes add the rows' w into the running sums
+        // ---- backward sweep in rounds of R rows from the top, software-pipelined: the
+        // recurrence of round rr + 1 and the pole sum of round rr are independent work in
+        // one block, and the sweep values of round rr + 2 are loaded meanwhile
         double2 wnext = make_double2(0.0, 0.0);
-        int slot = 0;
-        auto bwd = [&](int i, double2 y, double2 c) {
-          const double2 w = cfms_(y, c, wnext);
-          wb[slot * 32 + lane] = w;
-          wnext = w;
-          ++slot;
-          if (slot == R || i == 0) {
-            __syncwarp();
-            if (t_r < slot) {
-              const int ii = i + slot - 1 - t_r;  // the row this lane sums
-              double2 *ap = acc + (((size_t)wp * ST + ws * SB + t_s) * lmax + ii) * kStreams + t_t;
-              const double2 *W = a.fac + ((int64_t)t_comp * NR + row0 + ii) * P + kw;
-              const double2 *wv = wb + t_r * 32 + t_s * PL;
-              double2 s = *ap;
-              if (npa == PL) {
+        double2 yv[R], cv[R];
+        auto load_round = [&](int rr) {
 #pragma unroll
-                for (int q = 0; q < PL; ++q) s = cfma_(s, ldg2(W + q), wv[q]);
-              } else {
-                for (int q = 0; q < npa; ++q) s = cfma_(s, ldg2(W + q), wv[q]);
-              }
-              *ap = s;
-              // the next round's weights (R rows further down) into L1
-              if (ii - R >= 0) {
-                const double2 *Wn = W - (int64_t)R * P;
-#pragma unroll
-                for (int q = 0; q < PL; q += 8)
-                  if (q < npa) pf_l1(Wn + q);  // poles of this pass only: every address inside the factors
-              }
-            }
-            __syncwarp();
-            slot = 0;
+          for (int j = 0; j < R; ++j) {
+            const int i = max(len - 1 - rr * R - j, 0);
+            yv[j] = ybuf[(size_t)i * 32];
+            cv[j] = ldg2(fC + (int64_t)i * P);
           }
         };
-        {
-          double2 ya = ybuf[(size_t)(len - 1) * 32], ca = ldg2(fC + (int64_t)(len - 1) * P);
-          double2 yb, cb;
-          int i = len - 1;
-          for (; i - 1 >= 0; i -= 2) {
-            if (i - 4 >= 0) pf_l2(fC + (int64_t)(i - 4) * P);
-            yb = ybuf[(size_t)(i - 1) * 32];
-            cb = ldg2(fC + (int64_t)(i - 1) * P);
-            bwd(i, ya, ca);
-            if (i - 2 >= 0) {
-              ya = ybuf[(size_t)(i - 2) * 32];
-              ca = ldg2(fC + (int64_t)(i - 2) * P);
+        auto rec_round = [&](int rr, double2 *wbuf) {
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            if (len - 1 - rr * R - j >= 0) {
+              const double2 w = cfms_(yv[j], cv[j], wnext);
+              wbuf[j * RS + wslot] = active ? w : make_double2(0.0, 0.0);
+              wnext = w;
             }
-            bwd(i - 1, yb, cb);
           }
-          if (i == 0) bwd(0, ya, ca);
+        };
+        auto task_round = [&](int rr, const double2 *wbuf) {
+          const int iv = len - 1 - rr * R - t_r;  // the row this lane sums (< 0: none)
+          const int ii = max(iv, 0);
+          double2 *ap = acc + ((size_t)wp * ST + ws * SB + t_s) * ACS + ii * kStreams + t_t;
+          const double2 *W = a.fac + ((int64_t)t_comp * NR + row0 + ii) * P + kw;
+          const double2 *wv = wbuf + t_r * RS + t_s * (PL + 1);
+          double2 s = *ap;
+#pragma unroll
+          for (int q = 0; q < PL; ++q) s = cfma_(s, ldg2(W + min(q, npa - 1)), wv[q]);  // w = 0 past npa
+          if (iv >= 0) *ap = s;
+          if (iv - R >= 0) {  // the next round's weights (R rows further down) into L1
+            const double2 *Wn = W - (int64_t)R * P;
+#pragma unroll
+            for (int q = 0; q < PL; q += 8)
+              if (q < npa) pf_l1(Wn + q);  // poles of this pass only: every address inside the factors
+          }
+        };
+        load_round(0);
+        rec_round(0, wbase);
+        if (nr > 1) load_round(1);
+        __syncwarp();
+        for (int rr = 0; rr < nr; ++rr) {
+          double2 *wcur = wbase + (rr & 1) * R * RS, *wnxt = wbase + ((rr + 1) & 1) * R * RS;
+          if (rr + 1 < nr) rec_round(rr + 1, wnxt);
+          if (rr + 2 < nr) load_round(rr + 2);
+          task_round(rr, wcur);
+          __syncwarp();
         }
       }
     }
@@ -250,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
         auto sumacc = [&](int i, int t) {
           double2 v = make_double2(0.0, 0.0);
           for (int g = 0; g < a.WP; ++g) {
-            const double2 u = acc[(((size_t)g * ST + st) * lmax + i) * kStreams + t];
+            const double2 u = acc[((size_t)g * ST + st) * ACS + i * kStreams + t];
             v.x += u.x;
             v.y += u.y;
           }
@@ -311,7 +318,8 @@ bool build_fused_layout(Plan &pl, int B, FusedLayout &F) {
     int sb, ws, wp;
     if (st >= kWarps) { sb = st / kWarps; ws = kWarps; wp = 1; }
     else { sb = 1; ws = st; wp = kWarps / st; }
-    const size_t smem = ((size_t)wp * st * pl.lmax * kStreams + (size_t)kWarps * (8 / sb) * 32) * sizeof(double2);
+    const size_t smem =
+        ((size_t)wp * st * (pl.lmax * kStreams + 1) + (size_t)kWarps * 2 * (8 / sb) * (32 + sb)) * sizeof(double2);
     if (smem + 1024 > (size_t)smem_max) continue;
     F.sb = sb;
     F.ws = ws;
