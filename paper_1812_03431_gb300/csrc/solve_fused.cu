@@ -178,16 +178,19 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
         zprev = zinit;
         load_fwd(0, fcur);
       };
-      auto fwd_row = [&](int i) {  // row i of the current forward pass; loads row i + 1
-        FwdRow nx;
-        if (i + 1 < len) load_fwd(i + 1, nx);
-        double2 y = cfms_(fcur.d0, fcur.g, fcur.p0);
-        y = cfms_(y, fcur.e, zprev);
-        y = cfms_(y, fcur.f, fcur.zn);
-        y = cfms_(y, fcur.l, yprev);
+      auto fwd_compute = [&](int i, const FwdRow &r) {  // row i of the current forward pass
+        double2 y = cfms_(r.d0, r.g, r.p0);
+        y = cfms_(y, r.e, zprev);
+        y = cfms_(y, r.f, r.zn);
+        y = cfms_(y, r.l, yprev);
         ybuf[(size_t)slot_of(fpi, i) * 32] = y;
         yprev = y;
-        zprev = fcur.zn;
+        zprev = r.zn;
+      };
+      auto fwd_row = [&](int i) {  // row i with fcur holding it; loads row i + 1 into fcur
+        FwdRow nx;
+        if (i + 1 < len) load_fwd(i + 1, nx);
+        fwd_compute(i, fcur);
         if (i + 1 < len) fcur = nx;
       };
 
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
           const double2 *W = a.fac + ((int64_t)t_comp * NR + row0 + ii) * P + kw;
           const double2 *wv = wbuf + t_r * RS + t_s * (PL + 1);
           double2 s = *ap;
-#pragma unroll
+#pragma unroll 4
           for (int q = 0; q < PL; ++q) s = cfma_(s, ldg2(W + min(q, npa - 1)), wv[q]);  // w = 0 past npa
           if (iv >= 0) *ap = s;
           if (iv - R >= 0) {  // the next round's weights (R rows further down) into L1
@@ -254,14 +257,44 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
         __syncwarp();
         for (int rr = 0; rr < nr; ++rr) {
           double2 *wcur = wbase + (rr & 1) * R * RS, *wnxt = wbase + ((rr + 1) & 1) * R * RS;
-          if (rr + 1 < nr) rec_round(rr + 1, wnxt);
-          if (rr + 2 < nr) load_round(rr + 2);
-          // forward rows rr R .. rr R + R - 1 of pass pi + 1: their slots held rows
-          // len - 1 - rr R - j of pass pi, read by load_round(rr) two rounds ago
-          if (next) {
+          if (next && (rr + 3) * R <= len) {
+            // rounds rr + 1 and rr + 2 are full and the forward rows rr R .. rr R + R are
+            // inside the system: one branch-free block of three independent chains
+            // (backward recurrence, forward recurrence, pole sum)
 #pragma unroll
-            for (int j = 0; j < R; ++j)
-              if (rr * R + j < len) fwd_row(rr * R + j);
+            for (int j = 0; j < R; ++j) {
+              const double2 w = cfms_(yv[j], cv[j], wnext);
+              wnxt[j * RS + wslot] = active ? w : make_double2(0.0, 0.0);
+              wnext = w;
+            }
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+              const int i = len - 1 - (rr + 2) * R - j;
+              yv[j] = ybuf[(size_t)slot_of(pi, i) * 32];
+              cv[j] = ldg2(fC + (int64_t)i * P);
+            }
+            // forward rows t0 .. t0 + R - 1 of pass pi + 1 (their slots held rows
+            // len - 1 - t of pass pi, read by load_round(rr) two rounds ago); fcur holds
+            // row t0 on entry and row t0 + R on exit
+            const int t0 = rr * R;
+            FwdRow alt;
+#pragma unroll
+            for (int j = 0; j < R; j += 2) {
+              load_fwd(t0 + j + 1, alt);
+              fwd_compute(t0 + j, fcur);
+              load_fwd(t0 + j + 2, fcur);
+              fwd_compute(t0 + j + 1, alt);
+            }
+          } else {
+            if (rr + 1 < nr) rec_round(rr + 1, wnxt);
+            if (rr + 2 < nr) load_round(rr + 2);
+            // forward rows rr R .. rr R + R - 1 of pass pi + 1: their slots held rows
+            // len - 1 - rr R - j of pass pi, read by load_round(rr) two rounds ago
+            if (next) {
+#pragma unroll
+              for (int j = 0; j < R; ++j)
+                if (rr * R + j < len) fwd_row(rr * R + j);
+            }
           }
           task_round(rr, wcur);
           __syncwarp();
