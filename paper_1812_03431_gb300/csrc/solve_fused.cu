@@ -130,97 +130,75 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
       const int bsw = b0 + ws * SB + s_sw;  // the sweep lane's state (clamped for loads)
       const int bq = bsw < B ? bsw : b0;
       const double2 *sPhi = a.sin + bq, *sZeta = a.sin + NS * B + bq, *sDel = a.sin + 2 * NS * B + bq;
-      const int npp = a.WP * PL;                      // poles per CTA pass
-      const int nr = (len + R - 1) / R;               // task rounds of a backward sweep
-      const int npass = (a.pole_end - a.pole_begin + npp - 1) / npp;
-      const double2 zinit = (n0 - 1 >= nmin) ? ldg2(sZeta + (base_idx + n0 - 1) * B) : make_double2(0.0, 0.0);
-
-      // pass pi: this warp's poles kw .. kw + npa - 1 (npa <= 0: none this pass)
-      auto pass_kw = [&](int pi) { return a.pole_begin + pi * npp + wp * PL; };
-      // the sweep buffer slot of row i in pass pi: passes alternate the orientation, so that
-      // the forward sweep of pass pi + 1 writes row t into the slot from which the backward
-      // sweep of pass pi has just read row len - 1 - t (one buffer serves both sweeps)
-      auto slot_of = [&](int pi, int i) { return (pi & 1) ? len - 1 - i : i; };
-
-      // ---- forward sweep state (one pass at a time)
-      const double2 *fL = nullptr, *fG = nullptr, *fE = nullptr, *fF = nullptr;
-      int fpi = 0;
-      double2 yprev = make_double2(0.0, 0.0), zprev = zinit;
-      FwdRow fcur;
-      auto load_fwd = [&](int i, FwdRow &r) {
-        const int64_t o = (int64_t)i * P;
-        const int n = n0 + 2 * i;
-        const int64_t ix = base_idx + n;
-        if (i + 4 < len) {
-          const int64_t o4 = o + 4 * P;
-          pf_l2(fL + o4);
-          pf_l2(fG + o4);
-          pf_l2(fE + o4);
-          pf_l2(fF + o4);
-        }
-        r.l = ldg2(fL + o);
-        r.g = ldg2(fG + o);
-        r.e = ldg2(fE + o);
-        r.f = ldg2(fF + o);
-        r.d0 = ldg2(sDel + ix * B);
-        r.p0 = ldg2(sPhi + ix * B);
-        r.zn = (n + 1 <= N) ? ldg2(sZeta + (ix + 1) * B) : make_double2(0.0, 0.0);
-      };
-      auto fwd_begin = [&](int pi) {  // pass pi's pointers and its first row
-        fpi = pi;
-        const int kw = pass_kw(pi), npa = min(PL, a.pole_end - kw);
-        const int k = kw + min(pl, max(npa, 1) - 1);
-        fL = a.fac + ((int64_t)F_L * NR + row0) * P + k;
-        fG = a.fac + ((int64_t)F_G * NR + row0) * P + k;
-        fE = a.fac + ((int64_t)F_E * NR + row0) * P + k;
-        fF = a.fac + ((int64_t)F_F * NR + row0) * P + k;
-        yprev = make_double2(0.0, 0.0);
-        zprev = zinit;
-        load_fwd(0, fcur);
-      };
-      auto fwd_compute = [&](int i, const FwdRow &r) {  // row i of the current forward pass
-        double2 y = cfms_(r.d0, r.g, r.p0);
-        y = cfms_(y, r.e, zprev);
-        y = cfms_(y, r.f, r.zn);
-        y = cfms_(y, r.l, yprev);
-        ybuf[(size_t)slot_of(fpi, i) * 32] = y;
-        yprev = y;
-        zprev = r.zn;
-      };
-      auto fwd_row = [&](int i) {  // row i with fcur holding it; loads row i + 1 into fcur
-        FwdRow nx;
-        if (i + 1 < len) load_fwd(i + 1, nx);
-        fwd_compute(i, fcur);
-        if (i + 1 < len) fcur = nx;
-      };
-
-      // pass 0's forward sweep on its own; then every pass's backward sweep runs together
-      // with the next pass's forward sweep, row for row
-      if (npass > 0 && pass_kw(0) < a.pole_end) {
-        fwd_begin(0);
-        for (int i = 0; i < len; ++i) fwd_row(i);
-      }
-      for (int pi = 0; pi < npass; ++pi) {
-        const int kw = pass_kw(pi);
-        const int npa = min(PL, a.pole_end - kw);  // active poles of this warp's pass (warp-uniform)
-        const int kwn = pass_kw(pi + 1);
-        const bool next = pi + 1 < npass && kwn < a.pole_end;  // this warp sweeps pass pi + 1 too
+      const int npp = a.WP * PL;  // poles per CTA pass
+      const int nr = (len + R - 1) / R;  // task rounds of the backward sweep
+      for (int kb = a.pole_begin; kb < a.pole_end; kb += npp) {
+        const int kw = kb + wp * PL;               // this warp's first pole
+        const int npa = min(PL, a.pole_end - kw);  // its active poles (warp-uniform)
         if (npa <= 0) continue;
-        const bool active = pl < npa;  // inactive lanes repeat a valid pole and add zero
+        const bool active = pl < npa;              // inactive lanes repeat a valid pole, add zero
         const int k = kw + min(pl, npa - 1);
+        const double2 *fL = a.fac + ((int64_t)F_L * NR + row0) * P + k;
+        const double2 *fG = a.fac + ((int64_t)F_G * NR + row0) * P + k;
+        const double2 *fE = a.fac + ((int64_t)F_E * NR + row0) * P + k;
+        const double2 *fF = a.fac + ((int64_t)F_F * NR + row0) * P + k;
         const double2 *fC = a.fac + ((int64_t)F_C * NR + row0) * P + k;
-        if (next) fwd_begin(pi + 1);
+
+        // ---- forward sweep, two rows per iteration: the next row's factors and states
+        // are loaded while the current row computes (two register sets, no copies)
+        auto load_fwd = [&](int i, FwdRow &r) {
+          const int64_t o = (int64_t)i * P;
+          const int n = n0 + 2 * i;
+          const int64_t ix = base_idx + n;
+          if (i + 4 < len) {
+            const int64_t o4 = o + 4 * P;
+            pf_l2(fL + o4);
+            pf_l2(fG + o4);
+            pf_l2(fE + o4);
+            pf_l2(fF + o4);
+          }
+          r.l = ldg2(fL + o);
+          r.g = ldg2(fG + o);
+          r.e = ldg2(fE + o);
+          r.f = ldg2(fF + o);
+          r.d0 = ldg2(sDel + ix * B);
+          r.p0 = ldg2(sPhi + ix * B);
+          r.zn = (n + 1 <= N) ? ldg2(sZeta + (ix + 1) * B) : make_double2(0.0, 0.0);
+        };
+        double2 yprev = make_double2(0.0, 0.0);
+        double2 zprev = (n0 - 1 >= nmin) ? ldg2(sZeta + (base_idx + n0 - 1) * B) : make_double2(0.0, 0.0);
+        auto fwd = [&](int i, const FwdRow &r) {
+          double2 y = cfms_(r.d0, r.g, r.p0);
+          y = cfms_(y, r.e, zprev);
+          y = cfms_(y, r.f, r.zn);
+          y = cfms_(y, r.l, yprev);
+          ybuf[(size_t)i * 32] = y;
+          yprev = y;
+          zprev = r.zn;
+        };
+        {
+          FwdRow A, Bn;
+          load_fwd(0, A);
+          int i = 0;
+          for (; i + 1 < len; i += 2) {
+            load_fwd(i + 1, Bn);
+            fwd(i, A);
+            if (i + 2 < len) load_fwd(i + 2, A);
+            fwd(i + 1, Bn);
+          }
+          if (i < len) fwd(i, A);
+        }
 
         // ---- backward sweep in rounds of R rows from the top, software-pipelined: the
-        // recurrence of round rr + 1, the pole sum of round rr and R rows of the next pass's
-        // forward sweep are independent work in one block
+        // recurrence of round rr + 1 and the pole sum of round rr are independent work in
+        // one block, and the sweep values of round rr + 2 are loaded meanwhile
         double2 wnext = make_double2(0.0, 0.0);
         double2 yv[R], cv[R];
         auto load_round = [&](int rr) {
 #pragma unroll
           for (int j = 0; j < R; ++j) {
             const int i = max(len - 1 - rr * R - j, 0);
-            yv[j] = ybuf[(size_t)slot_of(pi, i) * 32];
+            yv[j] = ybuf[(size_t)i * 32];
             cv[j] = ldg2(fC + (int64_t)i * P);
           }
         };
@@ -241,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
           const double2 *W = a.fac + ((int64_t)t_comp * NR + row0 + ii) * P + kw;
           const double2 *wv = wbuf + t_r * RS + t_s * (PL + 1);
           double2 s = *ap;
-#pragma unroll 4
+#pragma unroll
           for (int q = 0; q < PL; ++q) s = cfma_(s, ldg2(W + min(q, npa - 1)), wv[q]);  // w = 0 past npa
           if (iv >= 0) *ap = s;
           if (iv - R >= 0) {  // the next round's weights (R rows further down) into L1
@@ -257,45 +235,8 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
         __syncwarp();
         for (int rr = 0; rr < nr; ++rr) {
           double2 *wcur = wbase + (rr & 1) * R * RS, *wnxt = wbase + ((rr + 1) & 1) * R * RS;
-          if (next && (rr + 3) * R <= len) {
-            // rounds rr + 1 and rr + 2 are full and the forward rows rr R .. rr R + R are
-            // inside the system: one branch-free block of three independent chains
-            // (backward recurrence, forward recurrence, pole sum)
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-              const double2 w = cfms_(yv[j], cv[j], wnext);
-              wnxt[j * RS + wslot] = active ? w : make_double2(0.0, 0.0);
-              wnext = w;
-            }
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-              const int i = len - 1 - (rr + 2) * R - j;
-              yv[j] = ybuf[(size_t)slot_of(pi, i) * 32];
-              cv[j] = ldg2(fC + (int64_t)i * P);
-            }
-            // forward rows t0 .. t0 + R - 1 of pass pi + 1 (their slots held rows
-            // len - 1 - t of pass pi, read by load_round(rr) two rounds ago); fcur holds
-            // row t0 on entry and row t0 + R on exit
-            const int t0 = rr * R;
-            FwdRow alt;
-#pragma unroll
-            for (int j = 0; j < R; j += 2) {
-              load_fwd(t0 + j + 1, alt);
-              fwd_compute(t0 + j, fcur);
-              load_fwd(t0 + j + 2, fcur);
-              fwd_compute(t0 + j + 1, alt);
-            }
-          } else {
-            if (rr + 1 < nr) rec_round(rr + 1, wnxt);
-            if (rr + 2 < nr) load_round(rr + 2);
-            // forward rows rr R .. rr R + R - 1 of pass pi + 1: their slots held rows
-            // len - 1 - rr R - j of pass pi, read by load_round(rr) two rounds ago
-            if (next) {
-#pragma unroll
-              for (int j = 0; j < R; ++j)
-                if (rr * R + j < len) fwd_row(rr * R + j);
-            }
-          }
+          if (rr + 1 < nr) rec_round(rr + 1, wnxt);
+          if (rr + 2 < nr) load_round(rr + 2);
           task_round(rr, wcur);
           __syncwarp();
         }
