@@ -531,10 +531,23 @@ const FusedLayout *fused_layout(Plan &pl, int B) {
   auto it = pl.fused.find(B);
   if (it == pl.fused.end()) {
     FusedLayout F;
-    if (!build_fused_layout(pl, B, F)) F = FusedLayout{};  // st == 0: not available
-    it = pl.fused.emplace(B, F).first;
+    auto ft = pl.fused_tile.find(B);
+    if (!build_fused_layout(pl, B, ft != pl.fused_tile.end() ? ft->second : 0, F)) F = FusedLayout{};
+    it = pl.fused.emplace(B, F).first;  // st == 0: not available
   }
   return it->second.st > 0 ? &it->second : nullptr;
+}
+
+// the fused layout for batch B with a requested CTA tile (0: the default), replacing any
+// earlier one
+const FusedLayout *set_fused_tile(Plan &pl, int B, int tile) {
+  auto it = pl.fused.find(B);
+  if (it != pl.fused.end()) {
+    if (it->second.items_dev) cudaFree(it->second.items_dev);
+    pl.fused.erase(it);
+  }
+  pl.fused_tile[B] = tile;
+  return fused_layout(pl, B);
 }
 
 // A given slot count for batch B: the layout with slots / kk pole groups replaces any
@@ -543,13 +556,13 @@ const FusedLayout *fused_layout(Plan &pl, int B) {
 rexi_status set_layout(Plan &pl, int B, int slots, int shape, int *used) {
   if (shape == 2) {
     pl.use_slots[B] = false;
-    if (!fused_layout(pl, B)) {
+    if (!set_fused_tile(pl, B, slots)) {
       pl.use_slots[B] = true;
       set_error("rexi_set_pole_slots: the fused solve (shape 2) needs binary64 solves of the delta solver on "
                 "the rotating sphere, with running sums that fit in shared memory");
       return REXI_EINVAL;
     }
-    if (used) *used = 0;
+    if (used) *used = fused_layout(pl, B)->st;
     return REXI_OK;
   }
   SolveLayout L;
@@ -625,16 +638,27 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
       cudaFree(L.items_dev);
     }
   }
-  // the fused solve (no slot partials, no reduction) competes with the best slot layout
+  // the fused solve (no slot partials, no reduction) in its CTA tiles of 32 ... 1 states
+  // competes with the best slot layout
   float fused_ms = 1e30f;
+  int best_tile = 0;
   pl.use_slots[B] = false;
-  if (const FusedLayout *F = fused_layout(pl, B)) {
+  for (int tile = 32; tile >= 1; tile /= 2) {
+    const FusedLayout *F = set_fused_tile(pl, B, tile);
+    if (!F || F->st != tile) continue;  // the default is smaller, or it does not fit
     launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);  // warm-up
     cudaEventRecord(e0, st);
     for (int rep = 0; rep < 2; ++rep) launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);
     cudaEventRecord(e1, st);
-    if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&fused_ms, e0, e1);
+    float ms = 1e30f;
+    if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < fused_ms) {
+      fused_ms = ms;
+      best_tile = tile;
+    }
+    if (tile <= 4) break;  // smaller tiles only re-read the factors more often
   }
+  if (best_tile > 0) set_fused_tile(pl, B, best_tile);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   auto it = pl.layouts.find(B);
@@ -645,7 +669,7 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
   pl.layouts.emplace(B, bestL);
   const bool fused_wins = fused_ms <= best;
   pl.use_slots[B] = !fused_wins;
-  if (slots_out) *slots_out = fused_wins ? 0 : bestL.slots;
+  if (slots_out) *slots_out = fused_wins ? best_tile : bestL.slots;
   if (shape_out) *shape_out = fused_wins ? 2 : bestL.shape;
   return REXI_OK;
 }

@@ -218,6 +218,7 @@ struct Plan {
   // layout above was chosen instead (rexi_tune, rexi_set_pole_slots, pole_slots)
   std::map<int, FusedLayout> fused;
   std::map<int, bool> use_slots;
+  std::map<int, int> fused_tile;  // requested states per CTA tile (0: the default)
 
   // optional per-stage timing with CUDA events on the launching stream
   bool prof = false;
@@ -267,7 +268,7 @@ SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double
                     int pole_begin, int pole_end);
 // fused solve: eligible plans (binary64 delta solver on the rotating sphere) whose running
 // sums fit in shared memory; sin -> sout ([3][nspec][B]) with no partial sums and no reduction
-bool build_fused_layout(Plan &pl, int B, FusedLayout &F);
+bool build_fused_layout(Plan &pl, int B, int tile, FusedLayout &F);
 cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, const double2 *sin, double2 *sout,
                                int B, cudaStream_t st);
 cudaError_t launch_solve_ragged(const SolveView *views_dev, const WorkItem *items, int nitems, double2 *ybuf,

@@ -303,14 +303,18 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
 }  // namespace
 
 // Work items and CTA shape of the fused solve for a batch of B states: ST states per
-// CTA tile (the smallest power of two >= B, at most 32), split over the eight warps as
-// WS state groups of SB states; when the tile has fewer than eight states the remaining
-// warps split the poles (WP groups).  Returns false when the running sums of a tile do
+// CTA tile (the smallest power of two >= B, at most 32, or a smaller requested tile),
+// split over the eight warps as WS state groups of SB states; when the tile has fewer
+// than eight states the remaining warps split the poles (WP groups).  Smaller tiles give
+// more, shorter work items (better balance over the SMs) at the cost of reading each
+// factor once per tile.  Returns false when the running sums of a tile do
 // not fit in shared memory (the slot-partial path then serves the plan).
-bool build_fused_layout(Plan &pl, int B, FusedLayout &F) {
+bool build_fused_layout(Plan &pl, int B, int tile, FusedLayout &F) {
   F = FusedLayout{};
   int st = 1;
   while (st < B && st < 32) st *= 2;
+  if (tile > 0)  // a requested tile: the largest power of two <= tile (and <= the default)
+    while (st > 1 && st > tile) st /= 2;
   const int dev = pl.device;
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -311,8 +311,8 @@ class Plan:
 
     def set_pole_slots(self, batch, slots, shape=0):
         """rexi_set_pole_slots: use this pole-slot count and layout shape (0: the same groups
-        for every zonal order, 1: in proportion to the system length; 2: the fused solve,
-        slots ignored) for this batch size."""
+        for every zonal order, 1: in proportion to the system length) for this batch size,
+        or shape 2: the fused solve with ``slots`` states per CTA tile (0: default)."""
         n = _I32()
         _check("rexi_set_pole_slots", load().rexi_set_pole_slots(self._h, batch, slots, shape, ctypes.byref(n)))
         self.layout_shape[batch] = shape

@@ -39,9 +39,13 @@ def test_fused_step_matches_oracle_and_slot_solve(N, M, B, tau):
     S = inputs.random_spectral(N, B, 500 + N + B)
     x = torch.from_numpy(S).cuda()
     plan = rexi.Plan(N, *grid(N), tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
-    assert plan.set_pole_slots(B, 0, 2) == 0  # the fused solve
+    tile = plan.set_pole_slots(B, 0, 2)  # the fused solve with its default CTA tile
+    assert tile >= 1 and tile >= min(B, 32) and tile & (tile - 1) == 0
     fused = plan.step(x).cpu().numpy()
     np.testing.assert_array_equal(plan.step(x).cpu().numpy(), fused)  # bit-reproducible
+    if B > 2:  # a smaller tile: more, shorter work items, the same sums
+        assert plan.set_pole_slots(B, tile // 2, 2) == tile // 2
+        np.testing.assert_array_equal(plan.step(x).cpu().numpy(), fused)
     plan.set_pole_slots(B, 8, 0)  # the pole-slot solve and its reduction
     slot = plan.step(x).cpu().numpy()
     plan.close()
