@@ -43,9 +43,13 @@ def test_fused_step_matches_oracle_and_slot_solve(N, M, B, tau):
     assert tile >= 1 and tile >= min(B, 32) and tile & (tile - 1) == 0
     fused = plan.step(x).cpu().numpy()
     np.testing.assert_array_equal(plan.step(x).cpu().numpy(), fused)  # bit-reproducible
-    if B > 2:  # a smaller tile: more, shorter work items, the same sums
+    if B > 2:  # a smaller tile: more, shorter work items; below 8 states the poles of a
+        # tile are split over warp groups, which changes the order of the sum
         assert plan.set_pole_slots(B, tile // 2, 2) == tile // 2
-        np.testing.assert_array_equal(plan.step(x).cpu().numpy(), fused)
+        half = plan.step(x).cpu().numpy()
+        if tile // 2 >= 8:
+            np.testing.assert_array_equal(half, fused)
+        assert fieldwise(half, fused) < 1e-13
     plan.set_pole_slots(B, 8, 0)  # the pole-slot solve and its reduction
     slot = plan.step(x).cpu().numpy()
     plan.close()
