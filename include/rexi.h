@@ -118,12 +118,13 @@ typedef struct {
   int32_t strict_range; /* 1: plan creation fails with REXI_ERANGE when tau * max|omega|
                            exceeds h (M - 10), the range where Re of the REXI symbol
                            matches cos to the fit level */
-  int32_t pole_slots;   /* 0: the default solve -- with binary64 solves of the delta solver
-                           on the rotating sphere, the fused solve that keeps the pole sum
-                           on chip (one kernel, every output written once), else the
-                           pole-slot solve; > 0: the pole-slot solve with this many pole
-                           groups summed separately, then reduced in slot order (a
-                           deterministic tuning knob, any >= 1) */
+  int32_t pole_slots;   /* 0: the default solve -- for batches of one or two states with
+                           binary64 solves of the delta solver on the rotating sphere, the
+                           fused solve that keeps the pole sum on chip (one kernel, every
+                           output written once), else the pole-slot solve (rexi_tune picks
+                           per batch); > 0: the pole-slot solve with this many pole groups
+                           summed separately, then reduced in slot order (a deterministic
+                           tuning knob, any >= 1) */
   const double *alpha;  /* optional: P complex poles (re, im interleaved); NULL -> computed */
   const double *beta;   /* optional: P complex weights, used as given (no renormalisation) */
   int32_t npoles;       /* P when alpha/beta are given */

@@ -520,14 +520,22 @@ rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out) {
   return REXI_OK;
 }
 
+// Largest batch for which the untuned default is the fused solve.  Measured on GB300
+// (T63-T341, M = 128-256): with one or two states the fused solve is 1.04-2x faster than
+// the best slot layout with its reduction (a single state's slot layout needs hundreds of
+// partial sums); from four states on the slot kernel, with four warps per scheduler,
+// keeps the FP64 pipe busier (98 % against 82-86 %) and wins.  rexi_tune decides per batch.
+constexpr int kFusedDefaultMaxBatch = 2;
+
 // The fused solve's layout for steps of B states, or null when the slot-partial path
 // serves them: float-float solves, the Phi-only solver, the f-sphere, an explicit
 // pole_slots at plan creation, a slot layout chosen for this batch (rexi_tune,
-// rexi_set_pole_slots), or running sums too large for shared memory.
+// rexi_set_pole_slots) or, without a choice, a batch above kFusedDefaultMaxBatch, or
+// running sums too large for shared memory.
 const FusedLayout *fused_layout(Plan &pl, int B) {
   if (pl.ff || pl.prm.solver != REXI_SOLVER_DELTA || pl.prm.fsphere) return nullptr;
   auto us = pl.use_slots.find(B);
-  if (us != pl.use_slots.end() ? us->second : pl.slots_override > 0) return nullptr;
+  if (us != pl.use_slots.end() ? us->second : (pl.slots_override > 0 || B > kFusedDefaultMaxBatch)) return nullptr;
   auto it = pl.fused.find(B);
   if (it == pl.fused.end()) {
     FusedLayout F;

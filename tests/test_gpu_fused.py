@@ -59,10 +59,10 @@ def test_fused_step_matches_oracle_and_slot_solve(N, M, B, tau):
     assert np.all(fused[:, 1:, 0] == 0) and np.all(fused[:, :, : N + 1].imag == 0)
 
 
-def test_fused_is_the_default_and_drops_the_reduction():
+def test_fused_is_the_small_batch_default_and_drops_the_reduction():
     import torch
     from paper_1812_03431_gb300 import rexi
-    N, B = 31, 4
+    N, B = 31, 2
     plan = rexi.Plan(N, 48, 96, M=32, max_batch=B, layout="spectral")
     x = torch.from_numpy(inputs.random_spectral(N, B, 9)).cuda()
     plan.profile_enable(1)
@@ -71,10 +71,16 @@ def test_fused_is_the_default_and_drops_the_reduction():
     assert n == 1 and st["solve"] > 0 and st["reduce"] == 0.0
     assert plan.info()["pole_slots"] == 0
     plan.close()
-    # an explicit pole_slots at plan creation selects the slot solve
+    # an explicit pole_slots at plan creation selects the slot solve, as does a larger batch
     plan = rexi.Plan(N, 48, 96, M=32, max_batch=B, layout="spectral", pole_slots=8)
     plan.profile_enable(1)
     plan.step(x)
+    st, _ = plan.profile_read()
+    assert st["reduce"] > 0
+    plan.close()
+    plan = rexi.Plan(N, 48, 96, M=32, max_batch=4, layout="spectral")
+    plan.profile_enable(1)
+    plan.step(torch.from_numpy(inputs.random_spectral(N, 4, 9)).cuda())
     st, _ = plan.profile_read()
     assert st["reduce"] > 0
     plan.close()
