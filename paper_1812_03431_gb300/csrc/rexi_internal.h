@@ -97,6 +97,7 @@ struct SolveLayout {
 // has fewer than four states.  items: (system 2 m + p, first state), longest first.
 struct FusedLayout {
   int sb = 0, ws = 0, wp = 0, st = 0;
+  int nw = 8;       // warps per CTA: 8 (one CTA per SM) or 4 (two CTAs per SM)
   int nitems = 0;
   int2 *items_dev = nullptr;
   size_t smem = 0;  // dynamic shared memory per CTA (running sums and the exchange buffer)

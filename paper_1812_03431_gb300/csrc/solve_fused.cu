@@ -56,15 +56,14 @@ __device__ __forceinline__ double2 ldg2(const double2 *p) { return __ldg(p); }
 __device__ __forceinline__ void pf_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" : : "l"(p)); }
 __device__ __forceinline__ void pf_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" : : "l"(p)); }
 
-constexpr int kWarps = 8;              // two warps per SM sub-partition, one CTA per SM
-constexpr int kThreads = 32 * kWarps;
+constexpr int kWarpsPerSM = 8;         // two warps per SM sub-partition: one CTA of 8 or two of 4
 constexpr int kStreams = 4;            // delta, Phi, zeta at n + 1, zeta at n - 1
 
 struct FusedArgs {
   const double2 *fac;   // [F_NCOMP][nrows][P]
   const double2 *sin;   // [3][nspec][B]
   double2 *sout;        // [3][nspec][B]
-  double2 *ybuf;        // [gridDim.x * kWarps][lmax][32]
+  double2 *ybuf;        // [gridDim.x * NW][lmax][32]
   const int4 *sys;      // per (m, p): {m, n0, len, row0}
   const int2 *items;    // (system 2 m + p, first state of the tile), longest first
   unsigned *counter;
@@ -85,9 +84,9 @@ struct FwdRow {
 // per warp two exchange buffers of R rows x (32 + SB) values (a pad after every state's
 // PL lanes and a row stride of SB mod 8 put the R x SB (row, state) groups that a task
 // instruction reads on distinct banks).
-template <int SB>
-__global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
-  constexpr int PL = 32 / SB, R = 8 / SB, RS = 32 + SB;
+template <int SB, int NW>
+__global__ void __launch_bounds__(32 * NW, kWarpsPerSM / NW) solve_fused_kernel(FusedArgs a) {
+  constexpr int PL = 32 / SB, R = 8 / SB, RS = 32 + SB, kThreads = 32 * NW;
   extern __shared__ double2 smem[];
   __shared__ int s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -98,7 +97,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_fused_kernel(FusedArgs a) {
   const int64_t NS = a.nspec, NR = a.nrows, P = a.P;
   double2 *acc = smem;                                                           // [WP * ST][ACS]
   double2 *wbase = smem + (size_t)a.WP * ST * ACS + (size_t)warp * 2 * R * RS;  // [2][R][RS]
-  double2 *ybuf = a.ybuf + ((size_t)blockIdx.x * kWarps + warp) * (size_t)lmax * 32 + lane;
+  double2 *ybuf = a.ybuf + ((size_t)blockIdx.x * NW + warp) * (size_t)lmax * 32 + lane;
   // sweep role: lane = (state s_sw, pole pl); task role: lane = (row r, state t_s, stream t)
   const int s_sw = lane / PL, pl = lane - s_sw * PL;
   const int wslot = lane + s_sw;  // this lane's place in an exchange row
@@ -316,21 +315,32 @@ bool build_fused_layout(Plan &pl, int B, int tile, FusedLayout &F) {
   if (tile > 0)  // a requested tile: the largest power of two <= tile (and <= the default)
     while (st > 1 && st > tile) st /= 2;
   const int dev = pl.device;
-  int smem_max = 0;
+  int smem_max = 0, smem_sm = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  auto smem_of = [&](int nw, int sb, int wp, int t) {
+    return ((size_t)wp * t * (pl.lmax * kStreams + 1) + (size_t)nw * 2 * (8 / sb) * (32 + sb)) * sizeof(double2);
+  };
   for (; st >= 1; st /= 2) {
-    int sb, ws, wp;
-    if (st >= kWarps) { sb = st / kWarps; ws = kWarps; wp = 1; }
-    else { sb = 1; ws = st; wp = kWarps / st; }
-    const size_t smem =
-        ((size_t)wp * st * (pl.lmax * kStreams + 1) + (size_t)kWarps * 2 * (8 / sb) * (32 + sb)) * sizeof(double2);
-    if (smem + 1024 > (size_t)smem_max) continue;
-    F.sb = sb;
-    F.ws = ws;
-    F.wp = wp;
-    F.st = st;
-    F.smem = smem;
-    break;
+    // two CTAs of four warps when both fit on an SM (a tile's poles then need no split over
+    // warps down to four states), else one CTA of eight warps
+    for (int nw : {4, 8}) {
+      int sb, ws, wp;
+      if (st >= nw) { sb = st / nw; ws = nw; wp = 1; }
+      else { sb = 1; ws = st; wp = nw / st; }
+      if (sb > 4) continue;
+      const int per_sm = kWarpsPerSM / nw;
+      const size_t smem = smem_of(nw, sb, wp, st);
+      if (smem + 1024 > (size_t)smem_max || per_sm * (smem + 1024) > (size_t)smem_sm) continue;
+      F.sb = sb;
+      F.ws = ws;
+      F.wp = wp;
+      F.st = st;
+      F.nw = nw;
+      F.smem = smem;
+      break;
+    }
+    if (F.st) break;
   }
   if (F.st == 0) return false;
   // items (system, first state), longest system first; m ascending breaks ties
@@ -379,21 +389,17 @@ cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, con
   a.nrows = pl.nrows;
   cudaError_t e = cudaMemsetAsync(pl.counter, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  const int grid = pl.num_sms;
+  const int grid = pl.num_sms * (kWarpsPerSM / F.nw);
   const int smem = (int)F.smem;
-  switch (F.sb) {
-    case 4:
-      e = cudaFuncSetAttribute(solve_fused_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e == cudaSuccess) solve_fused_kernel<4><<<grid, kThreads, smem, st>>>(a);
-      break;
-    case 2:
-      e = cudaFuncSetAttribute(solve_fused_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e == cudaSuccess) solve_fused_kernel<2><<<grid, kThreads, smem, st>>>(a);
-      break;
-    default:
-      e = cudaFuncSetAttribute(solve_fused_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e == cudaSuccess) solve_fused_kernel<1><<<grid, kThreads, smem, st>>>(a);
-      break;
+  auto go = [&](auto kernel) {
+    cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (r == cudaSuccess) kernel<<<grid, 32 * F.nw, smem, st>>>(a);
+    return r;
+  };
+  if (F.nw == 4) {
+    e = F.sb == 4 ? go(solve_fused_kernel<4, 4>) : F.sb == 2 ? go(solve_fused_kernel<2, 4>) : go(solve_fused_kernel<1, 4>);
+  } else {
+    e = F.sb == 4 ? go(solve_fused_kernel<4, 8>) : F.sb == 2 ? go(solve_fused_kernel<2, 8>) : go(solve_fused_kernel<1, 8>);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
