@@ -255,7 +255,7 @@ rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *
  * against reduction work) in two shapes -- 0: the same number of groups for every
  * zonal order; 1: groups in proportion to the order's system length -- and, where it
  * applies (binary64 delta solver on the rotating sphere), shape 2: the fused solve
- * with the pole sum on chip and no slots, in CTA tiles of 32 down to 4 states.  Keeps
+ * with the pole sum on chip and no slots, in CTA tiles of 32 down to 2 states.  Keeps
  * the fastest for later steps with this batch and writes its slot count (for shape 2
  * its states per CTA tile) to *slots and its shape to *shape (either may be NULL).  Synchronous; uses the plan's workspaces, so no step
  * of this plan may be in flight. */

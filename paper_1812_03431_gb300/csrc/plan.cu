@@ -646,7 +646,7 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
       cudaFree(L.items_dev);
     }
   }
-  // the fused solve (no slot partials, no reduction) in its CTA tiles of 32 ... 1 states
+  // the fused solve (no slot partials, no reduction) in its CTA tiles of 32 ... 2 states
   // competes with the best slot layout
   float fused_ms = 1e30f;
   int best_tile = 0;
@@ -664,7 +664,7 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
       fused_ms = ms;
       best_tile = tile;
     }
-    if (tile <= 4) break;  // smaller tiles only re-read the factors more often
+    if (tile <= 2) break;  // smaller tiles only re-read the factors more often
   }
   if (best_tile > 0) set_fused_tile(pl, B, best_tile);
   cudaEventDestroy(e0);

@@ -323,12 +323,16 @@ bool build_fused_layout(Plan &pl, int B, int tile, FusedLayout &F) {
   };
   for (; st >= 1; st /= 2) {
     // two CTAs of four warps when both fit on an SM (a tile's poles then need no split over
-    // warps down to four states), else one CTA of eight warps
-    for (int nw : {4, 8}) {
+    // warps down to four states), else one CTA of eight warps; at most two states per warp
+    // unless nothing else fits (four states per warp leave the FP64 pipe half idle: 50 %
+    // measured at T170)
+    for (int nw : {4, 8, 4 + 0x100, 8 + 0x100}) {
+      const bool wide = nw & 0x100;
+      nw &= 0xff;
       int sb, ws, wp;
       if (st >= nw) { sb = st / nw; ws = nw; wp = 1; }
       else { sb = 1; ws = st; wp = nw / st; }
-      if (sb > 4) continue;
+      if (sb > 4 || (sb > 2 && !wide)) continue;
       const int per_sm = kWarpsPerSM / nw;
       const size_t smem = smem_of(nw, sb, wp, st);
       if (smem + 1024 > (size_t)smem_max || per_sm * (smem + 1024) > (size_t)smem_sm) continue;
