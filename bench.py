@@ -64,7 +64,8 @@ FF_OPS_PER_ROW = 36 * 12
 # batch 16, by (pole slots, layout shape); traffic per row is constant, so a launch of the
 # bench workload moves this times rows(T341) / rows(T170).  Re-captured after each change
 # of the solve kernel.
-SOLVE_TRAFFIC_T170 = {(32, 0): 12.64e9, (32, 1): 12.58e9, (0, 2): None}  # (0, 2): the fused solve
+# (slots, 2): the fused solve with that many states per CTA tile
+SOLVE_TRAFFIC_T170 = {(32, 0): 12.64e9, (32, 1): 12.58e9, (64, 0): 11.63e9, (2, 2): 1.59e9, (4, 2): 1.82e9}
 SOLVE_FF_TRAFFIC_T170 = {(32, 0): 11.64e9}  # the float-float kernel (solve_kernel<true>)
 
 
