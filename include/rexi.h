@@ -159,7 +159,8 @@ typedef struct {
 void rexi_params_default(rexi_params *p);
 
 /* sizeof(rexi_params) as compiled into the library, so that a binding can check that
- * its copy of the struct matches before passing one.  Host only. */
+ * its copy of the struct matches before passing one (no counterpart in the paper).  Host
+ * only. */
 size_t rexi_params_size(void);
 
 /* T-REXI coefficients on the host, no GPU needed (Sec. 4.1; Sec. 6.1 for the
@@ -246,7 +247,9 @@ rexi_status rexi_synthesize(rexi_plan *plan, const void *spec_dev, void *grid_de
 rexi_status rexi_solve_pole(rexi_plan *plan, int32_t k, const void *in_dev, void *out_dev,
                             int32_t batch, void *stream);
 
-/* Copy the plan's poles to host arrays of 2P doubles each; *P receives P. */
+/* Copy the plan's poles (Sec. 4.1's alpha_k, beta_k, ascending k; a plan over a share of
+ * the poles gives its own) to host arrays of 2P doubles each; *P receives P.  For tests of
+ * bit-exact pole indexing. */
 rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *beta, int32_t *P);
 
 /* Autotuner (no paper counterpart; a tuning knob of this implementation): times
@@ -271,7 +274,7 @@ rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots, int32_t *s
  * final pole sum changes.  Synchronous, like rexi_tune. */
 rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t shape, int32_t *used);
 
-/* Host-side description of a plan: writes up to 8 int64 values
+/* Host-side description of a plan (no counterpart in the paper): writes up to 8 int64 values
  * {N, nspec, P, nlat, nlon, max_batch, pole_slots, device bytes held}; pole_slots is
  * that of steps with max_batch states, 0 when they use the fused solve. */
 rexi_status rexi_plan_info(const rexi_plan *plan, int64_t *info, int32_t n);
@@ -294,7 +297,7 @@ rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *c
                              const int32_t *state_plan, int32_t nstates, void *stream);
 void rexi_ragged_destroy(rexi_ragged *rg);
 
-/* Optional per-stage timing: with max_calls > 0 the next max_calls calls of
+/* Optional per-stage timing (no counterpart in the paper): with max_calls > 0 the next max_calls calls of
  * rexi_step / rexi_step_adjoint record CUDA events on their stream around each
  * stage (0 FFT forward, 1 Legendre analysis, 2 banded solve + pole sum,
  * 3 slot reduction (zero with the fused solve, which has none), 4 Legendre
@@ -304,7 +307,7 @@ void rexi_ragged_destroy(rexi_ragged *rg);
 rexi_status rexi_profile_enable(rexi_plan *plan, int32_t max_calls);
 rexi_status rexi_profile_read(rexi_plan *plan, double *stage_ms, int32_t n, int32_t *calls);
 
-/* Synchronise the device and report whether any kernel of this plan gave up a
+/* No counterpart in the paper.  Synchronise the device and report whether any kernel of this plan gave up a
  * bounded device-side wait (tensor-core completion barriers) since the last
  * check: REXI_ETIMEOUT (and the flag is cleared) or REXI_OK.  Kernels that give
  * up skip their outputs, free their tensor memory and return.  For
@@ -322,11 +325,12 @@ rexi_status rexi_check_device(rexi_plan *plan);
  * bits. */
 rexi_status rexi_inject_device_error(rexi_plan *plan, int32_t bits);
 
-/* Free everything the plan holds; NULL-safe.  The caller synchronises streams
+/* Free everything the plan holds (no counterpart in the paper); NULL-safe.  The caller synchronises streams
  * that still use the plan first. */
 void rexi_destroy(rexi_plan *plan);
 
-/* Message of the last failed call on this host thread ("" if none). */
+/* Message of the last failed call on this host thread ("" if none); no counterpart in the
+ * paper. */
 const char *rexi_last_error(void);
 
 #ifdef __cplusplus
