@@ -186,10 +186,11 @@ def test_full_size_sampled_orders(torch, rexi):
     plan = rexi.Plan(N, 512, 1024, tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
     got = plan.step(torch.from_numpy(S).cuda()).cpu().numpy()
     ms = [0, 1, 170, 340, 341]
-    ref = ostep.rexi_step_spectral(S[:2], N, al, be, tau, C, ms=ms)
+    ref = ostep.rexi_step_spectral(S, N, al, be, tau, C, ms=ms)  # every state of the batch
     from oracle.sphere import idx
     sel = np.concatenate([np.arange(idx(m, m, N), idx(m, N, N) + 1) for m in ms])
-    assert fieldwise(got[:2][..., sel], ref[..., sel]) < TOL
+    for b in range(B):
+        assert fieldwise(got[b:b + 1][..., sel], ref[b:b + 1][..., sel]) < TOL, b
 
 
 @pytest.fixture(scope="module")
@@ -216,6 +217,30 @@ def test_full_size_grid_step_bench_launch(torch, rexi, full_size_case, precision
     got = plan.step(torch.from_numpy(c["x"]).cuda()).cpu().numpy()
     plan.close()
     assert fieldwise(got[:1], c["ref"], axis_f=-3) < tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("mixed", 1e-5)])
+def test_full_size_every_state_of_the_bench_launch(torch, rexi, precision, tol):
+    """All 16 states of the bench's launch (T341, 1024x512, K=256, tau=1200 s, tuned layout,
+    seeded n^-3 spectra): the oracle analyses the GPU's grid output and, on sampled zonal
+    orders, compares it with its own spectral step of every state (the oracle's banded
+    solves take the 16 states as right-hand sides of one solve per pole and order)."""
+    from oracle.sphere import idx
+    N, nlat, nlon, M, B, tau = 341, 512, 1024, 256, 16, 1200.0
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    S = spectral_state(N, B, 1005)
+    gs = ostep.GridStep(N, nlat, nlon, al, be, tau, C)
+    x = gs.synthesise(S)
+    plan = rexi.Plan(N, nlat, nlon, tau=tau, max_batch=B, alpha=al, beta=be, precision=precision)
+    plan.tune(B)
+    y = plan.step(torch.from_numpy(x).cuda()).cpu().numpy()
+    plan.close()
+    got = gs.analyse(y)  # exact for the band-limited result of a grid step
+    ms = [0, 1, 2, 85, 170, 255, 340, 341]
+    ref = ostep.rexi_step_spectral(S, N, al, be, tau, C, ms=ms)
+    sel = np.concatenate([np.arange(idx(m, m, N), idx(m, N, N) + 1) for m in ms])
+    for b in range(B):
+        assert fieldwise(got[b:b + 1][..., sel], ref[b:b + 1][..., sel]) < tol, b
 
 
 def test_tune_cache_and_set_pole_slots(torch, rexi, tmp_path):
