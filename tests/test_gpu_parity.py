@@ -239,8 +239,21 @@ def test_full_size_every_state_of_the_bench_launch(torch, rexi, precision, tol):
     ms = [0, 1, 2, 85, 170, 255, 340, 341]
     ref = ostep.rexi_step_spectral(S, N, al, be, tau, C, ms=ms)
     sel = np.concatenate([np.arange(idx(m, m, N), idx(m, N, N) + 1) for m in ms])
+    if precision == "fp64":
+        for b in range(B):
+            assert fieldwise(got[b:b + 1][..., sel], ref[b:b + 1][..., sel]) < tol, b
+    # in the norm the error is stated in (h' and the wind on the grid): the sampled orders
+    # of the difference and of the reference, synthesised (vorticity and divergence
+    # coefficients weigh small scales by n, so FP32 rounding of the winds shows more there)
+    E = np.zeros_like(ref)
+    R = np.zeros_like(ref)
+    E[..., sel] = got[..., sel] - ref[..., sel]
+    R[..., sel] = ref[..., sel]
+    e, r = gs.synthesise(E), gs.synthesise(R)
     for b in range(B):
-        assert fieldwise(got[b:b + 1][..., sel], ref[b:b + 1][..., sel]) < tol, b
+        eh = np.linalg.norm(e[b, 0]) / np.linalg.norm(r[b, 0])
+        ew = np.linalg.norm(e[b, 1:]) / np.linalg.norm(r[b, 1:])
+        assert eh < tol and ew < tol, (b, eh, ew)
 
 
 def test_tune_cache_and_set_pole_slots(torch, rexi, tmp_path):
