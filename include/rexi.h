@@ -258,9 +258,10 @@ rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *
  * against reduction work) in two shapes -- 0: the same number of groups for every
  * zonal order; 1: groups in proportion to the order's system length -- and, where it
  * applies (binary64 delta solver on the rotating sphere), shape 2: the fused solve
- * with the pole sum on chip and no slots, in CTA tiles of 32 down to 2 states.  Keeps
- * the fastest for later steps with this batch and writes its slot count (for shape 2
- * its states per CTA tile) to *slots and its shape to *shape (either may be NULL).  Synchronous; uses the plan's workspaces, so no step
+ * with the pole sum on chip and no slots, in CTA tiles of 32 down to 2 states, and
+ * shape 3: its lean form (see rexi_set_pole_slots).  Keeps
+ * the fastest for later steps with this batch and writes its slot count (for shapes 2
+ * and 3 its states per CTA tile) to *slots and its shape to *shape (either may be NULL).  Synchronous; uses the plan's workspaces, so no step
  * of this plan may be in flight. */
 rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots, int32_t *shape);
 
@@ -269,8 +270,10 @@ rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots, int32_t *s
  * the lanes a warp gives each state and capped by the partial-sum buffer) and shape 0
  * or 1 as for rexi_tune, or shape 2 for the fused solve with `slots` states per CTA
  * tile (0: the default tile, the smallest power of two >= batch up to 32; a request is
- * rounded down to a power of two), REXI_EINVAL where that does not apply; the slot
- * count used (for shape 2 the tile) is written to *used (may be NULL).  Results are deterministic for any layout; only the order of the
+ * rounded down to a power of two), or shape 3 for its lean form (three or four CTAs of
+ * four warps per SM, fewer registers, the next rows prefetched into the caches),
+ * REXI_EINVAL where that does not apply; the slot count used (for shapes 2 and 3 the
+ * tile) is written to *used (may be NULL).  Results are deterministic for any layout; only the order of the
  * final pole sum changes.  Synchronous, like rexi_tune. */
 rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t shape, int32_t *used);
 

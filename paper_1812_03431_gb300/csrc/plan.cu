@@ -540,21 +540,25 @@ const FusedLayout *fused_layout(Plan &pl, int B) {
   if (it == pl.fused.end()) {
     FusedLayout F;
     auto ft = pl.fused_tile.find(B);
-    if (!build_fused_layout(pl, B, ft != pl.fused_tile.end() ? ft->second : 0, F)) F = FusedLayout{};
+    auto fl = pl.fused_lean.find(B);
+    if (!build_fused_layout(pl, B, ft != pl.fused_tile.end() ? ft->second : 0,
+                            fl != pl.fused_lean.end() && fl->second, F))
+      F = FusedLayout{};
     it = pl.fused.emplace(B, F).first;  // st == 0: not available
   }
   return it->second.st > 0 ? &it->second : nullptr;
 }
 
-// the fused layout for batch B with a requested CTA tile (0: the default), replacing any
-// earlier one
-const FusedLayout *set_fused_tile(Plan &pl, int B, int tile) {
+// the fused layout for batch B with a requested CTA tile (0: the default) and form,
+// replacing any earlier one
+const FusedLayout *set_fused_tile(Plan &pl, int B, int tile, bool lean = false) {
   auto it = pl.fused.find(B);
   if (it != pl.fused.end()) {
     if (it->second.items_dev) cudaFree(it->second.items_dev);
     pl.fused.erase(it);
   }
   pl.fused_tile[B] = tile;
+  pl.fused_lean[B] = lean;
   return fused_layout(pl, B);
 }
 
@@ -562,9 +566,9 @@ const FusedLayout *set_fused_tile(Plan &pl, int B, int tile) {
 // earlier one for that batch.  Shape 2 selects the fused solve instead (REXI_EINVAL where
 // it does not apply).
 rexi_status set_layout(Plan &pl, int B, int slots, int shape, int *used) {
-  if (shape == 2) {
+  if (shape == 2 || shape == 3) {
     pl.use_slots[B] = false;
-    if (!set_fused_tile(pl, B, slots)) {
+    if (!set_fused_tile(pl, B, slots, shape == 3)) {
       pl.use_slots[B] = true;
       set_error("rexi_set_pole_slots: the fused solve (shape 2) needs binary64 solves of the delta solver on "
                 "the rotating sphere, with running sums that fit in shared memory");
@@ -651,22 +655,26 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
   float fused_ms = 1e30f;
   int best_tile = 0;
   pl.use_slots[B] = false;
+  bool best_lean = false;
   for (int tile = 32; tile >= 1; tile /= 2) {
-    const FusedLayout *F = set_fused_tile(pl, B, tile);
-    if (!F || F->st != tile) continue;  // the default is smaller, or it does not fit
-    launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);  // warm-up
-    cudaEventRecord(e0, st);
-    for (int rep = 0; rep < 2; ++rep) launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);
-    cudaEventRecord(e1, st);
-    float ms = 1e30f;
-    if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < fused_ms) {
-      fused_ms = ms;
-      best_tile = tile;
+    for (int lean = 0; lean < 2; ++lean) {
+      const FusedLayout *F = set_fused_tile(pl, B, tile, lean != 0);
+      if (!F || F->st != tile) continue;  // the default is smaller, or it does not fit
+      launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);  // warm-up
+      cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 2; ++rep) launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);
+      cudaEventRecord(e1, st);
+      float ms = 1e30f;
+      if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < fused_ms) {
+        fused_ms = ms;
+        best_tile = tile;
+        best_lean = lean != 0;
+      }
     }
     if (tile <= 2) break;  // smaller tiles only re-read the factors more often
   }
-  if (best_tile > 0) set_fused_tile(pl, B, best_tile);
+  if (best_tile > 0) set_fused_tile(pl, B, best_tile, best_lean);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   auto it = pl.layouts.find(B);
@@ -678,7 +686,7 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
   const bool fused_wins = fused_ms <= best;
   pl.use_slots[B] = !fused_wins;
   if (slots_out) *slots_out = fused_wins ? best_tile : bestL.slots;
-  if (shape_out) *shape_out = fused_wins ? 2 : bestL.shape;
+  if (shape_out) *shape_out = fused_wins ? (best_lean ? 3 : 2) : bestL.shape;
   return REXI_OK;
 }
 

@@ -97,7 +97,8 @@ struct SolveLayout {
 // has fewer than four states.  items: (system 2 m + p, first state), longest first.
 struct FusedLayout {
   int sb = 0, ws = 0, wp = 0, st = 0;
-  int nw = 8;       // warps per CTA: 8 (one CTA per SM) or 4 (two CTAs per SM)
+  int nw = 8;       // warps per CTA: 8 (one CTA per SM) or 4 (two CTAs per SM, or the lean form)
+  int per_sm = 1;   // CTAs per SM (lean form: 3 or 4)
   int nitems = 0;
   int2 *items_dev = nullptr;
   size_t smem = 0;  // dynamic shared memory per CTA (running sums and the exchange buffer)
@@ -220,6 +221,7 @@ struct Plan {
   std::map<int, FusedLayout> fused;
   std::map<int, bool> use_slots;
   std::map<int, int> fused_tile;  // requested states per CTA tile (0: the default)
+  std::map<int, bool> fused_lean; // the lean form (three or four CTAs of four warps per SM)
 
   // optional per-stage timing with CUDA events on the launching stream
   bool prof = false;
@@ -269,7 +271,7 @@ SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double
                     int pole_begin, int pole_end);
 // fused solve: eligible plans (binary64 delta solver on the rotating sphere) whose running
 // sums fit in shared memory; sin -> sout ([3][nspec][B]) with no partial sums and no reduction
-bool build_fused_layout(Plan &pl, int B, int tile, FusedLayout &F);
+bool build_fused_layout(Plan &pl, int B, int tile, bool lean, FusedLayout &F);
 cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, const double2 *sin, double2 *sout,
                                int B, cudaStream_t st);
 cudaError_t launch_solve_ragged(const SolveView *views_dev, const WorkItem *items, int nitems, double2 *ybuf,

@@ -84,9 +84,17 @@ struct FwdRow {
 // per warp two exchange buffers of R rows x (32 + SB) values (a pad after every state's
 // PL lanes and a row stride of SB mod 8 put the R x SB (row, state) groups that a task
 // instruction reads on distinct banks).
-template <int SB, int NW>
-__global__ void __launch_bounds__(32 * NW, kWarpsPerSM / NW) solve_fused_kernel(FusedArgs a) {
+//
+// MINB CTAs per SM.  MINB = kWarpsPerSM / NW: the running sums and two exchange buffers per
+// warp, and the next rows' factors, states and sweep values prefetched into registers
+// (up to 222 registers).  MINB > 2 (four warps per CTA, three or four CTAs per SM): the
+// lean form for 12 or 16 warps per SM -- registers capped at 170 or 128, one exchange
+// buffer per warp, and the next rows brought into the caches instead of registers.
+template <int SB, int NW, int MINB = kWarpsPerSM / NW>
+__global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a) {
   constexpr int PL = 32 / SB, R = 8 / SB, RS = 32 + SB, kThreads = 32 * NW;
+  constexpr bool kLean = MINB * NW > kWarpsPerSM;
+  constexpr int kBufs = kLean ? 1 : 2;  // exchange buffers per warp
   extern __shared__ double2 smem[];
   __shared__ int s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -96,7 +104,7 @@ __global__ void __launch_bounds__(32 * NW, kWarpsPerSM / NW) solve_fused_kernel(
   const int ACS = lmax * kStreams + 1;                // running-sum plane stride
   const int64_t NS = a.nspec, NR = a.nrows, P = a.P;
   double2 *acc = smem;                                                           // [WP * ST][ACS]
-  double2 *wbase = smem + (size_t)a.WP * ST * ACS + (size_t)warp * 2 * R * RS;  // [2][R][RS]
+  double2 *wbase = smem + (size_t)a.WP * ST * ACS + (size_t)warp * kBufs * R * RS;  // [kBufs][R][RS]
   double2 *ybuf = a.ybuf + ((size_t)blockIdx.x * NW + warp) * (size_t)lmax * 32 + lane;
   // sweep role: lane = (state s_sw, pole pl); task role: lane = (row r, state t_s, stream t)
   const int s_sw = lane / PL, pl = lane - s_sw * PL;
@@ -175,7 +183,27 @@ __global__ void __launch_bounds__(32 * NW, kWarpsPerSM / NW) solve_fused_kernel(
           yprev = y;
           zprev = r.zn;
         };
-        {
+        if constexpr (kLean) {
+          // each row's values two rows ahead into L1 (no registers held), then loaded
+          auto pf_row = [&](int i) {
+            const int64_t o = (int64_t)i * P;
+            const int64_t ix = base_idx + n0 + 2 * i;
+            pf_l1(fL + o);
+            pf_l1(fG + o);
+            pf_l1(fE + o);
+            pf_l1(fF + o);
+            pf_l1(sDel + ix * B);
+            pf_l1(sPhi + ix * B);
+            pf_l1(sZeta + (ix + 1) * B);  // the state array's next field follows: in bounds
+          };
+          if (len > 1) pf_row(1);
+          for (int i = 0; i < len; ++i) {
+            if (i + 2 < len) pf_row(i + 2);
+            FwdRow r;
+            load_fwd(i, r);
+            fwd(i, r);
+          }
+        } else {
           FwdRow A, Bn;
           load_fwd(0, A);
           int i = 0;
@@ -228,16 +256,39 @@ __global__ void __launch_bounds__(32 * NW, kWarpsPerSM / NW) solve_fused_kernel(
               if (q < npa) pf_l1(Wn + q);  // poles of this pass only: every address inside the factors
           }
         };
-        load_round(0);
-        rec_round(0, wbase);
-        if (nr > 1) load_round(1);
-        __syncwarp();
-        for (int rr = 0; rr < nr; ++rr) {
-          double2 *wcur = wbase + (rr & 1) * R * RS, *wnxt = wbase + ((rr + 1) & 1) * R * RS;
-          if (rr + 1 < nr) rec_round(rr + 1, wnxt);
-          if (rr + 2 < nr) load_round(rr + 2);
-          task_round(rr, wcur);
+        if constexpr (kLean) {
+          // one exchange buffer: each round's recurrence, then its sums; the next round's
+          // sweep values and factors two rounds ahead into L1
+          auto pf_round = [&](int rr) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+              const int i = max(len - 1 - rr * R - j, 0);
+              pf_l1(ybuf + (size_t)i * 32);
+              pf_l1(fC + (int64_t)i * P);
+            }
+          };
+          pf_round(0);
+          if (nr > 1) pf_round(1);
+          for (int rr = 0; rr < nr; ++rr) {
+            if (rr + 2 < nr) pf_round(rr + 2);
+            load_round(rr);
+            rec_round(rr, wbase);
+            __syncwarp();
+            task_round(rr, wbase);
+            __syncwarp();
+          }
+        } else {
+          load_round(0);
+          rec_round(0, wbase);
+          if (nr > 1) load_round(1);
           __syncwarp();
+          for (int rr = 0; rr < nr; ++rr) {
+            double2 *wcur = wbase + (rr & 1) * R * RS, *wnxt = wbase + ((rr + 1) & 1) * R * RS;
+            if (rr + 1 < nr) rec_round(rr + 1, wnxt);
+            if (rr + 2 < nr) load_round(rr + 2);
+            task_round(rr, wcur);
+            __syncwarp();
+          }
         }
       }
     }
@@ -308,7 +359,7 @@ __global__ void __launch_bounds__(32 * NW, kWarpsPerSM / NW) solve_fused_kernel(
 // more, shorter work items (better balance over the SMs) at the cost of reading each
 // factor once per tile.  Returns false when the running sums of a tile do
 // not fit in shared memory (the slot-partial path then serves the plan).
-bool build_fused_layout(Plan &pl, int B, int tile, FusedLayout &F) {
+bool build_fused_layout(Plan &pl, int B, int tile, bool lean, FusedLayout &F) {
   F = FusedLayout{};
   int st = 1;
   while (st < B && st < 32) st *= 2;
@@ -318,10 +369,29 @@ bool build_fused_layout(Plan &pl, int B, int tile, FusedLayout &F) {
   int smem_max = 0, smem_sm = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  auto smem_of = [&](int nw, int sb, int wp, int t) {
-    return ((size_t)wp * t * (pl.lmax * kStreams + 1) + (size_t)nw * 2 * (8 / sb) * (32 + sb)) * sizeof(double2);
+  auto smem_of = [&](int nw, int sb, int wp, int t, int bufs) {
+    return ((size_t)wp * t * (pl.lmax * kStreams + 1) + (size_t)nw * bufs * (8 / sb) * (32 + sb)) * sizeof(double2);
   };
   for (; st >= 1; st /= 2) {
+    if (lean) {
+      // four-warp CTAs, one exchange buffer per warp, as many CTAs per SM (4 or 3) as fit
+      int sb, ws, wp;
+      if (st >= 4) { sb = st / 4; ws = 4; wp = 1; }
+      else { sb = 1; ws = st; wp = 4 / st; }
+      if (sb > 2) continue;
+      const size_t smem = smem_of(4, sb, wp, st, 1);
+      if (smem + 1024 > (size_t)smem_max) continue;
+      const int per_sm = std::min<int>(4, (int)(smem_sm / (smem + 1024)));
+      if (per_sm < 3) continue;
+      F.sb = sb;
+      F.ws = ws;
+      F.wp = wp;
+      F.st = st;
+      F.nw = 4;
+      F.per_sm = per_sm;
+      F.smem = smem;
+      break;
+    }
     // two CTAs of four warps when both fit on an SM (a tile's poles then need no split over
     // warps down to four states), else one CTA of eight warps; at most two states per warp
     // unless nothing else fits (four states per warp leave the FP64 pipe half idle: 50 %
@@ -334,13 +404,14 @@ bool build_fused_layout(Plan &pl, int B, int tile, FusedLayout &F) {
       else { sb = 1; ws = st; wp = nw / st; }
       if (sb > 4 || (sb > 2 && !wide)) continue;
       const int per_sm = kWarpsPerSM / nw;
-      const size_t smem = smem_of(nw, sb, wp, st);
+      const size_t smem = smem_of(nw, sb, wp, st, 2);
       if (smem + 1024 > (size_t)smem_max || per_sm * (smem + 1024) > (size_t)smem_sm) continue;
       F.sb = sb;
       F.ws = ws;
       F.wp = wp;
       F.st = st;
       F.nw = nw;
+      F.per_sm = per_sm;
       F.smem = smem;
       break;
     }
@@ -393,14 +464,18 @@ cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, con
   a.nrows = pl.nrows;
   cudaError_t e = cudaMemsetAsync(pl.counter, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  const int grid = pl.num_sms * (kWarpsPerSM / F.nw);
+  const int grid = pl.num_sms * F.per_sm;
   const int smem = (int)F.smem;
   auto go = [&](auto kernel) {
     cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (r == cudaSuccess) kernel<<<grid, 32 * F.nw, smem, st>>>(a);
     return r;
   };
-  if (F.nw == 4) {
+  if (F.per_sm == 4) {
+    e = F.sb == 2 ? go(solve_fused_kernel<2, 4, 4>) : go(solve_fused_kernel<1, 4, 4>);
+  } else if (F.per_sm == 3) {
+    e = F.sb == 2 ? go(solve_fused_kernel<2, 4, 3>) : go(solve_fused_kernel<1, 4, 3>);
+  } else if (F.nw == 4) {
     e = F.sb == 4 ? go(solve_fused_kernel<4, 4>) : F.sb == 2 ? go(solve_fused_kernel<2, 4>) : go(solve_fused_kernel<1, 4>);
   } else {
     e = F.sb == 4 ? go(solve_fused_kernel<4, 8>) : F.sb == 2 ? go(solve_fused_kernel<2, 8>) : go(solve_fused_kernel<1, 8>);

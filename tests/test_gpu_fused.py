@@ -50,6 +50,11 @@ def test_fused_step_matches_oracle_and_slot_solve(N, M, B, tau):
         if tile // 2 >= 8:
             np.testing.assert_array_equal(half, fused)
         assert fieldwise(half, fused) < 1e-13
+    # the lean form (three or four CTAs of four warps per SM, prefetching into the caches)
+    assert plan.set_pole_slots(B, tile, 3) == tile
+    lean = plan.step(x).cpu().numpy()
+    np.testing.assert_array_equal(plan.step(x).cpu().numpy(), lean)
+    assert fieldwise(lean, fused) < 1e-13
     plan.set_pole_slots(B, 8, 0)  # the pole-slot solve and its reduction
     slot = plan.step(x).cpu().numpy()
     plan.close()
