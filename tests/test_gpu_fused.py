@@ -51,7 +51,8 @@ def test_fused_step_matches_oracle_and_slot_solve(N, M, B, tau):
             np.testing.assert_array_equal(half, fused)
         assert fieldwise(half, fused) < 1e-13
     # the lean form (three or four CTAs of four warps per SM, prefetching into the caches)
-    assert plan.set_pole_slots(B, tile, 3) == tile
+    lt = plan.set_pole_slots(B, tile, 3)  # at most two states per warp: tiles of 8 or less
+    assert 1 <= lt <= min(tile, 8)
     lean = plan.step(x).cpu().numpy()
     np.testing.assert_array_equal(plan.step(x).cpu().numpy(), lean)
     assert fieldwise(lean, fused) < 1e-13
