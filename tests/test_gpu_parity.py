@@ -208,8 +208,8 @@ def full_size_case():
                                                 ("mixed", "fp32x2", 1e-5)])
 def test_full_size_grid_step_bench_launch(torch, rexi, full_size_case, precision, arith, tol):
     """The bench's launches: T341, 1024x512, K=256, tau=1200 s, batch 16, grid layout, in each
-    of its forms (mixed transforms with float-float solves is the chosen one).  The oracle
-    computes the whole grid-layout step for state 0 of the batch."""
+    of its forms (mixed transforms with binary64 solves is the chosen one; float-float
+    solves the extension).  The oracle computes the whole grid-layout step for state 0."""
     c = full_size_case
     plan = rexi.Plan(c["N"], c["nlat"], c["nlon"], tau=c["tau"], max_batch=c["B"], alpha=c["al"], beta=c["be"],
                      precision=precision, solve_arith=arith)
