@@ -101,17 +101,42 @@ def test_fused_not_offered_where_it_does_not_apply():
         plan.close()
 
 
-def test_fused_adjoint_matches_oracle():
+@pytest.mark.parametrize("shape", [2, 3])
+def test_fused_adjoint_matches_oracle(shape):
     import torch
     from paper_1812_03431_gb300 import rexi
     N, M, B, tau = 27, 32, 3, 3600.0
     al, be, _ = rc.rexi_coefficients(M, 0.2)
     G = inputs.random_spectral(N, B, 77)
     plan = rexi.Plan(N, *grid(N), tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
+    plan.set_pole_slots(B, 0, shape)  # the fused solve (shape 3: its lean form)
+    plan.profile_enable(1)
     got = plan.step_adjoint(torch.from_numpy(G).cuda()).cpu().numpy()
+    st, _ = plan.profile_read()
+    assert st["reduce"] == 0.0  # no slot reduction ran
     plan.close()
     ref = ostep.rexi_step_spectral(G, N, al, be, tau, C, adjoint=True)
     assert fieldwise(got, ref) < TOL
+
+
+@pytest.mark.parametrize("shape", [2, 3])
+def test_fused_grid_mixed_step_matches_oracle(shape):
+    # the chosen form's arithmetic (tcgen05 Legendre transforms, binary64 solves) with the
+    # fused solve, against the oracle's grid step
+    import torch
+    from paper_1812_03431_gb300 import rexi
+    N, nlat, nlon, M, B, tau = 63, 96, 192, 64, 5, 3600.0
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    gs = ostep.GridStep(N, nlat, nlon, al, be, tau, C)
+    x = gs.synthesise(inputs.random_spectral(N, B, 63))
+    plan = rexi.Plan(N, nlat, nlon, tau=tau, max_batch=B, alpha=al, beta=be, precision="mixed")
+    plan.set_pole_slots(B, 0, shape)
+    got = plan.step(torch.from_numpy(x).cuda()).cpu().numpy()
+    plan.check_device()
+    plan.close()
+    ref = gs(x)
+    for b in range(B):
+        assert relerr(got[b, 0], ref[b, 0]) < 1e-5 and relerr(got[b, 1:], ref[b, 1:]) < 1e-5
 
 
 def test_fused_large_truncation_smaller_tiles():

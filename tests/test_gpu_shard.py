@@ -15,12 +15,14 @@ def relerr(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("layout,precision,world,tol", [("spectral", "fp64", 2, 1e-13), ("spectral", "fp64", 3, 1e-13),
-                                                        ("grid", "fp64", 2, 1e-12), ("grid", "mixed", 4, 1e-5)])
-def test_shards_add_up_to_the_full_step(layout, precision, world, tol):
+@pytest.mark.parametrize("layout,precision,world,tol,B", [("spectral", "fp64", 2, 1e-13, 3),
+                                                          ("spectral", "fp64", 3, 1e-13, 3),
+                                                          ("spectral", "fp64", 2, 1e-13, 1),  # fused solve
+                                                          ("grid", "fp64", 2, 1e-12, 3), ("grid", "mixed", 4, 1e-5, 3)])
+def test_shards_add_up_to_the_full_step(layout, precision, world, tol, B):
     import torch
     from paper_1812_03431_gb300 import rexi
-    N, M, B, tau = 31, 32, 3, 3600.0
+    N, M, tau = 31, 32, 3600.0
     al, be, _ = rc.rexi_coefficients(M, 0.2)
     P = al.size
     kw = dict(tau=tau, max_batch=B, layout=layout, precision=precision, alpha=al, beta=be)
