@@ -418,6 +418,25 @@ bool build_fused_layout(Plan &pl, int B, int tile, bool lean, FusedLayout &F) {
     if (F.st) break;
   }
   if (F.st == 0) return false;
+  // the kernel's shared-memory limit, set here once (not per launch, so that steps can be
+  // captured in a CUDA graph): the device's opt-in maximum, which covers every layout
+  const int smem_opt = smem_max;
+  auto allow = [&](auto kernel) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opt);
+  };
+  cudaError_t ea;
+  if (F.per_sm == 4) ea = F.sb == 2 ? allow(solve_fused_kernel<2, 4, 4>) : allow(solve_fused_kernel<1, 4, 4>);
+  else if (F.per_sm == 3) ea = F.sb == 2 ? allow(solve_fused_kernel<2, 4, 3>) : allow(solve_fused_kernel<1, 4, 3>);
+  else if (F.nw == 4)
+    ea = F.sb == 4 ? allow(solve_fused_kernel<4, 4>) : F.sb == 2 ? allow(solve_fused_kernel<2, 4>)
+                                                      : allow(solve_fused_kernel<1, 4>);
+  else
+    ea = F.sb == 4 ? allow(solve_fused_kernel<4, 8>) : F.sb == 2 ? allow(solve_fused_kernel<2, 8>)
+                                                      : allow(solve_fused_kernel<1, 8>);
+  if (ea != cudaSuccess) {
+    F = FusedLayout{};
+    return false;
+  }
   // items (system, first state), longest system first; m ascending breaks ties
   struct Keyed { int2 it; int len; };
   std::vector<Keyed> keyed;
@@ -466,10 +485,9 @@ cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, con
   if (e != cudaSuccess) return e;
   const int grid = pl.num_sms * F.per_sm;
   const int smem = (int)F.smem;
-  auto go = [&](auto kernel) {
-    cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (r == cudaSuccess) kernel<<<grid, 32 * F.nw, smem, st>>>(a);
-    return r;
+  auto go = [&](auto kernel) {  // the shared-memory limit was raised when the layout was built
+    kernel<<<grid, 32 * F.nw, smem, st>>>(a);
+    return cudaSuccess;
   };
   if (F.per_sm == 4) {
     e = F.sb == 2 ? go(solve_fused_kernel<2, 4, 4>) : go(solve_fused_kernel<1, 4, 4>);
