@@ -419,8 +419,9 @@ bool build_fused_layout(Plan &pl, int B, int tile, bool lean, FusedLayout &F) {
   }
   if (F.st == 0) return false;
   // the kernel's shared-memory limit, set here once (not per launch, so that steps can be
-  // captured in a CUDA graph): the device's opt-in maximum, which covers every layout
-  const int smem_opt = smem_max;
+  // captured in a CUDA graph): the device's opt-in maximum less the 1 KiB every layout
+  // leaves for the static shared memory, which covers every layout
+  const int smem_opt = smem_max - 1024;
   auto allow = [&](auto kernel) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opt);
   };
