@@ -93,6 +93,15 @@ def measured_peaks():
         return 6800.0, 1900.0, "fallback"
 
 
+def solve_layout(r):
+    """The tuned solve layout of a form's record: pole slots and shape, or for the fused
+    solve (shapes 2 and 3) its CTA tile and the CTAs that split each tile's poles."""
+    if r["shape"] in (2, 3):
+        return {"fused": "lean" if r["shape"] == 3 else "register", "tile": r["slots"] % 256,
+                "pole_groups": r["slots"] // 256, "layout_shape": r["shape"]}
+    return {"pole_slots": r["slots"], "layout_shape": r["shape"]}
+
+
 def kernel_rooflines(form, stages, slots, sm_mhz, solve_arith="fp64", fp64_peak=None):
     """Every stage of the grid step against its own bound: algorithmic bytes (HBM-bound
     stages) or flops (ALU-bound stages) per launch / its live CUDA-event time.
@@ -557,9 +566,12 @@ def main():
         peak_source = ("measured: rexi_measure_fp64_fma, best of 5 per shape (FP64 FMA chains)" if fp64_tf else
                        "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz")
     achieved = amount / (solve_ms * 1e-3) / 1e12
-    tkey = min(traffic_t170, key=lambda k: (k[1] != r["shape"], abs(k[0] - r["slots"])))
+    fused = r["shape"] in (2, 3)
+    # the fused solve's slot count packs its CTA tile and pole groups (tile + 256 x groups)
+    tile_or_slots = r["slots"] % 256 if fused else r["slots"]
+    tkey = min(traffic_t170, key=lambda k: (k[1] != min(r["shape"], 2), abs(k[0] - tile_or_slots)))
     traffic = traffic_t170[tkey] * rows_of(W["N"]) / rows_of(170) if traffic_t170[tkey] else None
-    if r["shape"] == 2:
+    if fused:
         kname = "solve_fused_kernel (FP64 banded solves, beta-weighted pole sum on chip)"
     dtypes = {"mixed": "f64 solves + pole sum; 3xtf32 legendre; f32 fft", "fp64": "f64",
               "ff_solve": "f64 i/o; float-float (2 x f32) solves + pole sum; 3xtf32 legendre; f32 fft"}
@@ -579,7 +591,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
         "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": dtypes[chosen],
         "data": "synthetic", "config": cfg,
-        "form": chosen, "solve_layout": {"pole_slots": r["slots"], "layout_shape": r["shape"]},
+        "form": chosen, "solve_layout": solve_layout(r),
         "roofline": {"bound": "alu", "kernel": kname,
                      "achieved": achieved, "peak": peak, "unit": roof_unit, "frac": achieved / peak,
                      "traffic": traffic,
@@ -603,7 +615,7 @@ def main():
     for name, _, _ in forms[1:]:
         f = results[name]
         line[name + "_form"] = {"value": world * 1e3 / f["ms"], "ms_per_step": f["ms"], "stage_ms": f["stages"],
-                                "dtype": dtypes[name], "pole_slots": f["slots"], "layout_shape": f["shape"],
+                                "dtype": dtypes[name], "solve_layout": solve_layout(f),
                                 "clocks": f["clocks"],
                                 "kernels": kernel_rooflines(f["precision"], f["stages"], f["slots"], sm_mhz,
                                                             f["solve_arith"], fp64_tf)}

@@ -118,7 +118,7 @@ typedef struct {
   int32_t strict_range; /* 1: plan creation fails with REXI_ERANGE when tau * max|omega|
                            exceeds h (M - 10), the range where Re of the REXI symbol
                            matches cos to the fit level */
-  int32_t pole_slots;   /* 0: the default solve -- for batches of one or two states with
+  int32_t pole_slots;   /* 0: the default solve -- for batches of up to four states with
                            binary64 solves of the delta solver on the rotating sphere, the
                            fused solve that keeps the pole sum on chip (one kernel, every
                            output written once), else the pole-slot solve (rexi_tune picks
@@ -258,23 +258,29 @@ rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *
  * against reduction work) in two shapes -- 0: the same number of groups for every
  * zonal order; 1: groups in proportion to the order's system length -- and, where it
  * applies (binary64 delta solver on the rotating sphere), shape 2: the fused solve
- * with the pole sum on chip and no slots, in CTA tiles of 32 down to 2 states, and
- * shape 3: its lean form (see rexi_set_pole_slots).  Keeps
+ * with the pole sum on chip and no slots, in CTA tiles of 32 down to 2 states (down to
+ * 1 for batches of 1 and 2) and, for batches up to 8, with each tile's poles split over
+ * 1, 2, 3, 4, 6 or 8 CTAs, and shape 3: its lean form (see rexi_set_pole_slots).  Keeps
  * the fastest for later steps with this batch and writes its slot count (for shapes 2
- * and 3 its states per CTA tile) to *slots and its shape to *shape (either may be NULL).  Synchronous; uses the plan's workspaces, so no step
- * of this plan may be in flight. */
+ * and 3: tile + 256 x pole groups, as rexi_set_pole_slots takes it) to *slots and its
+ * shape to *shape (either may be NULL).  Synchronous; uses the plan's workspaces, so no
+ * step of this plan may be in flight. */
 rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots, int32_t *shape);
 
 /* Sets the pole-slot layout for steps with this batch size without timing (for instance
  * from a cache of earlier rexi_tune results): slots >= 1 (rounded down to a multiple of
  * the lanes a warp gives each state and capped by the partial-sum buffer) and shape 0
- * or 1 as for rexi_tune, or shape 2 for the fused solve with `slots` states per CTA
- * tile (0: the default tile, the smallest power of two >= batch up to 32; a request is
- * rounded down to a power of two), or shape 3 for its lean form (three or four CTAs of
- * four warps per SM, fewer registers, the next rows prefetched into the caches),
- * REXI_EINVAL where that does not apply; the slot count used (for shapes 2 and 3 the
- * tile) is written to *used (may be NULL).  Results are deterministic for any layout; only the order of the
- * final pole sum changes.  Synchronous, like rexi_tune. */
+ * or 1 as for rexi_tune, or shape 2 for the fused solve with slots = tile + 256 x groups
+ * >= 0: `tile` states per CTA tile (0: the default tile, the smallest power of two >=
+ * batch up to 32; a request is rounded down to a power of two) and each tile's poles
+ * split over `groups` CTAs in whole passes of the CTA's pole lanes (0: the default, more
+ * than one only when a batch is too small to fill the GPU; a request is capped at the
+ * passes), the last CTA of a tile to finish adding the groups' partial sums in group
+ * order, or shape 3 for its lean form (three or four CTAs of four warps per SM, fewer
+ * registers, the next rows prefetched into the caches), REXI_EINVAL where that does not
+ * apply; the slot count used (for shapes 2 and 3: the tile + 256 x the groups) is
+ * written to *used (may be NULL).  Results are deterministic for any layout; only the
+ * order of the final pole sum changes.  Synchronous, like rexi_tune. */
 rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t shape, int32_t *used);
 
 /* Host-side description of a plan (no counterpart in the paper): writes up to 8 int64 values

@@ -521,11 +521,12 @@ rexi_status get_layout(Plan &pl, int B, bool single, SolveLayout **out) {
 }
 
 // Largest batch for which the untuned default is the fused solve.  Measured on GB300
-// (T63-T341, M = 128-256): with one or two states the fused solve is 1.04-2x faster than
-// the best slot layout with its reduction (a single state's slot layout needs hundreds of
-// partial sums); from four states on the slot kernel, with four warps per scheduler,
-// keeps the FP64 pipe busier (98 % against 82-86 %) and wins.  rexi_tune decides per batch.
-constexpr int kFusedDefaultMaxBatch = 2;
+// (T63-T341, M = 128-256), with each tile's poles split over the default number of CTAs:
+// up to four states the fused solve is 1.03-3.4x faster than the best slot layout with
+// its reduction (a single state's slot layout needs hundreds of partial sums); at eight
+// states its default tile of eight is slower than the slot solve at T341.  rexi_tune
+// decides per batch (and finds fused layouts that win up to sixteen states at T127-T170).
+constexpr int kFusedDefaultMaxBatch = 4;
 
 // The fused solve's layout for steps of B states, or null when the slot-partial path
 // serves them: float-float solves, the Phi-only solver, the f-sphere, an explicit
@@ -541,40 +542,43 @@ const FusedLayout *fused_layout(Plan &pl, int B) {
     FusedLayout F;
     auto ft = pl.fused_tile.find(B);
     auto fl = pl.fused_lean.find(B);
+    auto fg = pl.fused_groups.find(B);
     if (!build_fused_layout(pl, B, ft != pl.fused_tile.end() ? ft->second : 0,
-                            fl != pl.fused_lean.end() && fl->second, F))
+                            fl != pl.fused_lean.end() && fl->second, fg != pl.fused_groups.end() ? fg->second : 0, F))
       F = FusedLayout{};
     it = pl.fused.emplace(B, F).first;  // st == 0: not available
   }
   return it->second.st > 0 ? &it->second : nullptr;
 }
 
-// the fused layout for batch B with a requested CTA tile (0: the default) and form,
-// replacing any earlier one
-const FusedLayout *set_fused_tile(Plan &pl, int B, int tile, bool lean = false) {
+// the fused layout for batch B with a requested CTA tile and number of pole groups (0:
+// the defaults) and form, replacing any earlier one
+const FusedLayout *set_fused_tile(Plan &pl, int B, int tile, bool lean = false, int groups = 0) {
   auto it = pl.fused.find(B);
   if (it != pl.fused.end()) {
-    if (it->second.items_dev) cudaFree(it->second.items_dev);
+    free_fused_layout(it->second);
     pl.fused.erase(it);
   }
   pl.fused_tile[B] = tile;
   pl.fused_lean[B] = lean;
+  pl.fused_groups[B] = groups;
   return fused_layout(pl, B);
 }
 
 // A given slot count for batch B: the layout with slots / kk pole groups replaces any
-// earlier one for that batch.  Shape 2 selects the fused solve instead (REXI_EINVAL where
-// it does not apply).
+// earlier one for that batch.  Shapes 2 and 3 select the fused solve instead (REXI_EINVAL
+// where it does not apply), with slots = tile + 256 x pole groups.
 rexi_status set_layout(Plan &pl, int B, int slots, int shape, int *used) {
   if (shape == 2 || shape == 3) {
     pl.use_slots[B] = false;
-    if (!set_fused_tile(pl, B, slots, shape == 3)) {
+    if (!set_fused_tile(pl, B, slots % 256, shape == 3, slots / 256)) {
       pl.use_slots[B] = true;
       set_error("rexi_set_pole_slots: the fused solve (shape 2) needs binary64 solves of the delta solver on "
                 "the rotating sphere, with running sums that fit in shared memory");
       return REXI_EINVAL;
     }
-    if (used) *used = fused_layout(pl, B)->st;
+    const FusedLayout *F = fused_layout(pl, B);
+    if (used) *used = F->st + 256 * F->ng;
     return REXI_OK;
   }
   SolveLayout L;
@@ -650,31 +654,39 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
       cudaFree(L.items_dev);
     }
   }
-  // the fused solve (no slot partials, no reduction) in its CTA tiles of 32 ... 2 states
-  // competes with the best slot layout
+  // the fused solve (no slot partials, no reduction) in its CTA tiles of 32 ... 2 states,
+  // with the poles of a tile split over the default number of CTAs and over 1 ... 8 CTAs
+  // (up to 2 above eight states), competes with the best slot layout
   float fused_ms = 1e30f;
-  int best_tile = 0;
+  int best_tile = 0, best_groups = 1;
   pl.use_slots[B] = false;
   bool best_lean = false;
   for (int tile = 32; tile >= 1; tile /= 2) {
     for (int lean = 0; lean < 2; ++lean) {
-      const FusedLayout *F = set_fused_tile(pl, B, tile, lean != 0);
-      if (!F || F->st != tile) continue;  // the default is smaller, or it does not fit
-      launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);  // warm-up
-      cudaEventRecord(e0, st);
-      for (int rep = 0; rep < 2; ++rep) launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);
-      cudaEventRecord(e1, st);
-      float ms = 1e30f;
-      if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < fused_ms) {
-        fused_ms = ms;
-        best_tile = tile;
-        best_lean = lean != 0;
+      std::vector<int> seen;
+      for (int groups : {0, 1, 2, 3, 4, 6, 8}) {  // 0: the default count
+        if (groups > 2 && B > 8) break;  // larger batches leave fewer schedulers idle
+        const FusedLayout *F = set_fused_tile(pl, B, tile, lean != 0, groups);
+        if (!F || F->st != tile) break;  // the default is smaller, or it does not fit
+        if (std::find(seen.begin(), seen.end(), F->ng) != seen.end()) continue;  // capped at the passes
+        seen.push_back(F->ng);
+        launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);  // warm-up
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2; ++rep) launch_solve_fused(pl, *F, false, pl.s_in, pl.s_out, B, st);
+        cudaEventRecord(e1, st);
+        float ms = 1e30f;
+        if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < fused_ms) {
+          fused_ms = ms;
+          best_tile = tile;
+          best_lean = lean != 0;
+          best_groups = F->ng;
+        }
       }
     }
-    if (tile <= 2) break;  // smaller tiles only re-read the factors more often
+    if (tile <= 2 && tile < B) break;  // smaller tiles only re-read the factors more often
   }
-  if (best_tile > 0) set_fused_tile(pl, B, best_tile, best_lean);
+  if (best_tile > 0) set_fused_tile(pl, B, best_tile, best_lean, best_groups);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   auto it = pl.layouts.find(B);
@@ -685,7 +697,7 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
   pl.layouts.emplace(B, bestL);
   const bool fused_wins = fused_ms <= best;
   pl.use_slots[B] = !fused_wins;
-  if (slots_out) *slots_out = fused_wins ? best_tile : bestL.slots;
+  if (slots_out) *slots_out = fused_wins ? best_tile + 256 * best_groups : bestL.slots;
   if (shape_out) *shape_out = fused_wins ? (best_lean ? 3 : 2) : bestL.shape;
   return REXI_OK;
 }
@@ -704,8 +716,7 @@ void free_plan(Plan *pl) {
     if (p) cudaFree(p);
   for (auto &kv : pl->layouts)
     if (kv.second.items_dev) cudaFree(kv.second.items_dev);
-  for (auto &kv : pl->fused)
-    if (kv.second.items_dev) cudaFree(kv.second.items_dev);
+  for (auto &kv : pl->fused) free_fused_layout(kv.second);
   delete pl;
 }
 

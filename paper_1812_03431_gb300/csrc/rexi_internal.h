@@ -94,15 +94,22 @@ struct SolveLayout {
 
 // CTA shape and work list of the fused solve (solve_fused.cu) for one batch size: ST
 // states per CTA tile over WS warps of SB states; WP warps split the poles when the tile
-// has fewer than four states.  items: (system 2 m + p, first state), longest first.
+// has fewer than four states; NG CTAs split the poles of one (system, tile) in groups of
+// gsz poles, the last of them to finish adding the groups' partial sums.  items: (system
+// 2 m + p, first state, pole group, (system, tile) index), longest first.
 struct FusedLayout {
   int sb = 0, ws = 0, wp = 0, st = 0;
   int nw = 8;       // warps per CTA: 8 (one CTA per SM) or 4 (two CTAs per SM, or the lean form)
   int per_sm = 1;   // CTAs per SM (lean form: 3 or 4)
+  int ng = 1, gsz = 0;  // pole groups per (system, tile) and poles per group
+  int ntiles = 0;       // (system, tile) pairs
   int nitems = 0;
-  int2 *items_dev = nullptr;
+  int4 *items_dev = nullptr;
+  double2 *part_dev = nullptr;   // NG > 1: [B / st][ng][st][nrows][4] partial sums
+  unsigned *sync_dev = nullptr;  // [1 + ntiles]: the work counter, then per (system, tile) arrivals
   size_t smem = 0;  // dynamic shared memory per CTA (running sums and the exchange buffer)
 };
+void free_fused_layout(FusedLayout &F);
 
 struct FftPlan {
   int n;
@@ -222,6 +229,7 @@ struct Plan {
   std::map<int, bool> use_slots;
   std::map<int, int> fused_tile;  // requested states per CTA tile (0: the default)
   std::map<int, bool> fused_lean; // the lean form (three or four CTAs of four warps per SM)
+  std::map<int, int> fused_groups; // requested CTAs per system's poles (0: the default)
 
   // optional per-stage timing with CUDA events on the launching stream
   bool prof = false;
@@ -271,7 +279,7 @@ SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double
                     int pole_begin, int pole_end);
 // fused solve: eligible plans (binary64 delta solver on the rotating sphere) whose running
 // sums fit in shared memory; sin -> sout ([3][nspec][B]) with no partial sums and no reduction
-bool build_fused_layout(Plan &pl, int B, int tile, bool lean, FusedLayout &F);
+bool build_fused_layout(Plan &pl, int B, int tile, bool lean, int groups, FusedLayout &F);
 cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, const double2 *sin, double2 *sout,
                                int B, cudaStream_t st);
 cudaError_t launch_solve_ragged(const SolveView *views_dev, const WorkItem *items, int nitems, double2 *ybuf,

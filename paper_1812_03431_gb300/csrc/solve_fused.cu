@@ -26,7 +26,11 @@
 //     at m = 0 and writes each output coefficient once.
 // The forward-sweep values y go through a per-warp global buffer (L2-resident: one CTA
 // of eight warps per SM, 256 lanes x lmax rows).  No partial sums leave the SM and no reduction kernel
-// follows.
+// follows -- except when a batch is too small to fill the GPU (one state has 2 (N + 1)
+// systems for 608 schedulers, and the longest one alone would set the time): then NG
+// CTAs split a tile's poles in whole passes, each writes its group's sums to global
+// memory, and the last of them to arrive (an atomic count; nothing waits) adds the NG
+// partials in group order and writes the outputs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -65,11 +69,13 @@ struct FusedArgs {
   double2 *sout;        // [3][nspec][B]
   double2 *ybuf;        // [gridDim.x * NW][lmax][32]
   const int4 *sys;      // per (m, p): {m, n0, len, row0}
-  const int2 *items;    // (system 2 m + p, first state of the tile), longest first
-  unsigned *counter;
+  const int4 *items;    // (system 2 m + p, first state of the tile, pole group, tile index)
+  unsigned *counter;    // work counter
+  unsigned *arrivals;   // NG > 1: per (system, tile), pole groups finished
+  double2 *part;        // NG > 1: [B / ST][NG][ST][nrows][4] the groups' partial sums
   const double2 *wz;    // [nspec] Sum beta_k / (alpha_k + i tau sigma_n) (adjoint: its counterpart)
   double2 sphi;         // Sum beta_k / alpha_k over the plan's poles
-  int nitems, P, N, B, WS, WP, lmax, pole_begin, pole_end, realm0;
+  int nitems, P, N, B, WS, WP, lmax, pole_begin, pole_end, realm0, NG, gsz;
   int64_t nspec, nrows;
 };
 
@@ -96,7 +102,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
   constexpr bool kLean = MINB * NW > kWarpsPerSM;
   constexpr int kBufs = kLean ? 1 : 2;  // exchange buffers per warp
   extern __shared__ double2 smem[];
-  __shared__ int s_item;
+  __shared__ int s_item, s_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ws = warp / a.WP, wp = warp - ws * a.WP;  // state group, pole group of this warp
   const int ST = a.WS * SB;                           // states per CTA tile
@@ -118,11 +124,13 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
     const int it = s_item;
     __syncthreads();
     if (it >= a.nitems) break;
-    const int2 item = a.items[it];
+    const int4 item = a.items[it];
     const int4 sy = a.sys[item.x];
     const int m = sy.x, n0 = sy.y, len = sy.z;
     const int64_t row0 = sy.w;
     const int p = item.x & 1, b0 = item.y;
+    const int kg0 = a.pole_begin + item.z * a.gsz;       // this CTA's poles [kg0, kg1)
+    const int kg1 = min(a.pole_end, kg0 + a.gsz);
     const int64_t base_idx = (int64_t)m * (2 * N + 3 - m) / 2 - m;  // idx(m, n) = base_idx + n
     const int nmin = m > 1 ? m : 1;
 
@@ -139,9 +147,9 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
       const double2 *sPhi = a.sin + bq, *sZeta = a.sin + NS * B + bq, *sDel = a.sin + 2 * NS * B + bq;
       const int npp = a.WP * PL;  // poles per CTA pass
       const int nr = (len + R - 1) / R;  // task rounds of the backward sweep
-      for (int kb = a.pole_begin; kb < a.pole_end; kb += npp) {
-        const int kw = kb + wp * PL;               // this warp's first pole
-        const int npa = min(PL, a.pole_end - kw);  // its active poles (warp-uniform)
+      for (int kb = kg0; kb < kg1; kb += npp) {
+        const int kw = kb + wp * PL;         // this warp's first pole
+        const int npa = min(PL, kg1 - kw);   // its active poles (warp-uniform)
         if (npa <= 0) continue;
         const bool active = pl < npa;              // inactive lanes repeat a valid pole, add zero
         const int k = kw + min(pl, npa - 1);
@@ -294,6 +302,34 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
     }
     __syncthreads();
 
+    // ---- NG > 1: the NG CTAs of one (system, tile) each hold the sums over their own
+    // pole group.  Each writes them (added over its WP warp groups) to the tile's partial
+    // slots and counts its arrival; the last to arrive adds the NG partials in group order
+    // and writes the outputs.  No CTA waits for another, and the order of the sum does not
+    // depend on which CTA comes last.
+    const int64_t PS = NR * kStreams;  // one state's partial sums of one group
+    const double2 *pg = nullptr;       // the tile's partials at this system (NG > 1, last CTA)
+    if (a.NG > 1) {
+      double2 *mine = a.part + ((size_t)(b0 / ST) * a.NG + item.z) * ST * PS + row0 * kStreams;
+      for (int q = threadIdx.x; q < ST * len * kStreams; q += kThreads) {
+        const int st = q / (len * kStreams), r = q - st * (len * kStreams);
+        double2 v = make_double2(0.0, 0.0);
+        for (int g = 0; g < a.WP; ++g) {
+          const double2 u = acc[((size_t)g * ST + st) * ACS + r];
+          v.x += u.x;
+          v.y += u.y;
+        }
+        mine[(size_t)st * PS + r] = v;
+      }
+      __threadfence();  // the partials are visible device-wide before the arrival counts
+      __syncthreads();
+      if (threadIdx.x == 0) s_last = atomicAdd(a.arrivals + item.w, 1u) == (unsigned)(a.NG - 1);
+      __syncthreads();
+      if (!s_last) continue;  // block-uniform
+      __threadfence();
+      pg = a.part + (size_t)(b0 / ST) * a.NG * ST * PS + row0 * kStreams;
+    }
+
     // ---- outputs of this item: delta and Phi at the degrees of parity p, zeta at the
     // other parity; every coefficient of the item written once
     {
@@ -306,6 +342,14 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
         if (b >= B) continue;
         auto sumacc = [&](int i, int t) {
           double2 v = make_double2(0.0, 0.0);
+          if (pg) {  // the groups' partials, from L2 (written by other SMs)
+            for (int g = 0; g < a.NG; ++g) {
+              const double2 u = __ldcg(pg + ((size_t)g * ST + st) * PS + i * kStreams + t);
+              v.x += u.x;
+              v.y += u.y;
+            }
+            return v;
+          }
           for (int g = 0; g < a.WP; ++g) {
             const double2 u = acc[((size_t)g * ST + st) * ACS + i * kStreams + t];
             v.x += u.x;
@@ -352,14 +396,22 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
 
 }  // namespace
 
+void free_fused_layout(FusedLayout &F) {
+  if (F.items_dev) cudaFree(F.items_dev);
+  if (F.part_dev) cudaFree(F.part_dev);
+  if (F.sync_dev) cudaFree(F.sync_dev);
+  F = FusedLayout{};
+}
+
 // Work items and CTA shape of the fused solve for a batch of B states: ST states per
 // CTA tile (the smallest power of two >= B, at most 32, or a smaller requested tile),
 // split over the eight warps as WS state groups of SB states; when the tile has fewer
 // than eight states the remaining warps split the poles (WP groups).  Smaller tiles give
 // more, shorter work items (better balance over the SMs) at the cost of reading each
-// factor once per tile.  Returns false when the running sums of a tile do
-// not fit in shared memory (the slot-partial path then serves the plan).
-bool build_fused_layout(Plan &pl, int B, int tile, bool lean, FusedLayout &F) {
+// factor once per tile.  `groups` CTAs (0: the default below) split each (system, tile)'s
+// poles in whole passes.  Returns false when the running sums of a tile do not fit in
+// shared memory (the slot-partial path then serves the plan).
+bool build_fused_layout(Plan &pl, int B, int tile, bool lean, int groups, FusedLayout &F) {
   F = FusedLayout{};
   int st = 1;
   while (st < B && st < 32) st *= 2;
@@ -438,21 +490,56 @@ bool build_fused_layout(Plan &pl, int B, int tile, bool lean, FusedLayout &F) {
     F = FusedLayout{};
     return false;
   }
-  // items (system, first state), longest system first; m ascending breaks ties
-  struct Keyed { int2 it; int len; };
+
+  // pole groups: NG CTAs share a (system, tile), each taking whole passes of WP x PL poles.
+  // Default: the fewest groups for which the longest system's CTA (its warps sharing their
+  // schedulers with the SM's other resident warps) needs at most half the FP64 work the
+  // average scheduler has in all -- so that the longest items, taken first, leave room to
+  // balance the rest; with a large batch, or many orders, that is one group.
+  const int npp = F.wp * (32 / F.sb), passes = (pl.P + npp - 1) / npp;
+  const int ntile_b = (B + F.st - 1) / F.st;
+  int ng = 1;
+  if (groups > 0) {
+    ng = std::min(groups, passes);
+  } else {
+    double work = 0;  // warp passes x rows over every (system, tile)
+    int lmax_sys = 0;
+    const double wpasses = (double)F.ws * ((pl.P + 32 / F.sb - 1) / (32 / F.sb));  // per tile, per row
+    for (int sy = 0; sy < 2 * (pl.N + 1); ++sy) {
+      work += wpasses * pl.sys[sy].len * ntile_b;
+      lmax_sys = std::max(lmax_sys, pl.sys[sy].len);
+    }
+    const double avg = work / (4.0 * pl.num_sms);        // per scheduler (four per SM)
+    const double share = std::max(1.0, F.per_sm * F.nw / 4.0);  // warps per scheduler, SM full
+    for (ng = 1; ng < passes; ++ng)
+      if (share * lmax_sys * ((passes + ng - 1) / ng) <= 0.5 * avg) break;
+  }
+  // the groups' partial sums take B x NG x rows x 64 bytes: at most 1 GiB
+  while (ng > 1 && (double)ntile_b * F.st * ng * pl.nrows * kStreams * sizeof(double2) > 1073741824.0) --ng;
+  F.gsz = ((passes + ng - 1) / ng) * npp;
+  F.ng = (pl.P + F.gsz - 1) / F.gsz;
+
+  // items (system, first state, group, tile index), longest system first; m ascending
+  // breaks ties and a tile's groups stay together
+  struct Keyed { int4 it; int len; };
   std::vector<Keyed> keyed;
+  int ti = 0;
   for (int m = 0; m <= pl.N; ++m)
     for (int p = 0; p < 2; ++p)
-      for (int b0 = 0; b0 < B; b0 += F.st) keyed.push_back(Keyed{make_int2(2 * m + p, b0), pl.sys[2 * m + p].len});
+      for (int b0 = 0; b0 < B; b0 += F.st, ++ti)
+        for (int g = 0; g < F.ng; ++g) keyed.push_back(Keyed{make_int4(2 * m + p, b0, g, ti), pl.sys[2 * m + p].len});
   std::stable_sort(keyed.begin(), keyed.end(), [](const Keyed &x, const Keyed &y) { return x.len > y.len; });
-  std::vector<int2> items;
+  std::vector<int4> items;
   for (const Keyed &k : keyed) items.push_back(k.it);
+  F.ntiles = ti;
   F.nitems = (int)items.size();
-  cudaError_t e = cudaMalloc(&F.items_dev, items.size() * sizeof(int2));
-  if (e == cudaSuccess) e = cudaMemcpy(F.items_dev, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMalloc(&F.items_dev, items.size() * sizeof(int4));
+  if (e == cudaSuccess) e = cudaMemcpy(F.items_dev, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&F.sync_dev, (size_t)(1 + (F.ng > 1 ? F.ntiles : 0)) * sizeof(unsigned));
+  if (e == cudaSuccess && F.ng > 1)
+    e = cudaMalloc(&F.part_dev, (size_t)ntile_b * F.ng * F.st * pl.nrows * kStreams * sizeof(double2));
   if (e != cudaSuccess) {
-    if (F.items_dev) cudaFree(F.items_dev);
-    F.items_dev = nullptr;
+    free_fused_layout(F);
     return false;
   }
   return true;
@@ -467,7 +554,11 @@ cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, con
   a.ybuf = pl.yscratch;  // sized for 16 warps x 2 poles per SM: eight warps of one pole here
   a.sys = pl.sys_dev;
   a.items = F.items_dev;
-  a.counter = pl.counter;
+  a.counter = F.sync_dev;
+  a.arrivals = F.sync_dev + 1;
+  a.part = F.part_dev;
+  a.NG = F.ng;
+  a.gsz = F.gsz;
   a.wz = adjoint ? pl.w_adj : pl.w_fwd;
   a.sphi = adjoint ? pl.sphi_adj : pl.sphi_fwd;
   a.nitems = F.nitems;
@@ -482,7 +573,7 @@ cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, con
   a.realm0 = 1;
   a.nspec = pl.nspec;
   a.nrows = pl.nrows;
-  cudaError_t e = cudaMemsetAsync(pl.counter, 0, sizeof(unsigned), st);
+  cudaError_t e = cudaMemsetAsync(F.sync_dev, 0, (size_t)(1 + (F.ng > 1 ? F.ntiles : 0)) * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const int grid = pl.num_sms * F.per_sm;
   const int smem = (int)F.smem;

@@ -32,7 +32,10 @@ def main():
     ap.add_argument("--solver", default="delta", choices=["delta", "phi"])
     ap.add_argument("--solve-arith", default="fp64", choices=["fp64", "fp32x2"])
     ap.add_argument("--layout-shape", type=int, default=-1,
-                    help="with --pole-slots: 0 same pole groups for every order, 1 proportional to length")
+                    help="with --pole-slots: 0 same pole groups for every order, 1 proportional to length; "
+                         "2 (3: lean) the fused solve with --pole-slots states per CTA tile")
+    ap.add_argument("--pole-groups", type=int, default=0,
+                    help="with layout shapes 2 and 3: CTAs per tile's poles (0: the default)")
     args = ap.parse_args()
     import torch
 
@@ -45,7 +48,7 @@ def main():
                      precision=args.precision, pole_slots=args.pole_slots, solver=args.solver,
                      solve_arith=args.solve_arith)
     if args.layout_shape >= 0 and args.pole_slots > 0:
-        plan.set_pole_slots(args.batch, args.pole_slots, args.layout_shape)
+        plan.set_pole_slots(args.batch, args.pole_slots, args.layout_shape, groups=args.pole_groups)
     slots = plan.tune(args.batch) if args.tune else plan.info()["pole_slots"]
     S = torch.from_numpy(inputs.random_spectral(args.N, args.batch, 3)).cuda()
     x = plan.synthesize(S) if args.layout == "grid" else S

@@ -284,8 +284,9 @@ class Plan:
     def tune(self, batch, cache=None):
         """rexi_tune: time the solve and reduction for several pole-group counts and both
         slot-layout shapes at this batch size, and the fused solve (shape 2, no slots) where
-        it applies, and keep the fastest; returns the chosen number of pole slots (0 for the
-        fused solve; the shape is kept in ``self.layout_shape[batch]``).
+        it applies, and keep the fastest; returns the chosen number of pole slots (for the
+        fused solve its tile + 256 x its pole groups; the shape is kept in
+        ``self.layout_shape[batch]``).
 
         ``cache``: path of a JSON file of earlier choices keyed by the plan's shape (N,
         grid, P, batch, precision, solver, solve arithmetic) and the GPU's name; a hit sets the layout
@@ -309,11 +310,16 @@ class Plan:
             os.replace(tmp, cache)
         return n.value
 
-    def set_pole_slots(self, batch, slots, shape=0):
+    def set_pole_slots(self, batch, slots, shape=0, groups=0):
         """rexi_set_pole_slots: use this pole-slot count and layout shape (0: the same groups
         for every zonal order, 1: in proportion to the system length) for this batch size,
-        or shape 2: the fused solve with ``slots`` states per CTA tile (0: default)."""
+        or shape 2 (3: its lean form): the fused solve with ``slots`` states per CTA tile
+        (0: default) and each tile's poles split over ``groups`` CTAs (0: default).  For
+        shapes 2 and 3 returns tile + 256 x groups as used (``slots`` may carry that packing
+        itself, as rexi_tune returns it)."""
         n = _I32()
+        if shape >= 2:
+            slots = slots + 256 * groups
         _check("rexi_set_pole_slots", load().rexi_set_pole_slots(self._h, batch, slots, shape, ctypes.byref(n)))
         self.layout_shape[batch] = shape
         return n.value

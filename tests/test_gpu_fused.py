@@ -39,23 +39,36 @@ def test_fused_step_matches_oracle_and_slot_solve(N, M, B, tau):
     S = inputs.random_spectral(N, B, 500 + N + B)
     x = torch.from_numpy(S).cuda()
     plan = rexi.Plan(N, *grid(N), tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
-    tile = plan.set_pole_slots(B, 0, 2)  # the fused solve with its default CTA tile
-    assert tile >= 1 and tile >= min(B, 32) and tile & (tile - 1) == 0
+    used = plan.set_pole_slots(B, 0, 2, groups=1)  # the default CTA tile, one CTA per tile
+    tile = used % 256
+    assert used // 256 == 1 and tile >= min(B, 32) and tile & (tile - 1) == 0
     fused = plan.step(x).cpu().numpy()
     np.testing.assert_array_equal(plan.step(x).cpu().numpy(), fused)  # bit-reproducible
     if B > 2:  # a smaller tile: more, shorter work items; below 8 states the poles of a
         # tile are split over warp groups, which changes the order of the sum
-        assert plan.set_pole_slots(B, tile // 2, 2) == tile // 2
+        assert plan.set_pole_slots(B, tile // 2, 2, groups=1) == tile // 2 + 256
         half = plan.step(x).cpu().numpy()
         if tile // 2 >= 8:
             np.testing.assert_array_equal(half, fused)
         assert fieldwise(half, fused) < 1e-13
+    # each tile's poles over several CTAs (the default count, then fixed ones, capped at
+    # the passes); whichever CTA finishes last adds the groups in the same order
+    for groups in (0, 2, 3):
+        used = plan.set_pole_slots(B, tile, 2, groups=groups)
+        assert used % 256 == tile and used // 256 >= 1 and (groups == 0 or used // 256 <= groups)
+        split = plan.step(x).cpu().numpy()
+        for _ in range(2):
+            np.testing.assert_array_equal(plan.step(x).cpu().numpy(), split)
+        assert fieldwise(split, fused) < 1e-13
     # the lean form (three or four CTAs of four warps per SM, prefetching into the caches)
-    lt = plan.set_pole_slots(B, tile, 3)  # at most two states per warp: tiles of 8 or less
+    lt = plan.set_pole_slots(B, tile, 3, groups=1) % 256  # at most two states per warp: tiles of 8 or less
     assert 1 <= lt <= min(tile, 8)
     lean = plan.step(x).cpu().numpy()
     np.testing.assert_array_equal(plan.step(x).cpu().numpy(), lean)
     assert fieldwise(lean, fused) < 1e-13
+    plan.set_pole_slots(B, lt, 3, groups=2)
+    lean2 = plan.step(x).cpu().numpy()
+    assert fieldwise(lean2, fused) < 1e-13
     plan.set_pole_slots(B, 8, 0)  # the pole-slot solve and its reduction
     slot = plan.step(x).cpu().numpy()
     plan.close()
@@ -65,10 +78,44 @@ def test_fused_step_matches_oracle_and_slot_solve(N, M, B, tau):
     assert np.all(fused[:, 1:, 0] == 0) and np.all(fused[:, :, : N + 1].imag == 0)
 
 
+@pytest.mark.parametrize("B", [1, 2])
+def test_pole_groups_single_state_match_oracle(B):
+    # Sec. 6.1's single state (T63, M = 128: 279 poles): every split of a tile's poles over
+    # 1 ... 9 CTAs against the oracle; the default for one state splits them (128 systems
+    # alone would leave most schedulers idle), and a split result is the same on every run
+    import torch
+    from paper_1812_03431_gb300 import rexi
+    N, M, tau = 63, 128, 3600.0
+    al, be, _ = rc.rexi_coefficients(M, 0.2)
+    S = inputs.noisy_balanced(N, 1000) if B == 1 else inputs.random_spectral(N, B, 64)
+    S = S.reshape(B, 3, -1)
+    x = torch.from_numpy(S).cuda()
+    plan = rexi.Plan(N, 96, 192, tau=tau, max_batch=B, layout="spectral", alpha=al, beta=be)
+    ref = ostep.rexi_step_spectral(S, N, al, be, tau, C)
+    ref_adj = ostep.rexi_step_spectral(S, N, al, be, tau, C, adjoint=True)
+    default = plan.set_pole_slots(B, 0, 2) // 256
+    if B == 1:
+        assert default > 1
+    seen = set()
+    for groups in range(1, 10):
+        ng = plan.set_pole_slots(B, 0, 2, groups=groups) // 256
+        if ng in seen:
+            continue
+        seen.add(ng)
+        got = plan.step(x).cpu().numpy()
+        for _ in range(3):
+            np.testing.assert_array_equal(plan.step(x).cpu().numpy(), got)
+        assert fieldwise(got, ref) < TOL
+        adj = plan.step_adjoint(x).cpu().numpy()
+        assert fieldwise(adj, ref_adj) < TOL
+    assert len(seen) >= 3
+    plan.close()
+
+
 def test_fused_is_the_small_batch_default_and_drops_the_reduction():
     import torch
     from paper_1812_03431_gb300 import rexi
-    N, B = 31, 2
+    N, B = 31, 4
     plan = rexi.Plan(N, 48, 96, M=32, max_batch=B, layout="spectral")
     x = torch.from_numpy(inputs.random_spectral(N, B, 9)).cuda()
     plan.profile_enable(1)
@@ -84,9 +131,9 @@ def test_fused_is_the_small_batch_default_and_drops_the_reduction():
     st, _ = plan.profile_read()
     assert st["reduce"] > 0
     plan.close()
-    plan = rexi.Plan(N, 48, 96, M=32, max_batch=4, layout="spectral")
+    plan = rexi.Plan(N, 48, 96, M=32, max_batch=8, layout="spectral")
     plan.profile_enable(1)
-    plan.step(torch.from_numpy(inputs.random_spectral(N, 4, 9)).cuda())
+    plan.step(torch.from_numpy(inputs.random_spectral(N, 8, 9)).cuda())
     st, _ = plan.profile_read()
     assert st["reduce"] > 0
     plan.close()

@@ -82,14 +82,19 @@ def test_ragged_c3_matches_per_plan_steps_and_graph_replay(env):
         plan.close()
 
 
-@pytest.mark.parametrize("shape,precision", [(None, "fp64"), (2, "fp64"), (3, "mixed"), (0, "mixed")])
-def test_step_in_cuda_graph(env, shape, precision):
-    # the default (slot) solve, the fused solve in both forms, a fixed slot layout
+@pytest.mark.parametrize("shape,precision,groups", [(None, "fp64", 0), (2, "fp64", 1), (3, "mixed", 0),
+                                                    (0, "mixed", 0), (2, "fp64", 3)])
+def test_step_in_cuda_graph(env, shape, precision, groups):
+    # the default (slot) solve, the fused solve in both forms, a fixed slot layout, and the
+    # fused solve with each tile's poles over three CTAs (the arrival counts are reset by
+    # a memset inside the graph)
     torch, rexi = env
     N, nlat, nlon, B = 127, 192, 384, 4
     plan = rexi.Plan(N, nlat, nlon, M=128, tau=1200.0, max_batch=B, precision=precision)
     if shape is not None:
-        plan.set_pole_slots(B, 16 if shape == 0 else 0, shape)
+        used = plan.set_pole_slots(B, 16 if shape == 0 else 0, shape, groups=groups)
+        if groups:
+            assert used // 256 == groups
     x = plan.synthesize(torch.from_numpy(inputs.random_spectral(N, B, 5)).cuda())
     y = torch.empty_like(x)
     plan.step(x, out=y)  # first call with this batch builds the work list
