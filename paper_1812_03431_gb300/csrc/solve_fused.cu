@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -264,6 +265,42 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
               if (q < npa) pf_l1(Wn + q);  // poles of this pass only: every address inside the factors
           }
         };
+        // The last round of a pass holds rv = len - rr R rows (1 ... R).  With rv <= R / H the
+        // lanes of the missing rows would sum nothing useful, so the round is laid out as
+        // R / H rows x SB states x 4 streams x H pole slices: each lane sums PL / H poles of
+        // its row and the H slices are added by shuffles (lanes 4 SB apart).  Slice 0 starts
+        // from the running sum; the order of every addition is fixed.
+        auto task_split = [&](auto Hc, int rr, const double2 *wbuf) {
+          constexpr int H = decltype(Hc)::value, QH = PL / H;
+          const int h = (lane / (4 * SB)) % H, tr = lane / (4 * SB * H);
+          const int iv = len - 1 - rr * R - tr;
+          const int ii = max(iv, 0);
+          double2 *ap = acc + ((size_t)wp * ST + ws * SB + t_s) * ACS + ii * kStreams + t_t;
+          const double2 *W = a.fac + ((int64_t)t_comp * NR + row0 + ii) * P + kw;
+          const double2 *wv = wbuf + tr * RS + t_s * (PL + 1) + h * QH;
+          double2 s = h == 0 ? *ap : make_double2(0.0, 0.0);
+#pragma unroll
+          for (int q = 0; q < QH; ++q) s = cfma_(s, ldg2(W + min(h * QH + q, npa - 1)), wv[q]);
+#pragma unroll
+          for (int o = 4 * SB; o < 4 * SB * H; o *= 2) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+          }
+          if (h == 0 && iv >= 0) *ap = s;
+        };
+        auto task_last = [&](int rr, const double2 *wbuf) {
+          const int rv = len - rr * R;
+          if constexpr (R >= 8) {
+            if (rv <= R / 8) { task_split(std::integral_constant<int, 8>{}, rr, wbuf); return; }
+          }
+          if constexpr (R >= 4) {
+            if (rv <= R / 4) { task_split(std::integral_constant<int, 4>{}, rr, wbuf); return; }
+          }
+          if constexpr (R >= 2) {
+            if (rv <= R / 2) { task_split(std::integral_constant<int, 2>{}, rr, wbuf); return; }
+          }
+          task_round(rr, wbuf);
+        };
         if constexpr (kLean) {
           // one exchange buffer: each round's recurrence, then its sums; the next round's
           // sweep values and factors two rounds ahead into L1
@@ -282,7 +319,8 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
             load_round(rr);
             rec_round(rr, wbase);
             __syncwarp();
-            task_round(rr, wbase);
+            if (rr + 1 < nr) task_round(rr, wbase);
+            else task_last(rr, wbase);
             __syncwarp();
           }
         } else {
@@ -294,7 +332,8 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
             double2 *wcur = wbase + (rr & 1) * R * RS, *wnxt = wbase + ((rr + 1) & 1) * R * RS;
             if (rr + 1 < nr) rec_round(rr + 1, wnxt);
             if (rr + 2 < nr) load_round(rr + 2);
-            task_round(rr, wcur);
+            if (rr + 1 < nr) task_round(rr, wcur);
+            else task_last(rr, wcur);
             __syncwarp();
           }
         }
