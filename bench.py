@@ -64,8 +64,9 @@ FF_OPS_PER_ROW = 36 * 12
 # batch 16, by (pole slots, layout shape); traffic per row is constant, so a launch of the
 # bench workload moves this times rows(T341) / rows(T170).  Re-captured after each change
 # of the solve kernel.
-# (slots, 2): the fused solve with that many states per CTA tile
-SOLVE_TRAFFIC_T170 = {(32, 0): 12.64e9, (32, 1): 12.58e9, (64, 0): 11.63e9, (2, 2): 1.59e9, (4, 2): 1.82e9}
+# (tile, 2) and (tile, 3): the fused solve's register and lean forms with that many states
+# per CTA tile and one pole group
+SOLVE_TRAFFIC_T170 = {(32, 0): 12.64e9, (32, 1): 12.58e9, (64, 0): 11.63e9, (2, 2): 1.64e9, (2, 3): 4.92e9}
 SOLVE_FF_TRAFFIC_T170 = {(32, 0): 11.64e9}  # the float-float kernel (solve_kernel<true>)
 
 
@@ -569,8 +570,10 @@ def main():
     fused = r["shape"] in (2, 3)
     # the fused solve's slot count packs its CTA tile and pole groups (tile + 256 x groups)
     tile_or_slots = r["slots"] % 256 if fused else r["slots"]
-    tkey = min(traffic_t170, key=lambda k: (k[1] != min(r["shape"], 2), abs(k[0] - tile_or_slots)))
-    traffic = traffic_t170[tkey] * rows_of(W["N"]) / rows_of(170) if traffic_t170[tkey] else None
+    tkey = min(traffic_t170, key=lambda k: (k[1] != r["shape"], abs(k[0] - tile_or_slots)))
+    traffic = traffic_t170[tkey] * rows_of(W["N"]) / rows_of(170) if tkey[1] == r["shape"] else None
+    if fused and r["slots"] // 256 != 1:
+        traffic = None  # the captures are of one pole group per tile
     if fused:
         kname = "solve_fused_kernel (FP64 banded solves, beta-weighted pole sum on chip)"
     dtypes = {"mixed": "f64 solves + pole sum; 3xtf32 legendre; f32 fft", "fp64": "f64",
@@ -595,9 +598,10 @@ def main():
         "roofline": {"bound": "alu", "kernel": kname,
                      "achieved": achieved, "peak": peak, "unit": roof_unit, "frac": achieved / peak,
                      "traffic": traffic,
-                     "traffic_source": ("ncu dram bytes at T170/K256/B16 with %d pole slots, layout shape %d "
-                                        "(the captured layout nearest the bench's %d, shape %d; shape 2 = fused), "
-                                        "scaled by rows to T341" % (tkey[0], tkey[1], r["slots"], r["shape"]))
+                     "traffic_source": ("ncu dram bytes at T170/K256/B16 with %d pole slots (fused: states per "
+                                        "tile), layout shape %d (the captured layout nearest the bench's %d, shape "
+                                        "%d; shapes 2 and 3 = fused), scaled by rows to T341"
+                                        % (tkey[0], tkey[1], tile_or_slots, r["shape"]))
                      if default_workload and traffic else "not captured for this workload or kernel",
                      "dram_gbs": traffic / (solve_ms * 1e-3) / 1e9 if traffic else None,
                      "peak_source": peak_source, "algorithmic_per_launch": amount, "launch_ms": solve_ms},
