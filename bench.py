@@ -60,13 +60,14 @@ FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve: 36 F
 # multiply-adds, each an error-free product and sum of 12 FP32 operations (1 mul, 3 FMA,
 # 8 add); stored values stay unnormalised pairs, so there is no renormalisation
 FF_OPS_PER_ROW = 36 * 12
-# DRAM bytes (read + write) of one solve_kernel launch from ncu captures at T170, K=256,
-# batch 16, by (pole slots, layout shape); traffic per row is constant, so a launch of the
-# bench workload moves this times rows(T341) / rows(T170).  Re-captured after each change
-# of the solve kernel.
-# (tile, 2) and (tile, 3): the fused solve's register and lean forms with that many states
-# per CTA tile and one pole group
-SOLVE_TRAFFIC_T170 = {(32, 0): 12.64e9, (32, 1): 12.58e9, (64, 0): 11.63e9, (2, 2): 1.64e9, (2, 3): 4.92e9}
+# DRAM bytes (read + write) of one solve launch from ncu captures (K=256, batch 16), keyed by
+# (truncation, pole slots or, for the fused solve, states per CTA tile, layout shape):
+# shape 0/1 the slot kernel, 2/3 the fused solve's register/lean form with one pole group.
+# A workload without its own capture takes the nearest layout captured at T170, scaled by
+# rows (traffic per row is constant).  Re-captured after each change of the solve kernels.
+SOLVE_TRAFFIC = {(341, 64, 0): 48.82e9, (341, 2, 3): 18.60e9,
+                 (170, 32, 0): 12.64e9, (170, 32, 1): 12.58e9, (170, 64, 0): 11.63e9,
+                 (170, 2, 2): 1.64e9, (170, 2, 3): 4.92e9}
 SOLVE_FF_TRAFFIC_T170 = {(32, 0): 11.64e9}  # the float-float kernel (solve_kernel<true>)
 
 
@@ -558,22 +559,32 @@ def main():
     sm_mhz = (r["clocks"] or {}).get("sm_max_mhz") or 2070.0
     if r["solve_arith"] == "fp32x2":
         amount, peak = FF_OPS_PER_ROW * B * P * rows_of(W["N"]), fp32_peak_tops(sm_mhz)
-        traffic_t170, kname = SOLVE_FF_TRAFFIC_T170, "solve_kernel<true> (float-float banded solves + pole sum)"
+        traffic_tab = {(170,) + k: v for k, v in SOLVE_FF_TRAFFIC_T170.items()}
+        kname = "solve_kernel<true> (float-float banded solves + pole sum)"
         roof_unit, peak_source = "Tops/s", "derived: 152 SMs x 128 FP32 lanes x sm_max_mhz (ops = adds, mults, FMAs)"
     else:
         amount, peak = FLOPS_PER_ROW * B * P * rows_of(W["N"]), fp64_tf or fp64_peak_tflops(sm_mhz)
-        traffic_t170, kname = SOLVE_TRAFFIC_T170, "solve_kernel<false> (FP64 banded solves + pole sum)"
+        traffic_tab, kname = SOLVE_TRAFFIC, "solve_kernel<false> (FP64 banded solves + pole sum)"
         roof_unit = "TFLOP/s"
         peak_source = ("measured: rexi_measure_fp64_fma, best of 5 per shape (FP64 FMA chains)" if fp64_tf else
                        "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz")
     achieved = amount / (solve_ms * 1e-3) / 1e12
     fused = r["shape"] in (2, 3)
     # the fused solve's slot count packs its CTA tile and pole groups (tile + 256 x groups)
-    tile_or_slots = r["slots"] % 256 if fused else r["slots"]
-    tkey = min(traffic_t170, key=lambda k: (k[1] != r["shape"], abs(k[0] - tile_or_slots)))
-    traffic = traffic_t170[tkey] * rows_of(W["N"]) / rows_of(170) if tkey[1] == r["shape"] else None
-    if fused and r["slots"] // 256 != 1:
-        traffic = None  # the captures are of one pole group per tile
+    tile_or_slots, groups = (r["slots"] % 256, r["slots"] // 256) if fused else (r["slots"], 1)
+    tkey, traffic = None, None
+    if (W["N"], tile_or_slots, r["shape"]) in traffic_tab:
+        tkey = (W["N"], tile_or_slots, r["shape"])
+        traffic = traffic_tab[tkey]
+    else:
+        near = [k for k in traffic_tab if k[0] == 170 and k[2] == r["shape"]]
+        if near:
+            tkey = min(near, key=lambda k: abs(k[1] - tile_or_slots))
+            traffic = traffic_tab[tkey] * rows_of(W["N"]) / rows_of(170)
+    if traffic and groups > 1:
+        # the captures hold one pole group; NG groups add their partial sums, written once
+        # and read once: B x NG x rows x 4 streams x 16 bytes each way
+        traffic += 2 * B * groups * rows_of(W["N"]) * 64
     if fused:
         kname = "solve_fused_kernel (FP64 banded solves, beta-weighted pole sum on chip)"
     dtypes = {"mixed": "f64 solves + pole sum; 3xtf32 legendre; f32 fft", "fp64": "f64",
@@ -598,13 +609,20 @@ def main():
         "roofline": {"bound": "alu", "kernel": kname,
                      "achieved": achieved, "peak": peak, "unit": roof_unit, "frac": achieved / peak,
                      "traffic": traffic,
-                     "traffic_source": ("ncu dram bytes at T170/K256/B16 with %d pole slots (fused: states per "
-                                        "tile), layout shape %d (the captured layout nearest the bench's %d, shape "
-                                        "%d; shapes 2 and 3 = fused), scaled by rows to T341"
-                                        % (tkey[0], tkey[1], tile_or_slots, r["shape"]))
+                     "traffic_source": ("ncu dram bytes at T%d/K256/B16, %d pole slots (fused: states per tile), "
+                                        "layout shape %d (shapes 2 and 3 = fused; the bench's layout: %d, shape %d, "
+                                        "%d pole group(s))%s" % (tkey[0], tkey[1], tkey[2], tile_or_slots, r["shape"],
+                                                                 groups, "" if tkey[0] == W["N"] else
+                                                                 ", scaled by rows to T%d" % W["N"]))
                      if default_workload and traffic else "not captured for this workload or kernel",
                      "dram_gbs": traffic / (solve_ms * 1e-3) / 1e9 if traffic else None,
                      "peak_source": peak_source, "algorithmic_per_launch": amount, "launch_ms": solve_ms},
+        # the whole S4 stage (banded solves and the complete pole sum): the fused solve's time
+        # alone, or the slot kernel's plus its reduction -- the two paths compared like for like
+        "solve_stage": {"ms": solve_ms + r["stages"].get("reduce", 0.0),
+                        "achieved": amount / ((solve_ms + r["stages"].get("reduce", 0.0)) * 1e-3) / 1e12,
+                        "frac": amount / ((solve_ms + r["stages"].get("reduce", 0.0)) * 1e-3) / 1e12 / peak,
+                        "unit": roof_unit, "kernels": "solve_fused_kernel" if fused else "solve_kernel + reduce_kernel"},
         "fp64_peak": {"tflops": fp64_tf, "ms": fp64_ms, "clocks": fp64_clocks,
                       "derived_tflops_at_max_clock": fp64_peak_tflops(sm_mhz)},
         "state_steps_per_s": jobs * B * 1e3 / r["ms"],

@@ -261,7 +261,8 @@ rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *
  * with the pole sum on chip and no slots, in CTA tiles of 32 down to 2 states (down to
  * 1 for batches of 1 and 2) and, for batches up to 8, with each tile's poles split over
  * 1, 2, 3, 4, 6 or 8 CTAs, and shape 3: its lean form (see rexi_set_pole_slots).  Keeps
- * the fastest for later steps with this batch and writes its slot count (for shapes 2
+ * the fastest for later steps with this batch (the fused solve unless a slot layout is
+ * more than 0.5 % faster: it needs no reduction) and writes its slot count (for shapes 2
  * and 3: tile + 256 x pole groups, as rexi_set_pole_slots takes it) to *slots and its
  * shape to *shape (either may be NULL).  Synchronous; uses the plan's workspaces, so no
  * step of this plan may be in flight. */

@@ -695,7 +695,9 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
     pl.layouts.erase(it);
   }
   pl.layouts.emplace(B, bestL);
-  const bool fused_wins = fused_ms <= best;
+  // at a tie the fused solve is kept: no reduction kernel and a fraction of the slot
+  // path's DRAM traffic for the same FP64 work
+  const bool fused_wins = fused_ms <= best * 1.005f;
   pl.use_slots[B] = !fused_wins;
   if (slots_out) *slots_out = fused_wins ? best_tile + 256 * best_groups : bestL.slots;
   if (shape_out) *shape_out = fused_wins ? (best_lean ? 3 : 2) : bestL.shape;
