@@ -573,8 +573,8 @@ rexi_status set_layout(Plan &pl, int B, int slots, int shape, int *used) {
     pl.use_slots[B] = false;
     if (!set_fused_tile(pl, B, slots % 256, shape == 3, slots / 256)) {
       pl.use_slots[B] = true;
-      set_error("rexi_set_pole_slots: the fused solve (shape 2) needs binary64 solves of the delta solver on "
-                "the rotating sphere, with running sums that fit in shared memory");
+      set_error("rexi_set_pole_slots: the fused solve (shapes 2 and 3) needs binary64 solves of the delta "
+                "solver on the rotating sphere, with running sums that fit in shared memory");
       return REXI_EINVAL;
     }
     const FusedLayout *F = fused_layout(pl, B);

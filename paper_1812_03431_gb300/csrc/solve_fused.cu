@@ -24,8 +24,9 @@
 //     passes; at the end of the item the CTA adds the pole-independent terms
 //     (Sum beta/alpha Phi0, Sum beta/(alpha + i tau sigma_n) zeta0), takes the real part
 //     at m = 0 and writes each output coefficient once.
-// The forward-sweep values y go through a per-warp global buffer (L2-resident: one CTA
-// of eight warps per SM, 256 lanes x lmax rows).  No partial sums leave the SM and no reduction kernel
+// The forward-sweep values y go through a per-warp global buffer of 32 lanes x lmax rows
+// (in L2 while the resident warps' buffers fit: 8 warps per SM at T341, 16 at T170).  No
+// partial sums leave the SM and no reduction kernel
 // follows -- except when a batch is too small to fill the GPU (one state has 2 (N + 1)
 // systems for 608 schedulers, and the longest one alone would set the time): then NG
 // CTAs split a tile's poles in whole passes, each writes its group's sums to global
