@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(THREADS) leg_ana_tc_kernel(TcArgs a) {
 
 // ---- synthesis ------------------------------------------------------------------------
 // dynamic smem: [A: 8 x 16 KiB][B1_0, B1_1: (hi, lo) 8G x 32][B2_0, B2_1: (hi, lo) 4G x 32]
-__global__ void __launch_bounds__(THREADS) leg_syn_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(THREADS, 1) leg_syn_tc_kernel(TcArgs a) {  // one CTA per SM (shared memory)
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -412,7 +412,12 @@ __global__ void __launch_bounds__(THREADS) leg_syn_tc_kernel(TcArgs a) {
     {
       constexpr int RMAX = 1024 / THREADS;  // 2 q x 8 kq x 4 G <= 1024
       const int nun = 2 * (KB / 4) * 4 * G;
-      float2 xv[RMAX][4];
+      // every load of the block first (an element outside the data reads element 0 and
+      // is zeroed), then the conversions: converting inside the load loop puts one memory
+      // latency per load on the critical path (measured: 11.6 of the block's 14 us at T341)
+      double2 xr[RMAX][4];
+      double zr[RMAX][4];
+      bool vr[RMAX][4];
 #pragma unroll
       for (int rr = 0; rr < RMAX; ++rr) {
         const int u = tid + rr * THREADS;
@@ -422,15 +427,22 @@ __global__ void __launch_bounds__(THREADS) leg_syn_tc_kernel(TcArgs a) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int n = m + q + 2 * (kb * KB + 4 * kq + r);
-          xv[rr][r] = make_float2(0.f, 0.f);
-          if (u < nun && f < 3 && n <= a.N && b < a.B) {
-            const int64_t ix = idx0 + (n - m);
-            const double2 x = a.sint[((int64_t)f * a.nspec + ix) * a.B + b];
-            const float sc = f > 0 ? f64_to_f32(a.zd[ix]) : 1.0f;
-            xv[rr][r] = make_float2(sc * f64_to_f32(x.x), sc * f64_to_f32(x.y));
-          }
+          const bool v = u < nun && f < 3 && n <= a.N && b < a.B;
+          const int64_t ix = v ? idx0 + (n - m) : 0;
+          xr[rr][r] = a.sint[((int64_t)(v ? f : 0) * a.nspec + ix) * a.B + (v ? b : 0)];
+          zr[rr][r] = f > 0 ? a.zd[ix] : 1.0;
+          vr[rr][r] = v;
         }
       }
+      float2 xv[RMAX][4];
+#pragma unroll
+      for (int rr = 0; rr < RMAX; ++rr)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float sc = f64_to_f32(zr[rr][r]);
+          xv[rr][r] = vr[rr][r] ? make_float2(sc * f64_to_f32(xr[rr][r].x), sc * f64_to_f32(xr[rr][r].y))
+                                : make_float2(0.f, 0.f);
+        }
 #pragma unroll
       for (int rr = 0; rr < RMAX; ++rr) {
         const int u = tid + rr * THREADS;
