@@ -508,10 +508,18 @@ __global__ void __launch_bounds__(THREADS, 1) leg_syn_tc_kernel(TcArgs a) {  // 
     if (tid == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
   } else {
     const int wq = warp & 3, half = warp >> 2;
-    const int j = jt * TM + wq * 32 + (tid & 31);
+    const int jl = wq * 32 + (tid & 31);  // this thread's latitude row of the tile
     const uint32_t lane_addr = tbase + ((uint32_t)(wq * 32) << 16);
     const int M1 = a.N + 1, ncol = 3 * a.B;
     const float fm = (float)m;
+    // With 8 or more states a group, the tile's results go through shared memory (free
+    // once the last MMA has completed), [north, south][TM latitudes][3G columns + 1], so
+    // that each latitude's 3G columns reach the Fourier array as one contiguous row (the
+    // odd row stride puts the 32 latitudes a warp writes on distinct banks): -14 % at 16
+    // states.  Smaller groups store directly, a few columns per latitude.
+    const bool via_smem = G >= 8;
+    const int CW = 3 * G, RSW = 3 * G + 1;
+    float2 *tr = reinterpret_cast<float2 *>(sm);
     for (int bl = half * (G / 2); bl < (half + 1) * (G / 2); ++bl) {
       float2 F[2][3];
       for (int cls = 0; cls < 2; ++cls) {
@@ -525,14 +533,33 @@ __global__ void __launch_bounds__(THREADS, 1) leg_syn_tc_kernel(TcArgs a) {  // 
         F[cls][1] = make_float2(-d2[0] - fm * d1[5], -d2[1] + fm * d1[4]);
         F[cls][2] = make_float2(-fm * d1[3] + d2[2], fm * d1[2] + d2[3]);
       }
-      const int b = b0 + bl;
-      if (j < a.J && b < a.B) {
-        float2 *north = a.four + ((int64_t)j * M1 + m) * ncol + 3 * b;
-        float2 *south = a.four + ((int64_t)(a.nlat - 1 - j) * M1 + m) * ncol + 3 * b;
+      if (via_smem) {
         for (int f = 0; f < 3; ++f) {
-          north[f] = make_float2(F[0][f].x + F[1][f].x, F[0][f].y + F[1][f].y);
-          south[f] = make_float2(F[0][f].x - F[1][f].x, F[0][f].y - F[1][f].y);
+          tr[jl * RSW + 3 * bl + f] = make_float2(F[0][f].x + F[1][f].x, F[0][f].y + F[1][f].y);
+          tr[(TM + jl) * RSW + 3 * bl + f] = make_float2(F[0][f].x - F[1][f].x, F[0][f].y - F[1][f].y);
         }
+      } else {
+        const int j = jt * TM + jl, b = b0 + bl;
+        if (j < a.J && b < a.B) {
+          float2 *north = a.four + ((int64_t)j * M1 + m) * ncol + 3 * b;
+          float2 *south = a.four + ((int64_t)(a.nlat - 1 - j) * M1 + m) * ncol + 3 * b;
+          for (int f = 0; f < 3; ++f) {
+            north[f] = make_float2(F[0][f].x + F[1][f].x, F[0][f].y + F[1][f].y);
+            south[f] = make_float2(F[0][f].x - F[1][f].x, F[0][f].y - F[1][f].y);
+          }
+        }
+      }
+    }
+    if (via_smem) {  // block-uniform
+      __syncthreads();
+      // one warp per row: the valid columns (states < B) of latitude j, north then south
+      const int ncw = min(CW, ncol - 3 * b0), lane = tid & 31;
+      for (int row = warp; row < 2 * TM; row += THREADS / 32) {
+        const int side = row / TM, jr = row - side * TM, j = jt * TM + jr;
+        if (j >= a.J) continue;
+        float2 *dst = a.four + ((int64_t)(side ? a.nlat - 1 - j : j) * M1 + m) * ncol + 3 * b0;
+        const float2 *srow = tr + row * RSW;
+        for (int c = lane; c < ncw; c += 32) dst[c] = srow[c];
       }
     }
   }
