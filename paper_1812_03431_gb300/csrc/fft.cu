@@ -182,21 +182,38 @@ __global__ void fft_fwd_kernel(FftArgs a, const double *grid, void *four_v, cons
   const int j = blockIdx.y;
   const int c0 = blockIdx.x * a.np;
   const double2 *g2 = reinterpret_cast<const double2 *>(grid);
-  for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
-    const int q = fdiv(t, a.mag_h, h), k = t - q * h;
-    const int c = c0 + q;
-    C v = {0, 0};
-    if (c < a.ncol) {
-      const double s = in_scale[(c % 3) * a.nlat + j];
-      const double2 x = g2[((int64_t)c * a.nlat + j) * h + k];
-      if constexpr (F32) {
-        const float s32 = f64_to_f32(s);
-        v = C{s32 * f64_to_f32(x.x), s32 * f64_to_f32(x.y)};
-      } else {
-        v = C{s * x.x, s * x.y};
-      }
+  // in chunks of kLd elements per thread: every load of a chunk first (an element outside
+  // the data reads element 0 and is zeroed), then the conversions, so that the loads'
+  // latencies overlap instead of one conversion waiting on each
+  constexpr int kLd = 8;
+  for (int t0 = 0; t0 < a.np * h; t0 += kLd * blockDim.x) {
+    double2 x[kLd];
+    double sv[kLd];
+    bool ok[kLd];
+#pragma unroll
+    for (int i = 0; i < kLd; ++i) {
+      const int t = t0 + i * blockDim.x + threadIdx.x;
+      const int q = fdiv(t, a.mag_h, h), k = t - q * h;
+      const int c = c0 + q;
+      ok[i] = t < a.np * h && c < a.ncol;
+      x[i] = g2[ok[i] ? ((int64_t)c * a.nlat + j) * h + k : 0];
+      sv[i] = in_scale[ok[i] ? (c % 3) * a.nlat + j : 0];
     }
-    buf0[t] = v;
+#pragma unroll
+    for (int i = 0; i < kLd; ++i) {
+      const int t = t0 + i * blockDim.x + threadIdx.x;
+      if (t >= a.np * h) break;
+      C v = {0, 0};
+      if (ok[i]) {
+        if constexpr (F32) {
+          const float s32 = f64_to_f32(sv[i]);
+          v = C{s32 * f64_to_f32(x[i].x), s32 * f64_to_f32(x[i].y)};
+        } else {
+          v = C{sv[i] * x[i].x, sv[i] * x[i].y};
+        }
+      }
+      buf0[t] = v;
+    }
   }
   __syncthreads();
   const C *Z = fft_smem<T>(buf0, buf1, a);
@@ -231,33 +248,53 @@ __global__ void fft_inv_kernel(FftArgs a, const void *four_v, double *grid, cons
   const int j = blockIdx.y;
   const int c0 = blockIdx.x * a.np;
   const int N = a.N, M1 = N + 1;
-  auto msc = [&](int mm) -> T {
-    if constexpr (F32) return f64_to_f32(m_scale[mm]); else return m_scale[mm];
-  };
-  // column index fastest, so that neighbouring threads read neighbouring Fourier columns
-  for (int t = threadIdx.x; t < a.np * h; t += blockDim.x) {
-    const int m = fdiv(t, a.mag_np, a.np), q = t - m * a.np;
-    const int c = c0 + q;
-    C A = {0, 0}, Bc = {0, 0};
-    if (c < a.ncol) {
-      if (m <= N) {
-        const T s = msc(m);
-        const C v = four[((int64_t)j * M1 + m) * a.ncol + c];
-        A = C{s * v.x, m == 0 ? (T)0 : s * v.y};
-      }
+  // column index fastest, so that neighbouring threads read neighbouring Fourier columns;
+  // in chunks of kLd elements per thread, every load of a chunk before any use (an element
+  // outside the data reads element 0 and is zeroed)
+  constexpr int kLd = 4;
+  for (int t0 = 0; t0 < a.np * h; t0 += kLd * blockDim.x) {
+    C va[kLd], vb[kLd];
+    double sa[kLd], sb[kLd];
+    bool oka[kLd], okb[kLd];
+#pragma unroll
+    for (int i = 0; i < kLd; ++i) {
+      const int t = t0 + i * blockDim.x + threadIdx.x;
+      const int m = fdiv(t, a.mag_np, a.np), q = t - m * a.np;
+      const int c = c0 + q;
+      const bool in = t < a.np * h && c < a.ncol;
       const int mr = h - m;  // partner X_{h-m}, present when h - m <= N
-      if (m > 0 && mr <= N) {
-        const T s = msc(mr);
-        const C v = four[((int64_t)j * M1 + mr) * a.ncol + c];
-        Bc = C{s * v.x, mr == 0 ? (T)0 : -s * v.y};  // conj(X_{h-m})
-      }
+      oka[i] = in && m <= N;
+      okb[i] = in && m > 0 && mr <= N;
+      va[i] = four[oka[i] ? ((int64_t)j * M1 + m) * a.ncol + c : 0];
+      vb[i] = four[okb[i] ? ((int64_t)j * M1 + mr) * a.ncol + c : 0];
+      sa[i] = m_scale[oka[i] ? m : 0];
+      sb[i] = m_scale[okb[i] ? mr : 0];
     }
-    // E' = X_m + conj X_{h-m},  O' = (X_m - conj X_{h-m}) e^{+2 pi i m / n},  Z' = E' + i O'
-    const C E = addz(A, Bc);
-    const C w = tw[m];
-    const C O = cmulz(subz(A, Bc), C{w.x, -w.y});
-    const C Zp = {E.x - O.y, E.y + O.x};
-    buf0[q * h + m] = C{Zp.x, -Zp.y};  // conj(Z') for the inverse by a forward FFT
+#pragma unroll
+    for (int i = 0; i < kLd; ++i) {
+      const int t = t0 + i * blockDim.x + threadIdx.x;
+      if (t >= a.np * h) break;
+      const int m = fdiv(t, a.mag_np, a.np), q = t - m * a.np;
+      const int mr = h - m;
+      auto toT = [](double v) -> T {
+        if constexpr (F32) return f64_to_f32(v); else return v;
+      };
+      C A = {0, 0}, Bc = {0, 0};
+      if (oka[i]) {
+        const T s = toT(sa[i]);
+        A = C{s * va[i].x, m == 0 ? (T)0 : s * va[i].y};
+      }
+      if (okb[i]) {
+        const T s = toT(sb[i]);
+        Bc = C{s * vb[i].x, mr == 0 ? (T)0 : -s * vb[i].y};  // conj(X_{h-m})
+      }
+      // E' = X_m + conj X_{h-m},  O' = (X_m - conj X_{h-m}) e^{+2 pi i m / n},  Z' = E' + i O'
+      const C E = addz(A, Bc);
+      const C w = tw[m];
+      const C O = cmulz(subz(A, Bc), C{w.x, -w.y});
+      const C Zp = {E.x - O.y, E.y + O.x};
+      buf0[q * h + m] = C{Zp.x, -Zp.y};  // conj(Z') for the inverse by a forward FFT
+    }
   }
   __syncthreads();
   const C *r = fft_smem<T>(buf0, buf1, a);
