@@ -208,10 +208,30 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         os.unlink(self.path)
+        note = None
+        if not sms:
+            # a timed region shorter than the sampling period: one reading right after it
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=10).stdout
+                parts = [p.strip() for p in out.strip().split(",")]
+                if len(parts) >= 9:
+                    sms.append(float(parts[1]))
+                    mx = float(parts[2])
+                    for n, v in zip(names, parts[5:9]):
+                        if v.lower() == "active":
+                            reasons.add(n)
+                    note = "timed region shorter than the 200 ms sampling period: one reading right after it"
+            except (OSError, ValueError, subprocess.TimeoutExpired):
+                pass
         if not sms:
             return None
-        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sms)}
+        rec = {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+               "samples": len(sms) if note is None else 0}
+        if note:
+            rec["note"] = note
+        return rec
 
 
 def host_threads():
