@@ -486,8 +486,8 @@ bool build_fused_layout(Plan &pl, int B, int tile, bool lean, int groups, FusedL
     }
     // two CTAs of four warps when both fit on an SM (a tile's poles then need no split over
     // warps down to four states), else one CTA of eight warps; at most two states per warp
-    // unless nothing else fits (four states per warp leave the FP64 pipe half idle: 50 %
-    // measured at T170)
+    // unless nothing else fits (four states per warp, in tiles of 16 states at T170, left
+    // the FP64 pipe 50 % idle)
     for (int nw : {4, 8, 4 + 0x100, 8 + 0x100}) {
       const bool wide = nw & 0x100;
       nw &= 0xff;
