@@ -299,8 +299,11 @@ rexi_status rexi_plan_info(const rexi_plan *plan, int64_t *info, int32_t n);
  * device arrays (p = state_plan[s]); at most max_batch of plan p's states per
  * call, nstates <= max_states.  A call with a new per-plan state count
  * allocates its work list once; after that the call allocates nothing and can
- * be captured in a CUDA graph.  Results equal each plan's rexi_step up to the
- * summation order of the poles. */
+ * be captured in a CUDA graph.  rexi_tune or rexi_set_pole_slots on one of the
+ * plans replaces the slot layout the work lists were built from: the next call
+ * rebuilds them (allocating once more), and a graph captured before must be
+ * captured again.  Results equal each plan's rexi_step up to the summation order
+ * of the poles. */
 rexi_status rexi_ragged_create(rexi_plan *const *plans, int32_t nplans, int32_t max_states,
                                rexi_ragged **out);
 rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *const *out_dev,

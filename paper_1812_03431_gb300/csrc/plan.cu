@@ -591,6 +591,7 @@ rexi_status set_layout(Plan &pl, int B, int slots, int shape, int *used) {
   if (it != pl.layouts.end()) {
     cudaFree(it->second.items_dev);
     pl.layouts.erase(it);
+    ++pl.layout_gen;
   }
   pl.layouts.emplace(B, L);
   pl.use_slots[B] = true;
@@ -693,6 +694,7 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
   if (it != pl.layouts.end()) {
     cudaFree(it->second.items_dev);
     pl.layouts.erase(it);
+    ++pl.layout_gen;
   }
   pl.layouts.emplace(B, bestL);
   // at a tie the fused solve is kept: no reduction kernel and a fraction of the slot

@@ -31,6 +31,7 @@ struct rexi_ragged {
     rexi::SolveView *views_dev = nullptr;
     rexi::WorkItem *items_dev = nullptr;
     int nitems = 0;
+    std::vector<uint64_t> gens;  // the plans' layout generations the views were built from
   };
   std::map<std::vector<int>, Cfg> cfgs;
 };
@@ -126,6 +127,17 @@ rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *c
       if (r != REXI_OK) return r;
     }
   auto it = rg->cfgs.find(counts);
+  std::vector<uint64_t> gens(np);
+  for (int p = 0; p < np; ++p) gens[p] = rg->plans[p]->layout_gen;
+  if (it != rg->cfgs.end() && it->second.gens != gens) {
+    // a plan's slot layout was replaced (rexi_tune, rexi_set_pole_slots) since this work
+    // list was built: its views point at the freed one, so it is rebuilt.  No step of
+    // this ragged object may be in flight meanwhile (the same rule as for the tuning call)
+    if (it->second.views_dev) cudaFree(it->second.views_dev);
+    if (it->second.items_dev) cudaFree(it->second.items_dev);
+    rg->cfgs.erase(it);
+    it = rg->cfgs.end();
+  }
   if (it == rg->cfgs.end()) {
     std::vector<SolveView> views(np);
     struct Tagged { WorkItem w; double work; };
@@ -150,6 +162,7 @@ rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *c
     for (const Tagged &t : all) items.push_back(t.w);
     rexi_ragged::Cfg cfg;
     cfg.nitems = (int)items.size();
+    cfg.gens = gens;
     cudaError_t e = cudaMalloc(&cfg.views_dev, views.size() * sizeof(SolveView));
     if (e == cudaSuccess) e = cudaMalloc(&cfg.items_dev, std::max<size_t>(1, items.size()) * sizeof(WorkItem));
     if (e == cudaSuccess) e = cudaMemcpy(cfg.views_dev, views.data(), views.size() * sizeof(SolveView), cudaMemcpyHostToDevice);

@@ -222,6 +222,9 @@ struct Plan {
   size_t partial_cap = 0;
 
   std::map<int, SolveLayout> layouts;  // per batch size
+  // bumped whenever a slot layout is replaced (its device work list freed): objects that
+  // cached views of the old one (ragged batches) rebuild them
+  uint64_t layout_gen = 0;
   int slots_override = 0;
   // fused solve (binary64 delta solver): per batch size its layout, and whether the slot
   // layout above was chosen instead (rexi_tune, rexi_set_pole_slots, pole_slots)

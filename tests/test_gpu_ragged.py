@@ -82,6 +82,39 @@ def test_ragged_c3_matches_per_plan_steps_and_graph_replay(env):
         plan.close()
 
 
+def test_ragged_rebuilds_after_a_plan_is_retuned(env):
+    # the ragged object caches views of each plan's slot layout; re-tuning a plan (or
+    # setting another slot count) replaces that layout, and the next ragged step must
+    # rebuild its work list rather than read the freed one
+    torch, rexi = env
+    plans = [rexi.Plan(N, *grid_of(N), M=K, tau=1200.0, max_batch=3, layout="spectral")
+             for N, K in ((63, 128), (127, 256))]
+    state_plan = [0, 1, 1, 0, 1]
+    states = [torch.from_numpy(inputs.random_spectral(63 if p == 0 else 127, 1, 3000 + s)[0]).cuda()
+              for s, p in enumerate(state_plan)]
+    outs = [torch.empty_like(x) for x in states]
+    rg = rexi.Ragged(plans, 5)
+
+    def check():
+        rg.step(states, outs, state_plan)
+        torch.cuda.synchronize()
+        for p, plan in enumerate(plans):
+            idx = [s for s in range(5) if state_plan[s] == p]
+            Y = plan.step(torch.stack([states[s] for s in idx])).cpu().numpy()
+            for r, s in enumerate(idx):
+                assert rel(outs[s].cpu().numpy(), Y[r]) < 1e-13
+
+    check()
+    plans[1].set_pole_slots(3, 256, 1)  # another slot layout for the 3 states of plan 1
+    check()
+    plans[0].tune(2)
+    plans[1].tune(3)
+    check()
+    rg.close()
+    for plan in plans:
+        plan.close()
+
+
 @pytest.mark.parametrize("shape,precision,groups", [(None, "fp64", 0), (2, "fp64", 1), (3, "mixed", 0),
                                                     (0, "mixed", 0), (2, "fp64", 3)])
 def test_step_in_cuda_graph(env, shape, precision, groups):
