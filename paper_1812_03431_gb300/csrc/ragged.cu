@@ -32,6 +32,8 @@ struct rexi_ragged {
     rexi::WorkItem *items_dev = nullptr;
     int nitems = 0;
     std::vector<uint64_t> gens;  // the plans' layout generations the views were built from
+    bool fused = false;          // binary64 plans: the fused solve over every plan's items
+    rexi::FusedRagged fr;
   };
   std::map<std::vector<int>, Cfg> cfgs;
 };
@@ -119,17 +121,27 @@ rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *c
       set_error("rexi_ragged_step: more states for plan " + std::to_string(p) + " than its max_batch");
       return REXI_EINVAL;
     }
-  // per-plan layouts and the merged work list (cached per count vector)
+  // binary64 plans: one fused launch over every plan's items (the pole sum on chip, no
+  // reductions); else the slot kernel over the merged work list, then per-plan reductions.
+  // Either work list is cached per count vector.
+  auto it = rg->cfgs.find(counts);
+  if (it == rg->cfgs.end() && !rg->plans[0]->ff) {
+    rexi_ragged::Cfg cfg;
+    if (build_fused_ragged(rg->plans, counts, cfg.fr)) {
+      cfg.fused = true;
+      it = rg->cfgs.emplace(counts, cfg).first;
+    }
+  }
+  const bool fused = it != rg->cfgs.end() && it->second.fused;
   std::vector<SolveLayout *> lays(np, nullptr);
-  for (int p = 0; p < np; ++p)
+  for (int p = 0; p < np && !fused; ++p)
     if (counts[p] > 0) {
       rexi_status r = get_layout(*rg->plans[p], counts[p], false, &lays[p]);
       if (r != REXI_OK) return r;
     }
-  auto it = rg->cfgs.find(counts);
   std::vector<uint64_t> gens(np);
   for (int p = 0; p < np; ++p) gens[p] = rg->plans[p]->layout_gen;
-  if (it != rg->cfgs.end() && it->second.gens != gens) {
+  if (!fused && it != rg->cfgs.end() && it->second.gens != gens) {
     // a plan's slot layout was replaced (rexi_tune, rexi_set_pole_slots) since this work
     // list was built: its views point at the freed one, so it is rebuilt.  No step of
     // this ragged object may be in flight meanwhile (the same rule as for the tuning call)
@@ -180,17 +192,22 @@ rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *c
     e = cudaGetLastError();
   }
   const bool ff = rg->plans[0]->ff;
-  for (int p = 0; p < np && e == cudaSuccess; ++p)  // float-float solves read split states
-    if (ff && counts[p] > 0) {
-      Plan &pl = *rg->plans[p];
-      e = launch_split_state(pl, pl.s_in, pl.s_ff, 3 * pl.nspec * counts[p], st);
-    }
-  if (e == cudaSuccess)
-    e = launch_solve_ragged(cfg.views_dev, cfg.items_dev, cfg.nitems, rg->ybuf, rg->lmax, rg->counter,
-                            rg->resident_warps, ff, st);
-  for (int p = 0; p < np && e == cudaSuccess; ++p)
-    if (counts[p] > 0)
-      e = launch_reduce(*rg->plans[p], *lays[p], false, rg->plans[p]->s_in, rg->plans[p]->s_out, counts[p], false, 0, st);
+  if (cfg.fused) {
+    if (e == cudaSuccess) e = launch_fused_ragged(cfg.fr, rg->ybuf, rg->plans[0]->num_sms, st);
+  } else {
+    for (int p = 0; p < np && e == cudaSuccess; ++p)  // float-float solves read split states
+      if (ff && counts[p] > 0) {
+        Plan &pl = *rg->plans[p];
+        e = launch_split_state(pl, pl.s_in, pl.s_ff, 3 * pl.nspec * counts[p], st);
+      }
+    if (e == cudaSuccess)
+      e = launch_solve_ragged(cfg.views_dev, cfg.items_dev, cfg.nitems, rg->ybuf, rg->lmax, rg->counter,
+                              rg->resident_warps, ff, st);
+    for (int p = 0; p < np && e == cudaSuccess; ++p)
+      if (counts[p] > 0)
+        e = launch_reduce(*rg->plans[p], *lays[p], false, rg->plans[p]->s_in, rg->plans[p]->s_out, counts[p],
+                          false, 0, st);
+  }
   for (int s = 0; s < nstates && e == cudaSuccess; ++s) {
     Plan &pl = *rg->plans[state_plan[s]];
     const int64_t n3 = 3 * pl.nspec;
@@ -206,6 +223,7 @@ void rexi_ragged_destroy(rexi_ragged *rg) {
   for (auto &kv : rg->cfgs) {
     if (kv.second.views_dev) cudaFree(kv.second.views_dev);
     if (kv.second.items_dev) cudaFree(kv.second.items_dev);
+    free_fused_ragged(kv.second.fr);
   }
   if (rg->ybuf) cudaFree(rg->ybuf);
   if (rg->counter) cudaFree(rg->counter);

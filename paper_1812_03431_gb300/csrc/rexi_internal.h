@@ -111,6 +111,15 @@ struct FusedLayout {
 };
 void free_fused_layout(FusedLayout &F);
 
+// The fused solve over the states of several plans in one launch (ragged batches).
+struct FusedRagged {
+  void *views_dev = nullptr;  // per plan (solve_fused.cu's FusedView)
+  int4 *items_dev = nullptr;
+  unsigned *counter = nullptr;
+  int nitems = 0, nviews = 0, lmax = 0, per_sm = 0, ws = 0, wp = 0;
+  size_t smem = 0;
+};
+
 struct FftPlan {
   int n;
   int nstages;
@@ -283,6 +292,9 @@ SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double
 // fused solve: eligible plans (binary64 delta solver on the rotating sphere) whose running
 // sums fit in shared memory; sin -> sout ([3][nspec][B]) with no partial sums and no reduction
 bool build_fused_layout(Plan &pl, int B, int tile, bool lean, int groups, FusedLayout &F);
+bool build_fused_ragged(const std::vector<Plan *> &plans, const std::vector<int> &counts, FusedRagged &R);
+void free_fused_ragged(FusedRagged &R);
+cudaError_t launch_fused_ragged(const FusedRagged &R, double2 *ybuf, int num_sms, cudaStream_t st);
 cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, const double2 *sin, double2 *sout,
                                int B, cudaStream_t st);
 cudaError_t launch_solve_ragged(const SolveView *views_dev, const WorkItem *items, int nitems, double2 *ybuf,

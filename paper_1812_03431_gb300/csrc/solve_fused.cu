@@ -65,21 +65,35 @@ __device__ __forceinline__ void pf_l1(const void *p) { asm volatile("prefetch.gl
 constexpr int kWarpsPerSM = 8;         // two warps per SM sub-partition: one CTA of 8 or two of 4
 constexpr int kStreams = 4;            // delta, Phi, zeta at n + 1, zeta at n - 1
 
-struct FusedArgs {
+// per-plan arguments of the fused solve (a ragged launch holds one per plan)
+struct FusedView {
   const double2 *fac;   // [F_NCOMP][nrows][P]
   const double2 *sin;   // [3][nspec][B]
   double2 *sout;        // [3][nspec][B]
-  double2 *ybuf;        // [gridDim.x * NW][lmax][32]
   const int4 *sys;      // per (m, p): {m, n0, len, row0}
-  const int4 *items;    // (system 2 m + p, first state of the tile, pole group, tile index)
-  unsigned *counter;    // work counter
-  unsigned *arrivals;   // NG > 1: per (system, tile), pole groups finished
-  double2 *part;        // NG > 1: [B / ST][NG][ST][nrows][4] the groups' partial sums
   const double2 *wz;    // [nspec] Sum beta_k / (alpha_k + i tau sigma_n) (adjoint: its counterpart)
   double2 sphi;         // Sum beta_k / alpha_k over the plan's poles
-  int nitems, P, N, B, WS, WP, lmax, pole_begin, pole_end, realm0, NG, gsz;
+  unsigned *arrivals;   // NG > 1: per (system, tile), pole groups finished
+  double2 *part;        // NG > 1: [B / ST][NG][ST][nrows][4] the groups' partial sums
+  int P, N, B, pole_begin, pole_end, realm0, NG, gsz;
   int64_t nspec, nrows;
 };
+
+struct FusedArgs {
+  FusedView v;              // the plan of a single-plan launch
+  const FusedView *views;   // a ragged launch: one per plan, the item's plan selects it
+  double2 *ybuf;            // [gridDim.x * NW][lmax][32]
+  const int4 *items;        // (system 2 m + p, first state of the tile, pole group (+ 256 x plan
+                            // in a ragged launch), tile index), longest first
+  unsigned *counter;        // work counter
+  int nitems, WS, WP, lmax;  // lmax: the largest over the launch's plans
+};
+
+template <bool RG>
+__device__ __forceinline__ const FusedView &pick_view(const FusedView &param, const FusedView &shared) {
+  if constexpr (RG) return shared;
+  else return param;
+}
 
 // one forward-sweep row of one lane: its factors and the states it reads
 struct FwdRow {
@@ -98,19 +112,19 @@ struct FwdRow {
 // (up to 222 registers).  MINB > 2 (four warps per CTA, three or four CTAs per SM): the
 // lean form for 12 or 16 warps per SM -- registers capped at 170 or 128, one exchange
 // buffer per warp, and the next rows brought into the caches instead of registers.
-template <int SB, int NW, int MINB = kWarpsPerSM / NW>
+template <int SB, int NW, int MINB = kWarpsPerSM / NW, bool RAGGED = false>
 __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a) {
   constexpr int PL = 32 / SB, R = 8 / SB, RS = 32 + SB, kThreads = 32 * NW;
   constexpr bool kLean = MINB * NW > kWarpsPerSM;
   constexpr int kBufs = kLean ? 1 : 2;  // exchange buffers per warp
   extern __shared__ double2 smem[];
   __shared__ int s_item, s_last;
+  __shared__ FusedView s_view;  // a ragged launch: the current item's plan
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ws = warp / a.WP, wp = warp - ws * a.WP;  // state group, pole group of this warp
   const int ST = a.WS * SB;                           // states per CTA tile
-  const int lmax = a.lmax, N = a.N, B = a.B;
+  const int lmax = a.lmax;
   const int ACS = lmax * kStreams + 1;                // running-sum plane stride
-  const int64_t NS = a.nspec, NR = a.nrows, P = a.P;
   double2 *acc = smem;                                                           // [WP * ST][ACS]
   double2 *wbase = smem + (size_t)a.WP * ST * ACS + (size_t)warp * kBufs * R * RS;  // [kBufs][R][RS]
   double2 *ybuf = a.ybuf + ((size_t)blockIdx.x * NW + warp) * (size_t)lmax * 32 + lane;
@@ -127,12 +141,20 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
     __syncthreads();
     if (it >= a.nitems) break;
     const int4 item = a.items[it];
-    const int4 sy = a.sys[item.x];
+    if constexpr (RAGGED) {
+      if (threadIdx.x == 0) s_view = a.views[item.z >> 8];
+      __syncthreads();
+    }
+    const FusedView &V = pick_view<RAGGED>(a.v, s_view);
+    const int gi = RAGGED ? (item.z & 255) : item.z;  // the item's pole group
+    const int N = V.N, B = V.B;
+    const int64_t NS = V.nspec, NR = V.nrows, P = V.P;
+    const int4 sy = V.sys[item.x];
     const int m = sy.x, n0 = sy.y, len = sy.z;
     const int64_t row0 = sy.w;
     const int p = item.x & 1, b0 = item.y;
-    const int kg0 = a.pole_begin + item.z * a.gsz;       // this CTA's poles [kg0, kg1)
-    const int kg1 = min(a.pole_end, kg0 + a.gsz);
+    const int kg0 = V.pole_begin + gi * V.gsz;  // this CTA's poles [kg0, kg1)
+    const int kg1 = min(V.pole_end, kg0 + V.gsz);
     const int64_t base_idx = (int64_t)m * (2 * N + 3 - m) / 2 - m;  // idx(m, n) = base_idx + n
     const int nmin = m > 1 ? m : 1;
 
@@ -146,7 +168,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
     if (len > 0) {
       const int bsw = b0 + ws * SB + s_sw;  // the sweep lane's state (clamped for loads)
       const int bq = bsw < B ? bsw : b0;
-      const double2 *sPhi = a.sin + bq, *sZeta = a.sin + NS * B + bq, *sDel = a.sin + 2 * NS * B + bq;
+      const double2 *sPhi = V.sin + bq, *sZeta = V.sin + NS * B + bq, *sDel = V.sin + 2 * NS * B + bq;
       const int npp = a.WP * PL;  // poles per CTA pass
       const int nr = (len + R - 1) / R;  // task rounds of the backward sweep
       for (int kb = kg0; kb < kg1; kb += npp) {
@@ -155,11 +177,11 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
         if (npa <= 0) continue;
         const bool active = pl < npa;              // inactive lanes repeat a valid pole, add zero
         const int k = kw + min(pl, npa - 1);
-        const double2 *fL = a.fac + ((int64_t)F_L * NR + row0) * P + k;
-        const double2 *fG = a.fac + ((int64_t)F_G * NR + row0) * P + k;
-        const double2 *fE = a.fac + ((int64_t)F_E * NR + row0) * P + k;
-        const double2 *fF = a.fac + ((int64_t)F_F * NR + row0) * P + k;
-        const double2 *fC = a.fac + ((int64_t)F_C * NR + row0) * P + k;
+        const double2 *fL = V.fac + ((int64_t)F_L * NR + row0) * P + k;
+        const double2 *fG = V.fac + ((int64_t)F_G * NR + row0) * P + k;
+        const double2 *fE = V.fac + ((int64_t)F_E * NR + row0) * P + k;
+        const double2 *fF = V.fac + ((int64_t)F_F * NR + row0) * P + k;
+        const double2 *fC = V.fac + ((int64_t)F_C * NR + row0) * P + k;
 
         // ---- forward sweep, two rows per iteration: the next row's factors and states
         // are loaded while the current row computes (two register sets, no copies)
@@ -253,7 +275,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
           const int iv = len - 1 - rr * R - t_r;  // the row this lane sums (< 0: none)
           const int ii = max(iv, 0);
           double2 *ap = acc + ((size_t)wp * ST + ws * SB + t_s) * ACS + ii * kStreams + t_t;
-          const double2 *W = a.fac + ((int64_t)t_comp * NR + row0 + ii) * P + kw;
+          const double2 *W = V.fac + ((int64_t)t_comp * NR + row0 + ii) * P + kw;
           const double2 *wv = wbuf + t_r * RS + t_s * (PL + 1);
           double2 s = *ap;
 #pragma unroll
@@ -277,7 +299,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
           const int iv = len - 1 - rr * R - tr;
           const int ii = max(iv, 0);
           double2 *ap = acc + ((size_t)wp * ST + ws * SB + t_s) * ACS + ii * kStreams + t_t;
-          const double2 *W = a.fac + ((int64_t)t_comp * NR + row0 + ii) * P + kw;
+          const double2 *W = V.fac + ((int64_t)t_comp * NR + row0 + ii) * P + kw;
           const double2 *wv = wbuf + tr * RS + t_s * (PL + 1) + h * QH;
           double2 s = h == 0 ? *ap : make_double2(0.0, 0.0);
 #pragma unroll
@@ -349,8 +371,8 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
     // depend on which CTA comes last.
     const int64_t PS = NR * kStreams;  // one state's partial sums of one group
     const double2 *pg = nullptr;       // the tile's partials at this system (NG > 1, last CTA)
-    if (a.NG > 1) {
-      double2 *mine = a.part + ((size_t)(b0 / ST) * a.NG + item.z) * ST * PS + row0 * kStreams;
+    if (V.NG > 1) {
+      double2 *mine = V.part + ((size_t)(b0 / ST) * V.NG + gi) * ST * PS + row0 * kStreams;
       for (int q = threadIdx.x; q < ST * len * kStreams; q += kThreads) {
         const int st = q / (len * kStreams), r = q - st * (len * kStreams);
         double2 v = make_double2(0.0, 0.0);
@@ -363,11 +385,11 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
       }
       __threadfence();  // the partials are visible device-wide before the arrival counts
       __syncthreads();
-      if (threadIdx.x == 0) s_last = atomicAdd(a.arrivals + item.w, 1u) == (unsigned)(a.NG - 1);
+      if (threadIdx.x == 0) s_last = atomicAdd(V.arrivals + item.w, 1u) == (unsigned)(V.NG - 1);
       __syncthreads();
       if (!s_last) continue;  // block-uniform
       __threadfence();
-      pg = a.part + (size_t)(b0 / ST) * a.NG * ST * PS + row0 * kStreams;
+      pg = V.part + (size_t)(b0 / ST) * V.NG * ST * PS + row0 * kStreams;
     }
 
     // ---- outputs of this item: delta and Phi at the degrees of parity p, zeta at the
@@ -383,7 +405,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
         auto sumacc = [&](int i, int t) {
           double2 v = make_double2(0.0, 0.0);
           if (pg) {  // the groups' partials, from L2 (written by other SMs)
-            for (int g = 0; g < a.NG; ++g) {
+            for (int g = 0; g < V.NG; ++g) {
               const double2 u = __ldcg(pg + ((size_t)g * ST + st) * PS + i * kStreams + t);
               v.x += u.x;
               v.y += u.y;
@@ -404,13 +426,13 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
           const bool row = n >= n0 && i < len;
           double2 dl = row ? sumacc(i, 0) : make_double2(0.0, 0.0);
           double2 ph = row ? sumacc(i, 1) : make_double2(0.0, 0.0);
-          ph = cfma_(ph, a.sphi, a.sin[ix * B + b]);
-          if (a.realm0 && m == 0) {
+          ph = cfma_(ph, V.sphi, V.sin[ix * B + b]);
+          if (V.realm0 && m == 0) {
             dl.y = 0.0;
             ph.y = 0.0;
           }
-          a.sout[ix * B + b] = ph;
-          a.sout[(2 * NS + ix) * B + b] = dl;
+          V.sout[ix * B + b] = ph;
+          V.sout[(2 * NS + ix) * B + b] = dl;
         } else {
           const int n = m + 1 - p + 2 * (jj - nown);
           const int64_t ix = base_idx + n;
@@ -423,10 +445,10 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
               ze.x += u.x;
               ze.y += u.y;
             }
-            ze = cfma_(ze, a.wz[ix], a.sin[(NS + ix) * B + b]);
-            if (a.realm0 && m == 0) ze.y = 0.0;
+            ze = cfma_(ze, V.wz[ix], V.sin[(NS + ix) * B + b]);
+            if (V.realm0 && m == 0) ze.y = 0.0;
           }
-          a.sout[(NS + ix) * B + b] = ze;
+          V.sout[(NS + ix) * B + b] = ze;
         }
       }
     }
@@ -585,34 +607,43 @@ bool build_fused_layout(Plan &pl, int B, int tile, bool lean, int groups, FusedL
   return true;
 }
 
+// the per-plan arguments of a fused solve of B states of plan pl with layout F
+FusedView fused_view(Plan &pl, const FusedLayout &F, bool adjoint, const double2 *sin, double2 *sout, int B,
+                     unsigned *arrivals, double2 *part) {
+  FusedView v;
+  v.fac = adjoint ? pl.fac_adj : pl.fac_fwd;
+  v.sin = sin;
+  v.sout = sout;
+  v.sys = pl.sys_dev;
+  v.wz = adjoint ? pl.w_adj : pl.w_fwd;
+  v.sphi = adjoint ? pl.sphi_adj : pl.sphi_fwd;
+  v.arrivals = arrivals;
+  v.part = part;
+  v.P = pl.P;
+  v.N = pl.N;
+  v.B = B;
+  v.pole_begin = 0;
+  v.pole_end = pl.P;
+  v.realm0 = 1;
+  v.NG = F.ng;
+  v.gsz = F.gsz;
+  v.nspec = pl.nspec;
+  v.nrows = pl.nrows;
+  return v;
+}
+
 cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, const double2 *sin, double2 *sout,
                                int B, cudaStream_t st) {
   FusedArgs a;
-  a.fac = adjoint ? pl.fac_adj : pl.fac_fwd;
-  a.sin = sin;
-  a.sout = sout;
+  a.v = fused_view(pl, F, adjoint, sin, sout, B, F.sync_dev + 1, F.part_dev);
+  a.views = nullptr;
   a.ybuf = pl.yscratch;  // sized for 16 warps x 2 poles per SM: eight warps of one pole here
-  a.sys = pl.sys_dev;
   a.items = F.items_dev;
   a.counter = F.sync_dev;
-  a.arrivals = F.sync_dev + 1;
-  a.part = F.part_dev;
-  a.NG = F.ng;
-  a.gsz = F.gsz;
-  a.wz = adjoint ? pl.w_adj : pl.w_fwd;
-  a.sphi = adjoint ? pl.sphi_adj : pl.sphi_fwd;
   a.nitems = F.nitems;
-  a.P = pl.P;
-  a.N = pl.N;
-  a.B = B;
   a.WS = F.ws;
   a.WP = F.wp;
   a.lmax = pl.lmax;
-  a.pole_begin = 0;
-  a.pole_end = pl.P;
-  a.realm0 = 1;
-  a.nspec = pl.nspec;
-  a.nrows = pl.nrows;
   cudaError_t e = cudaMemsetAsync(F.sync_dev, 0, (size_t)(1 + (F.ng > 1 ? F.ntiles : 0)) * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const int grid = pl.num_sms * F.per_sm;
@@ -631,6 +662,100 @@ cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, con
     e = F.sb == 4 ? go(solve_fused_kernel<4, 8>) : F.sb == 2 ? go(solve_fused_kernel<2, 8>) : go(solve_fused_kernel<1, 8>);
   }
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+
+// ---- ragged launches: the fused solve over the states of several plans -----------------
+// One persistent launch of the lean form (tiles of 2 states, four warps per CTA) over the
+// merged work list of every plan's (system, tile) items, longest (rows x poles) first; each
+// item names its plan, whose arguments the CTA reads from a per-plan view.  One pole group
+// per tile: the merged list is long enough to balance the SMs.  Needs the largest plan's
+// running sums to leave three CTAs per SM; returns false otherwise (the slot path serves).
+bool build_fused_ragged(const std::vector<Plan *> &plans, const std::vector<int> &counts, FusedRagged &R) {
+  R = FusedRagged{};
+  int lmax = 1;
+  for (size_t p = 0; p < plans.size(); ++p)
+    if (counts[p] > 0) {
+      if (plans[p]->ff) return false;
+      lmax = std::max(lmax, plans[p]->lmax);
+    }
+  const int dev = plans[0]->device;
+  int smem_max = 0, smem_sm = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const int st = 2, sb = 1, ws = 2, wp = 2, nw = 4;
+  const size_t smem = ((size_t)wp * st * (lmax * kStreams + 1) + (size_t)nw * 1 * (8 / sb) * (32 + sb)) * sizeof(double2);
+  if (smem + 1024 > (size_t)smem_max) return false;
+  const int per_sm = std::min<int>(4, (int)(smem_sm / (smem + 1024)));
+  if (per_sm < 3) return false;
+  const int smem_opt = smem_max - 1024;
+  cudaError_t e = per_sm == 4 ? cudaFuncSetAttribute(solve_fused_kernel<1, 4, 4, true>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opt)
+                              : cudaFuncSetAttribute(solve_fused_kernel<1, 4, 3, true>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opt);
+  if (e != cudaSuccess) return false;
+  // one pole group per tile: gsz covers every pole
+  FusedLayout F1;
+  F1.ng = 1;
+  std::vector<FusedView> views(plans.size());
+  struct Keyed { int4 it; double work; };
+  std::vector<Keyed> keyed;
+  for (size_t p = 0; p < plans.size(); ++p) {
+    if (counts[p] == 0) continue;
+    Plan &pl = *plans[p];
+    F1.gsz = pl.P;
+    views[p] = fused_view(pl, F1, false, pl.s_in, pl.s_out, counts[p], nullptr, nullptr);
+    int ti = 0;
+    for (int m = 0; m <= pl.N; ++m)
+      for (int par = 0; par < 2; ++par)
+        for (int b0 = 0; b0 < counts[p]; b0 += st, ++ti)
+          keyed.push_back(Keyed{make_int4(2 * m + par, b0, (int)(p << 8), ti), (double)pl.sys[2 * m + par].len * pl.P});
+  }
+  std::stable_sort(keyed.begin(), keyed.end(), [](const Keyed &x, const Keyed &y) { return x.work > y.work; });
+  std::vector<int4> items;
+  for (const Keyed &k : keyed) items.push_back(k.it);
+  R.nitems = (int)items.size();
+  R.nviews = (int)views.size();
+  R.lmax = lmax;
+  R.per_sm = per_sm;
+  R.smem = smem;
+  R.ws = ws;
+  R.wp = wp;
+  e = cudaMalloc(&R.views_dev, views.size() * sizeof(FusedView));
+  if (e == cudaSuccess) e = cudaMemcpy(R.views_dev, views.data(), views.size() * sizeof(FusedView), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&R.items_dev, std::max<size_t>(1, items.size()) * sizeof(int4));
+  if (e == cudaSuccess) e = cudaMemcpy(R.items_dev, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&R.counter, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    free_fused_ragged(R);
+    return false;
+  }
+  return true;
+}
+
+void free_fused_ragged(FusedRagged &R) {
+  if (R.views_dev) cudaFree(R.views_dev);
+  if (R.items_dev) cudaFree(R.items_dev);
+  if (R.counter) cudaFree(R.counter);
+  R = FusedRagged{};
+}
+
+cudaError_t launch_fused_ragged(const FusedRagged &R, double2 *ybuf, int num_sms, cudaStream_t st) {
+  FusedArgs a{};
+  a.views = static_cast<const FusedView *>(R.views_dev);
+  a.ybuf = ybuf;
+  a.items = R.items_dev;
+  a.counter = R.counter;
+  a.nitems = R.nitems;
+  a.WS = R.ws;
+  a.WP = R.wp;
+  a.lmax = R.lmax;
+  cudaError_t e = cudaMemsetAsync(R.counter, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const int grid = num_sms * R.per_sm;
+  if (R.per_sm == 4) solve_fused_kernel<1, 4, 4, true><<<grid, 128, R.smem, st>>>(a);
+  else solve_fused_kernel<1, 4, 3, true><<<grid, 128, R.smem, st>>>(a);
   return cudaGetLastError();
 }
 
