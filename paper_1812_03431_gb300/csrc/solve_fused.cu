@@ -165,7 +165,9 @@ __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a)
     }
     __syncthreads();
 
-    if (len > 0) {
+    // a warp group whose states all lie past the batch (the last tile of an odd batch)
+    // skips the sweeps: its running sums stay zero and no output of it is written
+    if (len > 0 && b0 + ws * SB < B) {
       const int bsw = b0 + ws * SB + s_sw;  // the sweep lane's state (clamped for loads)
       const int bq = bsw < B ? bsw : b0;
       const double2 *sPhi = V.sin + bq, *sZeta = V.sin + NS * B + bq, *sDel = V.sin + 2 * NS * B + bq;
