@@ -39,6 +39,9 @@
  *   is allocated inside rexi_step / rexi_step_adjoint once a batch size has
  *   been seen by the plan (its work list is cached), so those calls can be
  *   captured in a CUDA graph after a first eager call with the same batch.
+ *   Such a graph holds that batch's solve layout: rexi_tune or
+ *   rexi_set_pole_slots for the batch afterwards frees it, and the graph must be
+ *   captured again.
  *   A plan's workspaces (transposed states, Fourier data, slot partials) serve
  *   one call at a time: calls on one plan must be ordered on the GPU (one
  *   stream, or events between streams); independent plans may run
