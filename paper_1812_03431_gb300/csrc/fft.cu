@@ -324,7 +324,13 @@ FftArgs make_args(const Plan &pl, int B) {
   a.N = pl.N;
   a.nlat = pl.nlat;
   a.ncol = 3 * B;
-  a.np = pl.fft.nsplit;
+  // rows per CTA: the plan's nsplit (its shared memory holds that many), spread evenly
+  // over the fewest CTAs a latitude needs, so that a small batch does not transform rows
+  // of zeros (one state at T63: 3 rows, not 21)
+  {
+    const int nblk = (a.ncol + pl.fft.nsplit - 1) / pl.fft.nsplit;
+    a.np = (a.ncol + nblk - 1) / nblk;
+  }
   {
     int Ns = 1;
     for (int s = 0; s < a.nstages; ++s) {
