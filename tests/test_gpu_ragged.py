@@ -115,6 +115,35 @@ def test_ragged_rebuilds_after_a_plan_is_retuned(env):
         plan.close()
 
 
+def test_ragged_with_a_plan_left_out_and_odd_counts(env):
+    # a call in which one plan has no states, then one with odd counts (the last tile of
+    # each plan half empty), against each plan's own step and the oracle
+    torch, rexi = env
+    plans = [rexi.Plan(N, *grid_of(N), M=K, tau=1200.0, max_batch=5, layout="spectral")
+             for N, K in ((63, 128), (127, 128), (63, 256))]
+    rg = rexi.Ragged(plans, 8)
+    for state_plan in ([2, 2, 0], [0, 1, 1, 1, 2, 0, 1, 2]):
+        Ns = [63 if p != 1 else 127 for p in state_plan]
+        states = [torch.from_numpy(inputs.random_spectral(N, 1, 4000 + s)[0]).cuda() for s, N in enumerate(Ns)]
+        outs = [torch.empty_like(x) for x in states]
+        rg.step(states, outs, state_plan)
+        torch.cuda.synchronize()
+        for p, plan in enumerate(plans):
+            idx = [s for s in range(len(state_plan)) if state_plan[s] == p]
+            if not idx:
+                continue
+            Y = plan.step(torch.stack([states[s] for s in idx])).cpu().numpy()
+            for r, s in enumerate(idx):
+                assert rel(outs[s].cpu().numpy(), Y[r]) < 1e-13
+        s = state_plan.index(0)
+        al, be = plans[0].coefficients()
+        ref = ostep.rexi_step_spectral(states[s].cpu().numpy()[None], 63, al, be, 1200.0, C)[0]
+        assert max(rel(outs[s].cpu().numpy()[f], ref[f]) for f in range(3)) < TOL
+    rg.close()
+    for plan in plans:
+        plan.close()
+
+
 @pytest.mark.parametrize("shape,precision,groups", [(None, "fp64", 0), (2, "fp64", 1), (3, "mixed", 0),
                                                     (0, "mixed", 0), (2, "fp64", 3)])
 def test_step_in_cuda_graph(env, shape, precision, groups):
