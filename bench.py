@@ -62,10 +62,11 @@ FLOPS_PER_ROW = 72  # FP64 flops per (state, pole, row) of the fused solve: 36 F
 FF_OPS_PER_ROW = 36 * 12
 # DRAM bytes (read + write) of one solve launch from ncu captures (K=256, batch 16), keyed by
 # (truncation, pole slots or, for the fused solve, states per CTA tile, layout shape):
-# shape 0/1 the slot kernel, 2/3 the fused solve's register/lean form with one pole group.
+# shape 0/1 the slot kernel, 2/3/4 the fused solve's register form, lean form, lean form on
+# two-warp CTAs, with one pole group.
 # A workload without its own capture takes the nearest layout captured at T170, scaled by
 # rows (traffic per row is constant).  Re-captured after each change of the solve kernels.
-SOLVE_TRAFFIC = {(341, 64, 0): 48.82e9, (341, 2, 3): 18.60e9,
+SOLVE_TRAFFIC = {(341, 64, 0): 48.82e9, (341, 2, 3): 18.60e9, (341, 2, 4): 27.86e9,
                  (170, 32, 0): 12.64e9, (170, 32, 1): 12.58e9, (170, 64, 0): 11.63e9,
                  (170, 2, 2): 1.64e9, (170, 2, 3): 4.92e9}
 SOLVE_FF_TRAFFIC_T170 = {(32, 0): 11.64e9}  # the float-float kernel (solve_kernel<true>)
@@ -97,10 +98,10 @@ def measured_peaks():
 
 def solve_layout(r):
     """The tuned solve layout of a form's record: pole slots and shape, or for the fused
-    solve (shapes 2 and 3) its CTA tile and the CTAs that split each tile's poles."""
-    if r["shape"] in (2, 3):
-        return {"fused": "lean" if r["shape"] == 3 else "register", "tile": r["slots"] % 256,
-                "pole_groups": r["slots"] // 256, "layout_shape": r["shape"]}
+    solve (shapes 2 to 4) its form, CTA tile and the CTAs that split each tile's poles."""
+    if r["shape"] in (2, 3, 4):
+        return {"fused": {2: "register", 3: "lean", 4: "lean, two-warp CTAs"}[r["shape"]],
+                "tile": r["slots"] % 256, "pole_groups": r["slots"] // 256, "layout_shape": r["shape"]}
     return {"pole_slots": r["slots"], "layout_shape": r["shape"]}
 
 
@@ -589,7 +590,7 @@ def main():
         peak_source = ("measured: rexi_measure_fp64_fma, best of 5 per shape (FP64 FMA chains)" if fp64_tf else
                        "derived: 152 SMs x 2 FP64 FMA/clk x sm_max_mhz")
     achieved = amount / (solve_ms * 1e-3) / 1e12
-    fused = r["shape"] in (2, 3)
+    fused = r["shape"] in (2, 3, 4)
     # the fused solve's slot count packs its CTA tile and pole groups (tile + 256 x groups)
     tile_or_slots, groups = (r["slots"] % 256, r["slots"] // 256) if fused else (r["slots"], 1)
     tkey, traffic = None, None
@@ -630,7 +631,7 @@ def main():
                      "achieved": achieved, "peak": peak, "unit": roof_unit, "frac": achieved / peak,
                      "traffic": traffic,
                      "traffic_source": ("ncu dram bytes at T%d/K256/B16, %d pole slots (fused: states per tile), "
-                                        "layout shape %d (shapes 2 and 3 = fused; the bench's layout: %d, shape %d, "
+                                        "layout shape %d (shapes 2 to 4 = fused; the bench's layout: %d, shape %d, "
                                         "%d pole group(s))%s" % (tkey[0], tkey[1], tkey[2], tile_or_slots, r["shape"],
                                                                  groups, "" if tkey[0] == W["N"] else
                                                                  ", scaled by rows to T%d" % W["N"]))

@@ -263,10 +263,10 @@ rexi_status rexi_get_coefficients(const rexi_plan *plan, double *alpha, double *
  * applies (binary64 delta solver on the rotating sphere), shape 2: the fused solve
  * with the pole sum on chip and no slots, in CTA tiles of 32 down to 2 states (down to
  * 1 for batches of 1 and 2) and, for batches up to 8, with each tile's poles split over
- * 1, 2, 3, 4, 6 or 8 CTAs, and shape 3: its lean form (see rexi_set_pole_slots).  Keeps
- * the fastest for later steps with this batch (the fused solve unless a slot layout is
- * more than 0.5 % faster: it needs no reduction) and writes its slot count (for shapes 2
- * and 3: tile + 256 x pole groups, as rexi_set_pole_slots takes it) to *slots and its
+ * 1, 2, 3, 4, 6 or 8 CTAs, and shapes 3 and 4: its lean forms (see rexi_set_pole_slots).
+ * Keeps the fastest for later steps with this batch (the fused solve unless a slot layout
+ * is more than 0.5 % faster: it needs no reduction) and writes its slot count (for shapes
+ * 2 to 4: tile + 256 x pole groups, as rexi_set_pole_slots takes it) to *slots and its
  * shape to *shape (either may be NULL).  Synchronous; uses the plan's workspaces, so no
  * step of this plan may be in flight. */
 rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots, int32_t *shape);
@@ -281,8 +281,11 @@ rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots, int32_t *s
  * than one only when a batch is too small to fill the GPU; a request is capped at the
  * passes), the last CTA of a tile to finish adding the groups' partial sums in group
  * order, or shape 3 for its lean form (three or four CTAs of four warps per SM, fewer
- * registers, the next rows prefetched into the caches), REXI_EINVAL where that does not
- * apply; the slot count used (for shapes 2 and 3: the tile + 256 x the groups) is
+ * registers, the next rows prefetched into the caches; tiles of up to 8 states), or shape
+ * 4 for the lean form on CTAs of two warps (seven or eight per SM; tiles of up to 4
+ * states; a tile of 2 states puts each state on a warp of its own, so no CTA splits its
+ * poles over warps), REXI_EINVAL where that does not apply; the slot count used (for
+ * shapes 2 to 4: the tile + 256 x the groups) is
  * written to *used (may be NULL).  Results are deterministic for any layout; only the
  * order of the final pole sum changes.  Synchronous, like rexi_tune. */
 rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t shape, int32_t *used);

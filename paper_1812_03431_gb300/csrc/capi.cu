@@ -471,14 +471,14 @@ rexi_status rexi_tune(rexi_plan *plan, int32_t batch, int32_t *slots, int32_t *s
 rexi_status rexi_set_pole_slots(rexi_plan *plan, int32_t batch, int32_t slots, int32_t shape, int32_t *used) {
   if (!plan || !plan->pl) { set_error("null plan"); return REXI_EINVAL; }
   Plan &pl = *plan->pl;
-  if (batch < 1 || batch > pl.prm.max_batch || (shape < 2 && slots < 1) || slots < 0 || shape < 0 || shape > 3) {
-    set_error("rexi_set_pole_slots: batch must be in [1, max_batch], shape 0 to 3, slots >= 1 for "
-              "shapes 0 and 1 and >= 0 for shapes 2 and 3");
+  if (batch < 1 || batch > pl.prm.max_batch || (shape < 2 && slots < 1) || slots < 0 || shape < 0 || shape > 4) {
+    set_error("rexi_set_pole_slots: batch must be in [1, max_batch], shape 0 to 4, slots >= 1 for "
+              "shapes 0 and 1 and >= 0 for shapes 2 to 4");
     return REXI_EINVAL;
   }
   if (pl.prm.fsphere) {  // no banded solves, no layout
     if (shape >= 2) {
-      set_error("rexi_set_pole_slots: the fused solve (shapes 2 and 3) does not apply to f-sphere plans");
+      set_error("rexi_set_pole_slots: the fused solve (shapes 2 to 4) does not apply to f-sphere plans");
       return REXI_EINVAL;
     }
     if (used) *used = 0;

@@ -541,10 +541,10 @@ const FusedLayout *fused_layout(Plan &pl, int B) {
   if (it == pl.fused.end()) {
     FusedLayout F;
     auto ft = pl.fused_tile.find(B);
-    auto fl = pl.fused_lean.find(B);
+    auto ff = pl.fused_form.find(B);
     auto fg = pl.fused_groups.find(B);
     if (!build_fused_layout(pl, B, ft != pl.fused_tile.end() ? ft->second : 0,
-                            fl != pl.fused_lean.end() && fl->second, fg != pl.fused_groups.end() ? fg->second : 0, F))
+                            ff != pl.fused_form.end() ? ff->second : 0, fg != pl.fused_groups.end() ? fg->second : 0, F))
       F = FusedLayout{};
     it = pl.fused.emplace(B, F).first;  // st == 0: not available
   }
@@ -552,28 +552,29 @@ const FusedLayout *fused_layout(Plan &pl, int B) {
 }
 
 // the fused layout for batch B with a requested CTA tile and number of pole groups (0:
-// the defaults) and form, replacing any earlier one
-const FusedLayout *set_fused_tile(Plan &pl, int B, int tile, bool lean = false, int groups = 0) {
+// the defaults) and form (0: register; lean with CTAs of 1: four, 2: two warps),
+// replacing any earlier one
+const FusedLayout *set_fused_tile(Plan &pl, int B, int tile, int form = 0, int groups = 0) {
   auto it = pl.fused.find(B);
   if (it != pl.fused.end()) {
     free_fused_layout(it->second);
     pl.fused.erase(it);
   }
   pl.fused_tile[B] = tile;
-  pl.fused_lean[B] = lean;
+  pl.fused_form[B] = form;
   pl.fused_groups[B] = groups;
   return fused_layout(pl, B);
 }
 
 // A given slot count for batch B: the layout with slots / kk pole groups replaces any
-// earlier one for that batch.  Shapes 2 and 3 select the fused solve instead (REXI_EINVAL
+// earlier one for that batch.  Shapes 2, 3 and 4 select the fused solve instead (REXI_EINVAL
 // where it does not apply), with slots = tile + 256 x pole groups.
 rexi_status set_layout(Plan &pl, int B, int slots, int shape, int *used) {
-  if (shape == 2 || shape == 3) {
+  if (shape >= 2 && shape <= 4) {
     pl.use_slots[B] = false;
-    if (!set_fused_tile(pl, B, slots % 256, shape == 3, slots / 256)) {
+    if (!set_fused_tile(pl, B, slots % 256, shape - 2, slots / 256)) {
       pl.use_slots[B] = true;
-      set_error("rexi_set_pole_slots: the fused solve (shapes 2 and 3) needs binary64 solves of the delta "
+      set_error("rexi_set_pole_slots: the fused solve (shapes 2, 3 and 4) needs binary64 solves of the delta "
                 "solver on the rotating sphere, with running sums that fit in shared memory");
       return REXI_EINVAL;
     }
@@ -661,13 +662,13 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
   float fused_ms = 1e30f;
   int best_tile = 0, best_groups = 1;
   pl.use_slots[B] = false;
-  bool best_lean = false;
+  int best_form = 0;
   for (int tile = 32; tile >= 1; tile /= 2) {
-    for (int lean = 0; lean < 2; ++lean) {
+    for (int form = 0; form < 3; ++form) {
       std::vector<int> seen;
       for (int groups : {0, 1, 2, 3, 4, 6, 8}) {  // 0: the default count
         if (groups > 2 && B > 8) break;  // larger batches leave fewer schedulers idle
-        const FusedLayout *F = set_fused_tile(pl, B, tile, lean != 0, groups);
+        const FusedLayout *F = set_fused_tile(pl, B, tile, form, groups);
         if (!F || F->st != tile) break;  // the default is smaller, or it does not fit
         if (std::find(seen.begin(), seen.end(), F->ng) != seen.end()) continue;  // capped at the passes
         seen.push_back(F->ng);
@@ -680,14 +681,14 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
         if (ms < fused_ms) {
           fused_ms = ms;
           best_tile = tile;
-          best_lean = lean != 0;
+          best_form = form;
           best_groups = F->ng;
         }
       }
     }
     if (tile <= 2 && tile < B) break;  // smaller tiles only re-read the factors more often
   }
-  if (best_tile > 0) set_fused_tile(pl, B, best_tile, best_lean, best_groups);
+  if (best_tile > 0) set_fused_tile(pl, B, best_tile, best_form, best_groups);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   auto it = pl.layouts.find(B);
@@ -702,7 +703,7 @@ rexi_status tune_layout(Plan &pl, int B, int *slots_out, int *shape_out) {
   const bool fused_wins = fused_ms <= best * 1.005f;
   pl.use_slots[B] = !fused_wins;
   if (slots_out) *slots_out = fused_wins ? best_tile + 256 * best_groups : bestL.slots;
-  if (shape_out) *shape_out = fused_wins ? (best_lean ? 3 : 2) : bestL.shape;
+  if (shape_out) *shape_out = fused_wins ? 2 + best_form : bestL.shape;
   return REXI_OK;
 }
 

@@ -99,8 +99,8 @@ struct SolveLayout {
 // 2 m + p, first state, pole group, (system, tile) index), longest first.
 struct FusedLayout {
   int sb = 0, ws = 0, wp = 0, st = 0;
-  int nw = 8;       // warps per CTA: 8 (one CTA per SM) or 4 (two CTAs per SM, or the lean form)
-  int per_sm = 1;   // CTAs per SM (lean form: 3 or 4)
+  int nw = 8;       // warps per CTA: 8 (one CTA per SM), 4 (two per SM, or the lean form) or 2 (lean)
+  int per_sm = 1;   // CTAs per SM (lean form: 3 or 4 of four warps, 7 or 8 of two)
   int ng = 1, gsz = 0;  // pole groups per (system, tile) and poles per group
   int ntiles = 0;       // (system, tile) pairs
   int nitems = 0;
@@ -240,7 +240,7 @@ struct Plan {
   std::map<int, FusedLayout> fused;
   std::map<int, bool> use_slots;
   std::map<int, int> fused_tile;  // requested states per CTA tile (0: the default)
-  std::map<int, bool> fused_lean; // the lean form (three or four CTAs of four warps per SM)
+  std::map<int, int> fused_form;  // 0: register form; lean form with CTAs of 1: four warps, 2: two warps
   std::map<int, int> fused_groups; // requested CTAs per system's poles (0: the default)
 
   // optional per-stage timing with CUDA events on the launching stream
@@ -291,7 +291,7 @@ SolveView make_view(Plan &pl, const SolveLayout &lay, bool adjoint, const double
                     int pole_begin, int pole_end);
 // fused solve: eligible plans (binary64 delta solver on the rotating sphere) whose running
 // sums fit in shared memory; sin -> sout ([3][nspec][B]) with no partial sums and no reduction
-bool build_fused_layout(Plan &pl, int B, int tile, bool lean, int groups, FusedLayout &F);
+bool build_fused_layout(Plan &pl, int B, int tile, int form, int groups, FusedLayout &F);
 bool build_fused_ragged(const std::vector<Plan *> &plans, const std::vector<int> &counts, FusedRagged &R);
 void free_fused_ragged(FusedRagged &R);
 cudaError_t launch_fused_ragged(const FusedRagged &R, double2 *ybuf, int num_sms, cudaStream_t st);

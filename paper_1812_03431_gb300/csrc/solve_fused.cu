@@ -109,9 +109,10 @@ struct FwdRow {
 //
 // MINB CTAs per SM.  MINB = kWarpsPerSM / NW: the running sums and two exchange buffers per
 // warp, and the next rows' factors, states and sweep values prefetched into registers
-// (up to 222 registers).  MINB > 2 (four warps per CTA, three or four CTAs per SM): the
-// lean form for 12 or 16 warps per SM -- registers capped at 170 or 128, one exchange
-// buffer per warp, and the next rows brought into the caches instead of registers.
+// (up to 222 registers).  MINB x NW > kWarpsPerSM (three or four CTAs of four warps, or
+// seven or eight of two, per SM): the lean form for 12 to 16 warps per SM -- registers
+// capped at 170, 146 or 128, one exchange buffer per warp, and the next rows brought into
+// the caches instead of registers.
 template <int SB, int NW, int MINB = kWarpsPerSM / NW, bool RAGGED = false>
 __global__ void __launch_bounds__(32 * NW, MINB) solve_fused_kernel(FusedArgs a) {
   constexpr int PL = 32 / SB, R = 8 / SB, RS = 32 + SB, kThreads = 32 * NW;
@@ -475,7 +476,7 @@ void free_fused_layout(FusedLayout &F) {
 // factor once per tile.  `groups` CTAs (0: the default below) split each (system, tile)'s
 // poles in whole passes.  Returns false when the running sums of a tile do not fit in
 // shared memory (the slot-partial path then serves the plan).
-bool build_fused_layout(Plan &pl, int B, int tile, bool lean, int groups, FusedLayout &F) {
+bool build_fused_layout(Plan &pl, int B, int tile, int form, int groups, FusedLayout &F) {
   F = FusedLayout{};
   int st = 1;
   while (st < B && st < 32) st *= 2;
@@ -489,21 +490,23 @@ bool build_fused_layout(Plan &pl, int B, int tile, bool lean, int groups, FusedL
     return ((size_t)wp * t * (pl.lmax * kStreams + 1) + (size_t)nw * bufs * (8 / sb) * (32 + sb)) * sizeof(double2);
   };
   for (; st >= 1; st /= 2) {
-    if (lean) {
-      // four-warp CTAs, one exchange buffer per warp, as many CTAs per SM (4 or 3) as fit
+    if (form != 0) {
+      // lean: CTAs of four warps (form 1; 4 or 3 per SM) or two warps (form 2; 8 or 7 per
+      // SM), one exchange buffer per warp, as many CTAs per SM as fit
+      const int nwl = form == 2 ? 2 : 4;
       int sb, ws, wp;
-      if (st >= 4) { sb = st / 4; ws = 4; wp = 1; }
-      else { sb = 1; ws = st; wp = 4 / st; }
+      if (st >= nwl) { sb = st / nwl; ws = nwl; wp = 1; }
+      else { sb = 1; ws = st; wp = nwl / st; }
       if (sb > 2) continue;
-      const size_t smem = smem_of(4, sb, wp, st, 1);
+      const size_t smem = smem_of(nwl, sb, wp, st, 1);
       if (smem + 1024 > (size_t)smem_max) continue;
-      const int per_sm = std::min<int>(4, (int)(smem_sm / (smem + 1024)));
-      if (per_sm < 3) continue;
+      const int per_sm = std::min<int>(2 * kWarpsPerSM / nwl, (int)(smem_sm / (smem + 1024)));
+      if (per_sm < (nwl == 2 ? 7 : 3)) continue;
       F.sb = sb;
       F.ws = ws;
       F.wp = wp;
       F.st = st;
-      F.nw = 4;
+      F.nw = nwl;
       F.per_sm = per_sm;
       F.smem = smem;
       break;
@@ -542,7 +545,9 @@ bool build_fused_layout(Plan &pl, int B, int tile, bool lean, int groups, FusedL
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opt);
   };
   cudaError_t ea;
-  if (F.per_sm == 4) ea = F.sb == 2 ? allow(solve_fused_kernel<2, 4, 4>) : allow(solve_fused_kernel<1, 4, 4>);
+  if (F.nw == 2 && F.per_sm == 8) ea = F.sb == 2 ? allow(solve_fused_kernel<2, 2, 8>) : allow(solve_fused_kernel<1, 2, 8>);
+  else if (F.nw == 2) ea = F.sb == 2 ? allow(solve_fused_kernel<2, 2, 7>) : allow(solve_fused_kernel<1, 2, 7>);
+  else if (F.per_sm == 4) ea = F.sb == 2 ? allow(solve_fused_kernel<2, 4, 4>) : allow(solve_fused_kernel<1, 4, 4>);
   else if (F.per_sm == 3) ea = F.sb == 2 ? allow(solve_fused_kernel<2, 4, 3>) : allow(solve_fused_kernel<1, 4, 3>);
   else if (F.nw == 4)
     ea = F.sb == 4 ? allow(solve_fused_kernel<4, 4>) : F.sb == 2 ? allow(solve_fused_kernel<2, 4>)
@@ -654,7 +659,11 @@ cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, con
     kernel<<<grid, 32 * F.nw, smem, st>>>(a);
     return cudaSuccess;
   };
-  if (F.per_sm == 4) {
+  if (F.nw == 2 && F.per_sm == 8) {
+    e = F.sb == 2 ? go(solve_fused_kernel<2, 2, 8>) : go(solve_fused_kernel<1, 2, 8>);
+  } else if (F.nw == 2) {
+    e = F.sb == 2 ? go(solve_fused_kernel<2, 2, 7>) : go(solve_fused_kernel<1, 2, 7>);
+  } else if (F.per_sm == 4) {
     e = F.sb == 2 ? go(solve_fused_kernel<2, 4, 4>) : go(solve_fused_kernel<1, 4, 4>);
   } else if (F.per_sm == 3) {
     e = F.sb == 2 ? go(solve_fused_kernel<2, 4, 3>) : go(solve_fused_kernel<1, 4, 3>);

@@ -33,9 +33,9 @@ def main():
     ap.add_argument("--solve-arith", default="fp64", choices=["fp64", "fp32x2"])
     ap.add_argument("--layout-shape", type=int, default=-1,
                     help="with --pole-slots: 0 same pole groups for every order, 1 proportional to length; "
-                         "2 (3: lean) the fused solve with --pole-slots states per CTA tile")
+                         "2 (3: lean, 4: lean on two-warp CTAs) the fused solve with --pole-slots states per CTA tile")
     ap.add_argument("--pole-groups", type=int, default=0,
-                    help="with layout shapes 2 and 3: CTAs per tile's poles (0: the default)")
+                    help="with layout shapes 2 to 4: CTAs per tile's poles (0: the default)")
     args = ap.parse_args()
     import torch
 

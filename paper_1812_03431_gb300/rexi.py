@@ -283,8 +283,8 @@ class Plan:
 
     def tune(self, batch, cache=None):
         """rexi_tune: time the solve and reduction for several pole-group counts and both
-        slot-layout shapes at this batch size, and the fused solve (shape 2, no slots) where
-        it applies, and keep the fastest; returns the chosen number of pole slots (for the
+        slot-layout shapes at this batch size, and the fused solve (shapes 2 to 4, no slots)
+        where it applies, and keep the fastest; returns the chosen number of pole slots (for the
         fused solve its tile + 256 x its pole groups; the shape is kept in
         ``self.layout_shape[batch]``).
 
@@ -313,10 +313,10 @@ class Plan:
     def set_pole_slots(self, batch, slots, shape=0, groups=0):
         """rexi_set_pole_slots: use this pole-slot count and layout shape (0: the same groups
         for every zonal order, 1: in proportion to the system length) for this batch size,
-        or shape 2 (3: its lean form): the fused solve with ``slots`` states per CTA tile
-        (0: default) and each tile's poles split over ``groups`` CTAs (0: default).  For
-        shapes 2 and 3 returns tile + 256 x groups as used (``slots`` may carry that packing
-        itself, as rexi_tune returns it)."""
+        or shape 2 (3: its lean form, 4: the lean form on two-warp CTAs): the fused solve with
+        ``slots`` states per CTA tile (0: default) and each tile's poles split over ``groups``
+        CTAs (0: default).  For shapes 2 to 4 returns tile + 256 x groups as used (``slots``
+        may carry that packing itself, as rexi_tune returns it)."""
         n = _I32()
         if shape >= 2:
             slots = slots + 256 * groups

@@ -1,6 +1,7 @@
 """The fused solve (the beta-weighted pole sum kept on chip, Sec. 5 / Algorithm 1) against the
 oracle and against the pole-slot solve with its separate reduction, over every CTA shape
-it takes: tiles of 1, 2, 4, 8 and 16 states (warps split over poles or states), ragged
+it takes: tiles of 1, 2, 4, 8 and 16 states (warps split over poles or states), CTAs of
+eight, four and two warps, ragged
 state tiles, pole counts below and above a warp's pole lanes, truncations up to the
 largest whose running sums fit in shared memory."""
 import numpy as np
@@ -69,6 +70,14 @@ def test_fused_step_matches_oracle_and_slot_solve(N, M, B, tau):
     plan.set_pole_slots(B, lt, 3, groups=2)
     lean2 = plan.step(x).cpu().numpy()
     assert fieldwise(lean2, fused) < 1e-13
+    # the lean form on CTAs of two warps (seven or eight per SM): a tile of two states or
+    # fewer has no pole split over warps; larger tiles hold two states per warp
+    for groups in (1, 3):
+        lw = plan.set_pole_slots(B, tile, 4, groups=groups) % 256
+        assert 1 <= lw <= min(tile, 4)
+        two = plan.step(x).cpu().numpy()
+        np.testing.assert_array_equal(plan.step(x).cpu().numpy(), two)
+        assert fieldwise(two, fused) < 1e-13
     plan.set_pole_slots(B, 8, 0)  # the pole-slot solve and its reduction
     slot = plan.step(x).cpu().numpy()
     plan.close()
@@ -148,7 +157,7 @@ def test_fused_not_offered_where_it_does_not_apply():
         plan.close()
 
 
-@pytest.mark.parametrize("shape", [2, 3])
+@pytest.mark.parametrize("shape", [2, 3, 4])
 def test_fused_adjoint_matches_oracle(shape):
     import torch
     from paper_1812_03431_gb300 import rexi
@@ -166,7 +175,7 @@ def test_fused_adjoint_matches_oracle(shape):
     assert fieldwise(got, ref) < TOL
 
 
-@pytest.mark.parametrize("shape", [2, 3])
+@pytest.mark.parametrize("shape", [2, 3, 4])
 def test_fused_grid_mixed_step_matches_oracle(shape):
     # the chosen form's arithmetic (tcgen05 Legendre transforms, binary64 solves) with the
     # fused solve, against the oracle's grid step
