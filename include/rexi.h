@@ -300,8 +300,8 @@ rexi_status rexi_plan_info(const rexi_plan *plan, int64_t *info, int32_t n);
  * work list of every plan's items sorted longest first (Sec. 5: every (pole, m)
  * system is independent).  With binary64 solves that launch is the fused solve:
  * items are (system, tile of 2 states, plan), the pole sum stays on chip and no
- * reduction follows, provided the largest plan's running sums leave three CTAs per
- * SM.  Otherwise (and with float-float solves) it is the pole-slot solve over
+ * reduction follows, provided the largest plan's running sums leave seven CTAs of two
+ * warps, or three of four warps, per SM.  Otherwise (and with float-float solves) it is the pole-slot solve over
  * (m, pole group, state group, plan) items, then each plan's reduction.  Plans must use
  * REXI_SPECTRAL, the rotating sphere and REXI_SOLVER_DELTA; the ragged object
  * keeps pointers to them (destroy it first).

@@ -2,7 +2,7 @@
 // whose banded solves run as ONE persistent launch over the union of their work
 // items, sorted longest first (the per-item plan index selects factors, layout and
 // buffers).  Inputs are gathered into each plan's internal layout and results
-// scattered back by small per-state kernels; after a first call with the same
+// scattered back, up to 32 states per launch; after a first call with the same
 // per-plan state counts nothing is allocated, so the step can be captured in a
 // CUDA graph.
 #include <cuda_runtime.h>
@@ -41,14 +41,54 @@ struct rexi_ragged {
 namespace rexi {
 namespace {
 
-// s_int[(f * nspec + idx) * B + b] <-> state[f * nspec + idx]
-__global__ void gather_state_kernel(const double2 *state, double2 *sint, int64_t n3, int B, int b) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += (int64_t)gridDim.x * blockDim.x)
-    sint[t * B + b] = state[t];
+// s_int[(f * nspec + idx) * B + b] <-> state[f * nspec + idx], for up to kMoveChunk states
+// per launch (blockIdx.y), their pointers passed by value so that a captured graph keeps them
+constexpr int kMoveChunk = 32;
+struct StateMoves {
+  const double2 *src[kMoveChunk];
+  double2 *dst[kMoveChunk];
+  int64_t n3[kMoveChunk];
+  int B[kMoveChunk], b[kMoveChunk];
+};
+template <bool kGather>
+__global__ void move_states_kernel(StateMoves m) {
+  const int s = blockIdx.y;
+  const int64_t n3 = m.n3[s];
+  const int B = m.B[s], b = m.b[s];
+  const double2 *src = m.src[s];
+  double2 *dst = m.dst[s];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += (int64_t)gridDim.x * blockDim.x) {
+    if (kGather) dst[t * B + b] = src[t];
+    else dst[t] = src[t * B + b];
+  }
 }
-__global__ void scatter_state_kernel(const double2 *sint, double2 *state, int64_t n3, int B, int b) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += (int64_t)gridDim.x * blockDim.x)
-    state[t] = sint[t * B + b];
+
+// every state into (gather) or out of (scatter) its plan's internal layout, in launches of
+// up to kMoveChunk states
+cudaError_t move_states(const std::vector<Plan *> &plans, const void *const *ext, const int32_t *state_plan,
+                        int nstates, const std::vector<int> &counts, const std::vector<int> &rank, bool gather,
+                        cudaStream_t st) {
+  for (int s0 = 0; s0 < nstates; s0 += kMoveChunk) {
+    const int n = std::min(kMoveChunk, nstates - s0);
+    StateMoves m{};
+    int64_t n3max = 1;
+    for (int i = 0; i < n; ++i) {
+      const int s = s0 + i, p = state_plan[s];
+      Plan &pl = *plans[p];
+      m.n3[i] = 3 * pl.nspec;
+      m.B[i] = counts[p];
+      m.b[i] = rank[s];
+      m.src[i] = gather ? static_cast<const double2 *>(ext[s]) : pl.s_out;
+      m.dst[i] = gather ? pl.s_in : static_cast<double2 *>(const_cast<void *>(ext[s]));
+      n3max = std::max(n3max, m.n3[i]);
+    }
+    const dim3 grid((unsigned)std::min<int64_t>((n3max + 255) / 256, 512), (unsigned)n);
+    if (gather) move_states_kernel<true><<<grid, 256, 0, st>>>(m);
+    else move_states_kernel<false><<<grid, 256, 0, st>>>(m);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 rexi_status fail(const std::string &what, cudaError_t e) {
@@ -183,14 +223,7 @@ rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *c
     it = rg->cfgs.emplace(counts, cfg).first;
   }
   const rexi_ragged::Cfg &cfg = it->second;
-  cudaError_t e = cudaSuccess;
-  for (int s = 0; s < nstates && e == cudaSuccess; ++s) {
-    Plan &pl = *rg->plans[state_plan[s]];
-    const int64_t n3 = 3 * pl.nspec;
-    gather_state_kernel<<<(unsigned)std::min<int64_t>((n3 + 255) / 256, 1024), 256, 0, st>>>(
-        static_cast<const double2 *>(in_dev[s]), pl.s_in, n3, counts[state_plan[s]], rank[s]);
-    e = cudaGetLastError();
-  }
+  cudaError_t e = move_states(rg->plans, in_dev, state_plan, nstates, counts, rank, true, st);
   const bool ff = rg->plans[0]->ff;
   if (cfg.fused) {
     if (e == cudaSuccess) e = launch_fused_ragged(cfg.fr, rg->ybuf, rg->plans[0]->num_sms, st);
@@ -208,13 +241,9 @@ rexi_status rexi_ragged_step(rexi_ragged *rg, const void *const *in_dev, void *c
         e = launch_reduce(*rg->plans[p], *lays[p], false, rg->plans[p]->s_in, rg->plans[p]->s_out, counts[p],
                           false, 0, st);
   }
-  for (int s = 0; s < nstates && e == cudaSuccess; ++s) {
-    Plan &pl = *rg->plans[state_plan[s]];
-    const int64_t n3 = 3 * pl.nspec;
-    scatter_state_kernel<<<(unsigned)std::min<int64_t>((n3 + 255) / 256, 1024), 256, 0, st>>>(
-        pl.s_out, static_cast<double2 *>(out_dev[s]), n3, counts[state_plan[s]], rank[s]);
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess)
+    e = move_states(rg->plans, reinterpret_cast<const void *const *>(out_dev), state_plan, nstates, counts, rank,
+                    false, st);
   return e == cudaSuccess ? REXI_OK : fail("launch", e);
 }
 

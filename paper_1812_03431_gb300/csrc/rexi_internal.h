@@ -116,7 +116,7 @@ struct FusedRagged {
   void *views_dev = nullptr;  // per plan (solve_fused.cu's FusedView)
   int4 *items_dev = nullptr;
   unsigned *counter = nullptr;
-  int nitems = 0, nviews = 0, lmax = 0, per_sm = 0, ws = 0, wp = 0;
+  int nitems = 0, nviews = 0, lmax = 0, per_sm = 0, ws = 0, wp = 0, nw = 4;
   size_t smem = 0;
 };
 

@@ -678,11 +678,12 @@ cudaError_t launch_solve_fused(Plan &pl, const FusedLayout &F, bool adjoint, con
 
 
 // ---- ragged launches: the fused solve over the states of several plans -----------------
-// One persistent launch of the lean form (tiles of 2 states, four warps per CTA) over the
-// merged work list of every plan's (system, tile) items, longest (rows x poles) first; each
-// item names its plan, whose arguments the CTA reads from a per-plan view.  One pole group
-// per tile: the merged list is long enough to balance the SMs.  Needs the largest plan's
-// running sums to leave three CTAs per SM; returns false otherwise (the slot path serves).
+// One persistent launch of the lean form (tiles of 2 states; CTAs of two warps, else four)
+// over the merged work list of every plan's (system, tile) items, longest (rows x poles)
+// first; each item names its plan, whose arguments the CTA reads from a per-plan view.  One
+// pole group per tile: the merged list is long enough to balance the SMs.  Needs the
+// largest plan's running sums to leave seven two-warp or three four-warp CTAs per SM;
+// returns false otherwise (the slot path serves).
 bool build_fused_ragged(const std::vector<Plan *> &plans, const std::vector<int> &counts, FusedRagged &R) {
   R = FusedRagged{};
   int lmax = 1;
@@ -695,16 +696,32 @@ bool build_fused_ragged(const std::vector<Plan *> &plans, const std::vector<int>
   int smem_max = 0, smem_sm = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  const int st = 2, sb = 1, ws = 2, wp = 2, nw = 4;
-  const size_t smem = ((size_t)wp * st * (lmax * kStreams + 1) + (size_t)nw * 1 * (8 / sb) * (32 + sb)) * sizeof(double2);
-  if (smem + 1024 > (size_t)smem_max) return false;
-  const int per_sm = std::min<int>(4, (int)(smem_sm / (smem + 1024)));
-  if (per_sm < 3) return false;
+  // CTAs of two warps (one state each, seven or eight per SM) where they fit, else of four
+  // warps (two per state, splitting its poles; three or four per SM)
+  int nw = 0, per_sm = 0, wp = 0;
+  size_t smem = 0;
+  const int st = 2, sb = 1, ws = 2;
+  for (int nwc : {2, 4}) {
+    const int wpc = nwc / st;
+    const size_t sm = ((size_t)wpc * st * (lmax * kStreams + 1) + (size_t)nwc * 1 * (8 / sb) * (32 + sb)) * sizeof(double2);
+    if (sm + 1024 > (size_t)smem_max) continue;
+    const int ps = std::min<int>(2 * kWarpsPerSM / nwc, (int)(smem_sm / (sm + 1024)));
+    if (ps < (nwc == 2 ? 7 : 3)) continue;
+    nw = nwc;
+    per_sm = ps;
+    wp = wpc;
+    smem = sm;
+    break;
+  }
+  if (nw == 0) return false;
   const int smem_opt = smem_max - 1024;
-  cudaError_t e = per_sm == 4 ? cudaFuncSetAttribute(solve_fused_kernel<1, 4, 4, true>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opt)
-                              : cudaFuncSetAttribute(solve_fused_kernel<1, 4, 3, true>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opt);
+  cudaError_t e;
+  if (nw == 2)
+    e = per_sm == 8 ? cudaFuncSetAttribute(solve_fused_kernel<1, 2, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opt)
+                    : cudaFuncSetAttribute(solve_fused_kernel<1, 2, 7, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opt);
+  else
+    e = per_sm == 4 ? cudaFuncSetAttribute(solve_fused_kernel<1, 4, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opt)
+                    : cudaFuncSetAttribute(solve_fused_kernel<1, 4, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_opt);
   if (e != cudaSuccess) return false;
   // one pole group per tile: gsz covers every pole
   FusedLayout F1;
@@ -733,6 +750,7 @@ bool build_fused_ragged(const std::vector<Plan *> &plans, const std::vector<int>
   R.smem = smem;
   R.ws = ws;
   R.wp = wp;
+  R.nw = nw;
   e = cudaMalloc(&R.views_dev, views.size() * sizeof(FusedView));
   if (e == cudaSuccess) e = cudaMemcpy(R.views_dev, views.data(), views.size() * sizeof(FusedView), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&R.items_dev, std::max<size_t>(1, items.size()) * sizeof(int4));
@@ -765,7 +783,9 @@ cudaError_t launch_fused_ragged(const FusedRagged &R, double2 *ybuf, int num_sms
   cudaError_t e = cudaMemsetAsync(R.counter, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const int grid = num_sms * R.per_sm;
-  if (R.per_sm == 4) solve_fused_kernel<1, 4, 4, true><<<grid, 128, R.smem, st>>>(a);
+  if (R.nw == 2 && R.per_sm == 8) solve_fused_kernel<1, 2, 8, true><<<grid, 64, R.smem, st>>>(a);
+  else if (R.nw == 2) solve_fused_kernel<1, 2, 7, true><<<grid, 64, R.smem, st>>>(a);
+  else if (R.per_sm == 4) solve_fused_kernel<1, 4, 4, true><<<grid, 128, R.smem, st>>>(a);
   else solve_fused_kernel<1, 4, 3, true><<<grid, 128, R.smem, st>>>(a);
   return cudaGetLastError();
 }
