@@ -372,8 +372,16 @@ __global__ void __launch_bounds__(THREADS) leg_ana_tc_kernel(TcArgs a) {
 }
 
 // ---- synthesis ------------------------------------------------------------------------
-// dynamic smem: [A: 8 x 16 KiB][B1_0, B1_1: (hi, lo) 8G x 32][B2_0, B2_1: (hi, lo) 4G x 32]
-__global__ void __launch_bounds__(THREADS, 1) leg_syn_tc_kernel(TcArgs a) {  // one CTA per SM (shared memory)
+// Two accumulator classes per tile: class c holds the Pbar rows of parity c against B1_c
+// (Phi, psi', chi' of degrees n - m = c mod 2) and the H rows of parity 1 - c against B2_c
+// (psi', chi' of the other parity); north and south are their sum and difference.
+// SPLIT = false: each degree block stages both classes, dynamic smem [A: 8 x 16 KiB]
+// [B1_0, B1_1: (hi, lo) 8G x 32][B2_0, B2_1: (hi, lo) 4G x 32], one CTA per SM.
+// SPLIT = true (groups of up to 8 states): each block is staged one class at a time, smem
+// [A: 4 x 16 KiB][B1: (hi, lo) 8G x 32][B2: (hi, lo) 4G x 32], so that two CTAs fit on
+// an SM and one fetches tables while the other converts and multiplies.
+template <bool SPLIT>
+__global__ void __launch_bounds__(THREADS, SPLIT ? 2 : 1) leg_syn_tc_kernel(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -385,9 +393,10 @@ __global__ void __launch_bounds__(THREADS, 1) leg_syn_tc_kernel(TcArgs a) {  // 
   const int L0 = (a.N - m) / 2 + 1;                    // degrees with n - m even
   const int L1 = (a.N - m - 1) >= 0 ? (a.N - m - 1) / 2 + 1 : 0;
   const int nkb = (max(L0, L1) + KB - 1) / KB;
+  constexpr int kCls = SPLIT ? 1 : 2;                  // classes staged per iteration
   unsigned char *sA = sm;
-  unsigned char *sB1 = sm + 8 * SUB;                   // class s at sB1 + s * 2 * N1 * KB * 4
-  unsigned char *sB2 = sB1 + 2 * (2 * N1 * KB * 4);    // class s at sB2 + s * 2 * N2 * KB * 4
+  unsigned char *sB1 = sm + 4 * kCls * SUB;            // class slot s at sB1 + s * 2 * N1 * KB * 4
+  unsigned char *sB2 = sB1 + kCls * (2 * N1 * KB * 4); // class slot s at sB2 + s * 2 * N2 * KB * 4
   const int tid = threadIdx.x, warp = tid >> 5;
   uint32_t ncols = 32;
   while (ncols < (uint32_t)(2 * (N1 + N2))) ncols <<= 1;
@@ -402,13 +411,26 @@ __global__ void __launch_bounds__(THREADS, 1) leg_syn_tc_kernel(TcArgs a) {  // 
   const uint32_t tbase = tmem_base;
   const int64_t idx0 = (int64_t)m * (2 * a.N + 3 - m) / 2;
   bool ok = true;
-  for (int kb = 0; kb < nkb; ++kb) {
+  const int nit = SPLIT ? 2 * nkb : nkb;
+  for (int it = 0; it < nit; ++it) {
+    const int kb = SPLIT ? it >> 1 : it;
+    const int c0 = SPLIT ? (it & 1) : 0;  // the (first) class of this iteration
     const uint4 *src = reinterpret_cast<const uint4 *>(a.tab + (blk0 + kb) * (int64_t)(8 * SUB / 4));
     uint4 *dstA = reinterpret_cast<uint4 *>(sA);
-    for (int t = tid; t < 8 * SUB / 16; t += THREADS) cp_async16(dstA + t, src + t);
+    if constexpr (SPLIT) {
+      // class c0: sub-tiles Pbar parity c0 (2 c0, 2 c0 + 1) and H parity 1 - c0 (4 + 2 (1 - c0), +1)
+      const uint4 *srcP = src + (2 * c0) * (SUB / 16), *srcH = src + (4 + 2 * (1 - c0)) * (SUB / 16);
+      for (int t = tid; t < 2 * SUB / 16; t += THREADS) {
+        cp_async16(dstA + t, srcP + t);
+        cp_async16(dstA + 2 * SUB / 16 + t, srcH + t);
+      }
+    } else {
+      for (int t = tid; t < 8 * SUB / 16; t += THREADS) cp_async16(dstA + t, src + t);
+    }
     // spectral data: unit = (parity q, 4 degrees kq, state bl, field f in Phi, psi', chi',
     // pad); rows i = kb*32 + 4 kq + r have n = m + q + 2 i.  P-terms feed class q (B1_q),
-    // H-terms (psi', chi') class 1 - q (B2_{1-q}); all loads are issued first.
+    // H-terms (psi', chi') class 1 - q (B2_{1-q}); with SPLIT only those of class c0 are
+    // loaded and staged.  All loads are issued first.
     {
       constexpr int RMAX = 1024 / THREADS;  // 2 q x 8 kq x 4 G <= 1024
       const int nun = 2 * (KB / 4) * 4 * G;
@@ -425,9 +447,11 @@ __global__ void __launch_bounds__(THREADS, 1) leg_syn_tc_kernel(TcArgs a) {  // 
         const int kq = u2 / (4 * G), rem = u2 - kq * (4 * G), bl = rem >> 2, f = rem & 3;
         const int b = b0 + bl;
 #pragma unroll
+        const bool need = !SPLIT || q == c0 || f == 1 || f == 2;
+#pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int n = m + q + 2 * (kb * KB + 4 * kq + r);
-          const bool v = u < nun && f < 3 && n <= a.N && b < a.B;
+          const bool v = need && u < nun && f < 3 && n <= a.N && b < a.B;
           const int64_t ix = v ? idx0 + (n - m) : 0;
           xr[rr][r] = a.sint[((int64_t)(v ? f : 0) * a.nspec + ix) * a.B + (v ? b : 0)];
           zr[rr][r] = f > 0 ? a.zd[ix] : 1.0;
@@ -455,14 +479,17 @@ __global__ void __launch_bounds__(THREADS, 1) leg_syn_tc_kernel(TcArgs a) {  // 
           split_tf32f(xv[rr][r].x, hi[0][r], lo[0][r]);
           split_tf32f(xv[rr][r].y, hi[1][r], lo[1][r]);
         }
-        unsigned char *b1 = sB1 + q * (2 * N1 * KB * 4);
-        unsigned char *b2 = sB2 + (1 - q) * (2 * N2 * KB * 4);
+        const bool w1 = !SPLIT || q == c0, w2 = !SPLIT || 1 - q == c0;  // B1 of class q, B2 of class 1 - q
+        unsigned char *b1 = sB1 + (SPLIT ? 0 : q) * (2 * N1 * KB * 4);
+        unsigned char *b2 = sB2 + (SPLIT ? 0 : 1 - q) * (2 * N2 * KB * 4);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const uint32_t off = core_off(8 * bl + 2 * f + c, 4 * kq, N1 / 8);
-          *reinterpret_cast<uint4 *>(b1 + off) = make_uint4(hi[c][0], hi[c][1], hi[c][2], hi[c][3]);
-          *reinterpret_cast<uint4 *>(b1 + N1 * KB * 4 + off) = make_uint4(lo[c][0], lo[c][1], lo[c][2], lo[c][3]);
-          if (f == 1 || f == 2) {
+          if (w1) {
+            *reinterpret_cast<uint4 *>(b1 + off) = make_uint4(hi[c][0], hi[c][1], hi[c][2], hi[c][3]);
+            *reinterpret_cast<uint4 *>(b1 + N1 * KB * 4 + off) = make_uint4(lo[c][0], lo[c][1], lo[c][2], lo[c][3]);
+          }
+          if (w2 && (f == 1 || f == 2)) {
             const uint32_t off2 = core_off(4 * bl + 2 * (f - 1) + c, 4 * kq, N2 / 8);
             *reinterpret_cast<uint4 *>(b2 + off2) = make_uint4(hi[c][0], hi[c][1], hi[c][2], hi[c][3]);
             *reinterpret_cast<uint4 *>(b2 + N2 * KB * 4 + off2) =
@@ -479,12 +506,14 @@ __global__ void __launch_bounds__(THREADS, 1) leg_syn_tc_kernel(TcArgs a) {  // 
       const uint32_t idesc1 = make_idesc(TM, N1), idesc2 = make_idesc(TM, N2);
       const uint32_t lboA = (TM / 8) * 128, lbo1 = (N1 / 8) * 128, lbo2 = (N2 / 8) * 128;
       const uint32_t A0 = smem_u32(sA);
-      for (int cls = 0; cls < 2; ++cls) {
+      for (int cs = 0; cs < kCls; ++cs) {
         // class cls: Pbar rows of parity cls with B1_cls; H rows of parity 1 - cls with B2_cls
-        const uint32_t aP = A0 + (2 * cls) * SUB, aPl = aP + SUB;
-        const uint32_t aH = A0 + (4 + 2 * (1 - cls)) * SUB, aHl = aH + SUB;
-        const uint32_t b1 = smem_u32(sB1 + cls * (2 * N1 * KB * 4)), b1l = b1 + N1 * KB * 4;
-        const uint32_t b2 = smem_u32(sB2 + cls * (2 * N2 * KB * 4)), b2l = b2 + N2 * KB * 4;
+        // (SPLIT: the staged class sits in slot 0, its Pbar tiles then its H tiles)
+        const int cls = c0 + cs;
+        const uint32_t aP = A0 + (SPLIT ? 0 : 2 * cls) * SUB, aPl = aP + SUB;
+        const uint32_t aH = A0 + (SPLIT ? 2 : 4 + 2 * (1 - cls)) * SUB, aHl = aH + SUB;
+        const uint32_t b1 = smem_u32(sB1 + cs * (2 * N1 * KB * 4)), b1l = b1 + N1 * KB * 4;
+        const uint32_t b2 = smem_u32(sB2 + cs * (2 * N2 * KB * 4)), b2l = b2 + N2 * KB * 4;
         const uint32_t d1 = tbase + cls * (N1 + N2), d2 = d1 + N1;
         for (int s = 0; s < KB / 8; ++s) {
           const uint32_t oA = 2 * s * lboA, o1 = 2 * s * lbo1, o2 = 2 * s * lbo2;
@@ -499,7 +528,7 @@ __global__ void __launch_bounds__(THREADS, 1) leg_syn_tc_kernel(TcArgs a) {  // 
       }
       mma_commit(&mbar);
     }
-    if (!mbar_wait(&mbar, (uint32_t)(kb & 1))) ok = false;
+    if (!mbar_wait(&mbar, (uint32_t)(it & 1))) ok = false;
     tc_fence_after();
     ok = __syncthreads_and(ok) != 0;  // block-uniform, so every thread leaves the loop together
     if (!ok) break;
@@ -571,7 +600,18 @@ __global__ void __launch_bounds__(THREADS, 1) leg_syn_tc_kernel(TcArgs a) {  // 
 int group_size(int B) { return std::min(B, 16) + (4 - std::min(B, 16) % 4) % 4; }
 
 size_t ana_smem(int G) { return 4 * (size_t)SUB + 2 * (8 * G) * KB * 4 + 2 * (4 * G) * KB * 4; }
-size_t syn_smem(int G) { return 8 * (size_t)SUB + 2 * (2 * (8 * G) * KB * 4) + 2 * (2 * (4 * G) * KB * 4); }
+// The synthesis stages one accumulator class per block iteration (two CTAs per SM) when
+//  - two CTAs' tensor-memory accumulators (2 classes x 12 G columns each, rounded up to a
+//    power of two) fit in the SM's 512 columns: groups of up to 8 states, and
+//  - the grid has at least three CTAs per SM, so that CTAs do share SMs.  With fewer, the
+//    split only doubles each CTA's chain of table fetches and MMA round trips (measured,
+//    T170 one state, 171 CTAs: 0.0335 against 0.0242 ms; T255 one state, 512 CTAs: 0.0609
+//    against 0.0669 ms; T1279 one state: 3.77 against 4.24 ms).
+bool syn_split(int G, int64_t ncta, int num_sms) { return G <= 8 && ncta >= 3 * (int64_t)num_sms; }
+size_t syn_smem(int G, bool split) {
+  const int cls = split ? 1 : 2;
+  return 4 * (size_t)cls * SUB + cls * (2 * (8 * G) * KB * 4) + cls * (2 * (4 * G) * KB * 4);
+}
 
 }  // namespace
 
@@ -634,7 +674,11 @@ cudaError_t tc_setup(Plan &pl) {
   if ((e = cudaFuncSetAttribute(leg_ana_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)ana_smem(Gmax))))
     return e;
-  return cudaFuncSetAttribute(leg_syn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syn_smem(Gmax));
+  if ((e = cudaFuncSetAttribute(leg_syn_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)syn_smem(std::min(Gmax, 8), true))))
+    return e;
+  return cudaFuncSetAttribute(leg_syn_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)syn_smem(Gmax, false));
 }
 
 cudaError_t launch_leg_ana_tc(Plan &pl, const double2 *four, double2 *sint, int B, const double *zd,
@@ -654,7 +698,10 @@ cudaError_t launch_leg_syn_tc(Plan &pl, const double2 *sint, double2 *four, int 
   TcArgs a{pl.tc_tab_syn, pl.tc_work_syn, reinterpret_cast<float2 *>(four), const_cast<double2 *>(sint), zd,
            pl.dev_err, pl.N, pl.nlat, pl.J, B, G, 0, pl.nspec};
   dim3 grid((unsigned)pl.tc_nwork_syn, (unsigned)((B + G - 1) / G));
-  leg_syn_tc_kernel<<<grid, THREADS, syn_smem(G), st>>>(a);
+  if (syn_split(G, (int64_t)grid.x * grid.y, pl.num_sms))
+    leg_syn_tc_kernel<true><<<grid, THREADS, syn_smem(G, true), st>>>(a);
+  else
+    leg_syn_tc_kernel<false><<<grid, THREADS, syn_smem(G, false), st>>>(a);
   return cudaGetLastError();
 }
 

@@ -93,3 +93,27 @@ def test_c2_batched_mixed_vs_fp64(env):
         worst = max(rel(out["mixed", arith][b, f], out["fp64", "fp64"][b, f]) for b in range(B) for f in range(3))
         assert worst < TOL_MIXED
     assert rel(out["mixed", "fp32x2"], out["mixed", "fp64"]) < 1e-11
+
+
+def test_mixed_synthesis_staged_by_class_matches_oracle(env):
+    """The tcgen05 synthesis stages one accumulator class per degree block (two CTAs per SM)
+    for groups of up to 8 states on grids of at least three CTAs per SM, else both classes
+    per block.  T255 (512 work tiles): 2 states take the first way, 12 the second; both
+    against the oracle's synthesis, and against each other (the same products in the same
+    order per state)."""
+    torch, rexi = env
+    N, nlat, nlon, B = 255, 384, 768, 12
+    gs = ostep.GridStep(N, nlat, nlon, np.ones(1, complex), np.ones(1, complex), 1.0, C)
+    plan = rexi.Plan(N, nlat, nlon, M=8, max_batch=B, precision="mixed")
+    S = inputs.random_spectral(N, B, 31)
+    ref = gs.synthesise(S)
+    x2 = plan.synthesize(torch.from_numpy(S[:2]).cuda()).cpu().numpy()
+    x12 = plan.synthesize(torch.from_numpy(S).cuda()).cpu().numpy()
+    plan.check_device()
+    plan.close()
+    for f in range(3):
+        for b in range(2):
+            assert rel(x2[b, f], ref[b, f]) < TOL_MIXED
+        for b in range(B):
+            assert rel(x12[b, f], ref[b, f]) < TOL_MIXED
+    assert rel(x2, x12[:2]) < 1e-6
