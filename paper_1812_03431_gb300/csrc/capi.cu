@@ -160,8 +160,11 @@ rexi_status core(Plan &pl, int B, bool adjoint, cudaStream_t st, Marks &mk) {
 }
 
 rexi_status analyze(Plan &pl, const double *grid, int B, bool adjoint, cudaStream_t st, Marks &mk) {
-  const double *isc = adjoint ? pl.scale_syn_out : pl.scale_ana_in;
-  const double *msc = adjoint ? pl.mscale_c : pl.mscale_fwd;
+  const bool f32 = pl.prm.precision == REXI_MIXED;  // the mixed form's FFTs scale in binary32
+  const void *isc = adjoint ? (f32 ? (const void *)pl.scale_syn_out32 : pl.scale_syn_out)
+                            : (f32 ? (const void *)pl.scale_ana_in32 : pl.scale_ana_in);
+  const void *msc = adjoint ? (f32 ? (const void *)pl.mscale_c32 : pl.mscale_c)
+                            : (f32 ? (const void *)pl.mscale_fwd32 : pl.mscale_fwd);
   const double *zd = adjoint ? pl.zd_ana_adj : pl.zd_one;
   mk.mark(ST_FFT_FWD);
   cudaError_t e = launch_fft_fwd(pl, grid, pl.four, B, isc, msc, st);
@@ -176,8 +179,11 @@ rexi_status analyze(Plan &pl, const double *grid, int B, bool adjoint, cudaStrea
 rexi_status synthesize(Plan &pl, const double2 *spec, double *grid, int B, bool adjoint,
                        cudaStream_t st, Marks &mk) {
   const double *zd = adjoint ? pl.zd_mone : pl.zd_syn;
-  const double *msc = adjoint ? pl.mscale_adj : pl.mscale_one;
-  const double *osc = adjoint ? pl.scale_ana_in : pl.scale_syn_out;
+  const bool f32 = pl.prm.precision == REXI_MIXED;
+  const void *msc = adjoint ? (f32 ? (const void *)pl.mscale_adj32 : pl.mscale_adj)
+                            : (f32 ? (const void *)pl.mscale_one32 : pl.mscale_one);
+  const void *osc = adjoint ? (f32 ? (const void *)pl.scale_ana_in32 : pl.scale_ana_in)
+                            : (f32 ? (const void *)pl.scale_syn_out32 : pl.scale_syn_out);
   mk.mark(ST_LEG_SYN);
   cudaError_t e = pl.prm.precision == REXI_MIXED ? launch_leg_syn_tc(pl, spec, pl.four, B, zd, st)
                                                  : launch_leg_syn(pl, spec, pl.four, B, zd, st);

@@ -16,8 +16,9 @@
 // Layouts: grid [B][3][nlat][nlon] float64; Fourier [nlat][N+1][3B] complex (FP64 in
 // the FP64 form, FP32 in the mixed form, where the transform itself is FP32), column
 // c = 3 b + field, so that for each latitude the Legendre kernels read contiguous
-// columns.  The mixed form scales in FP32 and converts between FP64 and FP32 on the
-// integer pipe (f64_to_f32 / f32_to_f64): no FP64 instruction is left in its kernels.
+// columns.  The mixed form scales in FP32 (scales rounded to binary32 once, at plan time)
+// and converts the data between FP64 and FP32 on the integer pipe (f64_to_f32 /
+// f32_to_f64): no FP64 instruction is left in its kernels.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -166,11 +167,10 @@ __device__ typename V2<T>::t *fft_smem(typename V2<T>::t *buf0, typename V2<T>::
   return src;
 }
 
-// T: arithmetic type inside the transform (double, or float in the mixed form);
-// grid and Fourier arrays stay FP64 either way.
+// T: arithmetic type inside the transform (double, or float in the mixed form, whose
+// Fourier array is FP32); the grid stays FP64 either way, and the scales come in type T.
 template <typename T>
-__global__ void fft_fwd_kernel(FftArgs a, const double *grid, void *four_v, const double *in_scale,
-                               const double *m_scale) {
+__global__ void fft_fwd_kernel(FftArgs a, const double *grid, void *four_v, const T *in_scale, const T *m_scale) {
   using C = typename V2<T>::t;
   constexpr bool F32 = std::is_same<T, float>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -188,7 +188,7 @@ __global__ void fft_fwd_kernel(FftArgs a, const double *grid, void *four_v, cons
   constexpr int kLd = 8;
   for (int t0 = 0; t0 < a.np * h; t0 += kLd * blockDim.x) {
     double2 x[kLd];
-    double sv[kLd];
+    T sv[kLd];
     bool ok[kLd];
 #pragma unroll
     for (int i = 0; i < kLd; ++i) {
@@ -206,8 +206,7 @@ __global__ void fft_fwd_kernel(FftArgs a, const double *grid, void *four_v, cons
       C v = {0, 0};
       if (ok[i]) {
         if constexpr (F32) {
-          const float s32 = f64_to_f32(sv[i]);
-          v = C{s32 * f64_to_f32(x[i].x), s32 * f64_to_f32(x[i].y)};
+          v = C{sv[i] * f64_to_f32(x[i].x), sv[i] * f64_to_f32(x[i].y)};
         } else {
           v = C{sv[i] * x[i].x, sv[i] * x[i].y};
         }
@@ -228,15 +227,13 @@ __global__ void fft_fwd_kernel(FftArgs a, const double *grid, void *four_v, cons
     const C E = {(T)0.5 * (zm.x + zr.x), (T)0.5 * (zm.y - zr.y)};
     const C O = {(T)0.5 * (zm.y + zr.y), (T)-0.5 * (zm.x - zr.x)};
     const C X = addz(E, cmulz(tw[m], O));
-    T s;
-    if constexpr (F32) s = f64_to_f32(m_scale[m]); else s = m_scale[m];
+    const T s = m_scale[m];
     four[((int64_t)j * M1 + m) * a.ncol + c] = C{s * X.x, s * X.y};
   }
 }
 
 template <typename T>
-__global__ void fft_inv_kernel(FftArgs a, const void *four_v, double *grid, const double *m_scale,
-                               const double *out_scale) {
+__global__ void fft_inv_kernel(FftArgs a, const void *four_v, double *grid, const T *m_scale, const T *out_scale) {
   using C = typename V2<T>::t;
   constexpr bool F32 = std::is_same<T, float>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -254,7 +251,7 @@ __global__ void fft_inv_kernel(FftArgs a, const void *four_v, double *grid, cons
   constexpr int kLd = 4;
   for (int t0 = 0; t0 < a.np * h; t0 += kLd * blockDim.x) {
     C va[kLd], vb[kLd];
-    double sa[kLd], sb[kLd];
+    T sa[kLd], sb[kLd];
     bool oka[kLd], okb[kLd];
 #pragma unroll
     for (int i = 0; i < kLd; ++i) {
@@ -276,18 +273,9 @@ __global__ void fft_inv_kernel(FftArgs a, const void *four_v, double *grid, cons
       if (t >= a.np * h) break;
       const int m = fdiv(t, a.mag_np, a.np), q = t - m * a.np;
       const int mr = h - m;
-      auto toT = [](double v) -> T {
-        if constexpr (F32) return f64_to_f32(v); else return v;
-      };
       C A = {0, 0}, Bc = {0, 0};
-      if (oka[i]) {
-        const T s = toT(sa[i]);
-        A = C{s * va[i].x, m == 0 ? (T)0 : s * va[i].y};
-      }
-      if (okb[i]) {
-        const T s = toT(sb[i]);
-        Bc = C{s * vb[i].x, mr == 0 ? (T)0 : -s * vb[i].y};  // conj(X_{h-m})
-      }
+      if (oka[i]) A = C{sa[i] * va[i].x, m == 0 ? (T)0 : sa[i] * va[i].y};
+      if (okb[i]) Bc = C{sb[i] * vb[i].x, mr == 0 ? (T)0 : -sb[i] * vb[i].y};  // conj(X_{h-m})
       // E' = X_m + conj X_{h-m},  O' = (X_m - conj X_{h-m}) e^{+2 pi i m / n},  Z' = E' + i O'
       const C E = addz(A, Bc);
       const C w = tw[m];
@@ -303,11 +291,10 @@ __global__ void fft_inv_kernel(FftArgs a, const void *four_v, double *grid, cons
     const int q = fdiv(t, a.mag_h, h), k = t - q * h;
     const int c = c0 + q;
     if (c >= a.ncol) continue;
-    const double s = out_scale[(c % 3) * a.nlat + j];
+    const T s = out_scale[(c % 3) * a.nlat + j];
     const C v = r[t];  // conj of z_k = x_{2k} + i x_{2k+1}
     if constexpr (F32) {
-      const float s32 = f64_to_f32(s);
-      g2[((int64_t)c * a.nlat + j) * h + k] = make_double2(f32_to_f64(s32 * v.x), f32_to_f64(-s32 * v.y));
+      g2[((int64_t)c * a.nlat + j) * h + k] = make_double2(f32_to_f64(s * v.x), f32_to_f64(-s * v.y));
     } else {
       g2[((int64_t)c * a.nlat + j) * h + k] = make_double2(s * v.x, -s * v.y);
     }
@@ -370,27 +357,31 @@ size_t fft_smem_bytes(const Plan &pl) {
   return (size_t)pl.fft.nsplit * pl.fft.n * (fft32(pl) ? sizeof(float2) : sizeof(double2));
 }
 
-cudaError_t launch_fft_fwd(Plan &pl, const double *grid, double2 *four, int B, const double *in_scale,
-                           const double *m_scale, cudaStream_t st) {
+cudaError_t launch_fft_fwd(Plan &pl, const double *grid, double2 *four, int B, const void *in_scale,
+                           const void *m_scale, cudaStream_t st) {
   FftArgs a = make_args(pl, B);
   dim3 g((unsigned)((a.ncol + a.np - 1) / a.np), (unsigned)pl.nlat);
   size_t sm = fft_smem_bytes(pl);
   if (fft32(pl))
-    fft_fwd_kernel<float><<<g, 256, sm, st>>>(a, grid, four, in_scale, m_scale);
+    fft_fwd_kernel<float><<<g, 256, sm, st>>>(a, grid, four, static_cast<const float *>(in_scale),
+                                              static_cast<const float *>(m_scale));
   else
-    fft_fwd_kernel<double><<<g, 256, sm, st>>>(a, grid, four, in_scale, m_scale);
+    fft_fwd_kernel<double><<<g, 256, sm, st>>>(a, grid, four, static_cast<const double *>(in_scale),
+                                               static_cast<const double *>(m_scale));
   return cudaGetLastError();
 }
 
-cudaError_t launch_fft_inv(Plan &pl, const double2 *four, double *grid, int B, const double *m_scale,
-                           const double *out_scale, cudaStream_t st) {
+cudaError_t launch_fft_inv(Plan &pl, const double2 *four, double *grid, int B, const void *m_scale,
+                           const void *out_scale, cudaStream_t st) {
   FftArgs a = make_args(pl, B);
   dim3 g((unsigned)((a.ncol + a.np - 1) / a.np), (unsigned)pl.nlat);
   size_t sm = fft_smem_bytes(pl);
   if (fft32(pl))
-    fft_inv_kernel<float><<<g, 256, sm, st>>>(a, four, grid, m_scale, out_scale);
+    fft_inv_kernel<float><<<g, 256, sm, st>>>(a, four, grid, static_cast<const float *>(m_scale),
+                                              static_cast<const float *>(out_scale));
   else
-    fft_inv_kernel<double><<<g, 256, sm, st>>>(a, four, grid, m_scale, out_scale);
+    fft_inv_kernel<double><<<g, 256, sm, st>>>(a, four, grid, static_cast<const double *>(m_scale),
+                                               static_cast<const double *>(out_scale));
   return cudaGetLastError();
 }
 

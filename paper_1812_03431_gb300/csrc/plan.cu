@@ -368,6 +368,20 @@ rexi_status build_plan(const rexi_params &prm, Plan *pl) {
     if ((e = upload(&pl->mscale_c, mc, &bytes))) return fail("mscale", e);
     if ((e = upload(&pl->mscale_adj, ma, &bytes))) return fail("mscale", e);
     if ((e = upload(&pl->mscale_one, m1, &bytes))) return fail("mscale", e);
+    {
+      // binary32 copies (round to nearest even; every scale is a normal binary32 number)
+      auto up32 = [&](float **d, const std::vector<double> &v) {
+        std::vector<float> f(v.begin(), v.end());
+        cudaError_t r = cudaMalloc(d, f.size() * sizeof(float));
+        if (r == cudaSuccess) r = cudaMemcpy(*d, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
+        bytes += f.size() * sizeof(float);
+        return r;
+      };
+      if ((e = up32(&pl->scale_ana_in32, sin_)) || (e = up32(&pl->scale_syn_out32, sout)) ||
+          (e = up32(&pl->mscale_fwd32, mf)) || (e = up32(&pl->mscale_c32, mc)) || (e = up32(&pl->mscale_adj32, ma)) ||
+          (e = up32(&pl->mscale_one32, m1)))
+        return fail("scales", e);
+    }
     FftPlan &f = pl->fft;
     f.n = pl->nlon;
     fft_factor(f.n / 2, f.radix, &f.nstages);  // half-length complex FFT per real row
@@ -713,6 +727,8 @@ void free_plan(Plan *pl) {
                   pl->beta_dev, pl->w_fwd, pl->w_adj, pl->rflags_dev, pl->mu_dev, pl->tabP, pl->tabH,
                   pl->tabP_hi, pl->tabP_lo, pl->tabH_hi, pl->tabH_lo, pl->scale_ana_in,
                   pl->scale_syn_out, pl->mscale_fwd, pl->mscale_c, pl->mscale_adj, pl->mscale_one,
+                  pl->scale_ana_in32, pl->scale_syn_out32, pl->mscale_fwd32, pl->mscale_c32, pl->mscale_adj32,
+                  pl->mscale_one32,
                   pl->zd_syn, pl->zd_ana_adj, pl->zd_one, pl->zd_mone, pl->fft.tw_dev, pl->fft.tw32_dev, pl->four,
                   pl->s_in, pl->s_out, pl->s_ff, pl->partial, pl->yscratch, pl->counter, pl->tc_tab_ana,
                   pl->tc_tab_syn, pl->tc_work_ana, pl->tc_work_syn, pl->dev_err, pl->phi_zc, pl->phi_q, pl->phi_abf, pl->ffc_rows, pl->ffc_ia};

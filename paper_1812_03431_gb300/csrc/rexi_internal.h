@@ -186,6 +186,9 @@ struct Plan {
   double *mscale_c = nullptr;       // [N+1]: c_m = 1, 2, 2, ...
   double *mscale_adj = nullptr;     // [N+1]: 1/nlon, 1/(2 nlon), ...
   double *mscale_one = nullptr;     // [N+1]: 1
+  // the same six scales rounded to binary32 (the mixed form's FFTs scale in FP32)
+  float *scale_ana_in32 = nullptr, *scale_syn_out32 = nullptr, *mscale_fwd32 = nullptr, *mscale_c32 = nullptr,
+        *mscale_adj32 = nullptr, *mscale_one32 = nullptr;
   double *zd_syn = nullptr;         // [nspec]: -a/(n(n+1)) (0 at n = 0)
   double *zd_ana_adj = nullptr;     // [nspec]: +a/(n(n+1))
   double *zd_one = nullptr;         // [nspec]: 1
@@ -311,10 +314,11 @@ cudaError_t launch_transpose_in(const double2 *user, double2 *sint, int64_t nspe
                                 cudaStream_t st);
 cudaError_t launch_transpose_out(const double2 *sint, double2 *user, int64_t nspec, int B, int N,
                                  cudaStream_t st);
+// scales: binary64 arrays in the FP64 form, their binary32 copies in the mixed form
 cudaError_t launch_fft_fwd(Plan &pl, const double *grid, double2 *four, int B,
-                           const double *in_scale, const double *m_scale, cudaStream_t st);
+                           const void *in_scale, const void *m_scale, cudaStream_t st);
 cudaError_t launch_fft_inv(Plan &pl, const double2 *four, double *grid, int B,
-                           const double *m_scale, const double *out_scale, cudaStream_t st);
+                           const void *m_scale, const void *out_scale, cudaStream_t st);
 cudaError_t launch_leg_ana(Plan &pl, const double2 *four, double2 *sint, int B,
                            const double *zdscale, cudaStream_t st);
 cudaError_t launch_leg_syn(Plan &pl, const double2 *sint, double2 *four, int B,
